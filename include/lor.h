@@ -1,0 +1,188 @@
+/*
+ * lor.h -- C ABI of liblor, a GB300 (sm_103a) implementation of
+ * low-order-refined (LOR) preconditioning for high-order H1 diffusion,
+ *   -div(kappa grad u) = f  on hexahedral meshes, u = 0 on the boundary,
+ * after W. Pazner, Tz. Kolev, J.-S. Camier, "End-to-end GPU acceleration of
+ * low-order-refined preconditioning for high-order finite element
+ * discretizations" (arXiv 2210.12253).
+ *
+ * The paper's pipeline (Section 3) is: S1.1 high-order operator setup
+ * (partial assembly of D at quadrature points), S1.2 LOR matrix assembly
+ * (A1 macro-element batching, A2 local CSR, A4 boundary elimination),
+ * S1.3 preconditioner setup, S2 preconditioned CG whose iterations apply the
+ * high-order operator A_p = P^T G^T B^T D B G P matrix-free (Eq. (4),
+ * Step S2.1) and the LOR-based preconditioner B_h (Step S2.2).  This library
+ * implements that pipeline on one GPU for structured meshes of the unit cube
+ * (nex x ney x nez trilinear hexes with arbitrary interior vertex positions),
+ * with B_h a Chebyshev-Jacobi smoother on the assembled LOR matrix.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every call returns LOR_OK (0) or a positive LOR_E* code;
+ *    lor_last_error() gives a message.  A failed call leaves the context
+ *    usable unless it returns LOR_ECUDA.
+ *  - Pointers named d_* are DEVICE pointers owned by the caller and borrowed
+ *    for the duration of the call (for asynchronous calls: until the work
+ *    enqueued on the stream has run).  Host scalars are returned through
+ *    plain host pointers.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is enqueued on it in order; no call synchronises
+ *    the device except those documented as returning a host scalar.
+ *  - Layouts (x fastest everywhere):
+ *      vertex (a,b,c)      -> a + (nex+1)(b + (ney+1) c), 3 f64 (x,y,z)
+ *      element (ex,ey,ez)  -> ex + nex (ey + ney ez)
+ *      DOF (I,J,K)         -> I + nx (J + ny K), nx = nex p + 1, etc.;
+ *                             element node (i,j,k) is DOF (ex p+i, ey p+j, ez p+k)
+ *      quadrature point    -> g0 + q (g1 + q g2), q = p + 2 Gauss-Legendre
+ *                             points per axis; kappa is [nel][q^3] f64
+ *      LOR CSR             -> rowptr int64[N+1], colidx int32[nnz] (sorted),
+ *                             values f64 or f32 [nnz]; full symmetric matrix
+ *                             with the 27-point pattern of the LOR mesh.
+ *  - Essential DOFs are all DOFs on the boundary of the unit cube.  Their rows
+ *    and columns are eliminated with the sparsity pattern kept and the
+ *    diagonal set to 1 (Step S1.2, A4); the high-order apply returns
+ *    y_ess = x_ess and ignores x_ess elsewhere.
+ */
+#ifndef LOR_H
+#define LOR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOR_MAX_P 10 /* largest supported polynomial degree */
+
+enum lor_status {
+  LOR_OK = 0,
+  LOR_EINVAL = 1,   /* bad argument (size, pointer, degree, coefficient <= 0 or NaN) */
+  LOR_EGEOM = 2,    /* a Jacobian determinant <= 0 (inverted or degenerate element) */
+  LOR_ENOMEM = 3,   /* device allocation failed */
+  LOR_ECUDA = 4,    /* CUDA runtime error (message in lor_last_error) */
+  LOR_ENOCONV = 5,  /* PCG hit maxit before reaching the tolerance */
+  LOR_ESTATE = 7    /* call out of order (e.g. apply before set_coefficient) */
+};
+
+enum lor_dtype { LOR_F64 = 0, LOR_F32 = 1 };
+
+enum lor_precond { LOR_PRECOND_NONE = 0, LOR_PRECOND_JACOBI = 1, LOR_PRECOND_CHEB = 2 };
+
+typedef struct lor_ctx lor_ctx;
+
+typedef struct lor_config {
+  int32_t p;   /* polynomial degree, 1 <= p <= LOR_MAX_P */
+  int32_t nex; /* elements along x, y, z (>= 1 each) */
+  int32_t ney;
+  int32_t nez;
+} lor_config;
+
+/* Message for the last failed call on ctx (or, for ctx == NULL, the last
+ * failed lor_create on this thread).  Valid until the next call. */
+const char* lor_last_error(const lor_ctx* ctx);
+
+/* Create a context for the order-p space on the structured hex mesh with
+ * vertex coordinates d_vertices [(nex+1)(ney+1)(nez+1)][3] f64 (device,
+ * copied).  Element maps are the trilinear maps through the 8 element
+ * vertices (p_g = 1); the LOR mesh (Section 2.1) splits each element at the
+ * Gauss-Lobatto points into p^3 sub-hexes.  Checks every Jacobian at the
+ * Gauss points used by the high-order operator and by the LOR assembly and
+ * returns LOR_EGEOM if one is <= 0.  Synchronises the stream.  *out receives
+ * the context (NULL on failure). */
+int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, void* stream);
+
+/* Free the context and every device buffer it owns.  Synchronises the device
+ * work of the context first.  NULL is accepted. */
+int lor_destroy(lor_ctx* ctx);
+
+/* Sizes: DOFs N = nx ny nz, LOR nonzeros (3nx-2)(3ny-2)(3nz-2), elements,
+ * quadrature points nel q^3.  Any pointer may be NULL. */
+int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int64_t* nqpt);
+
+/* Step S1.1 (high-order operator setup, partial assembly): from the mesh and
+ * kappa [nel][q^3] (device, f64) compute at every Gauss point
+ *   D_g = kappa_g w_g detJ_g J_g^-1 J_g^-T
+ * in FP64 and keep it (and a copy of kappa) in the context.  kappa must be
+ * finite and > 0; a violation is recorded on the device and reported by the
+ * next lor_check (the call itself does not synchronise). */
+int lor_set_coefficient(lor_ctx* ctx, const double* d_kappa, void* stream);
+
+/* Synchronise the stream and report any error recorded by earlier device
+ * work of this context (LOR_EINVAL for a bad coefficient). */
+int lor_check(lor_ctx* ctx, void* stream);
+
+/* Step S1.2 / A2: build the CSR sparsity of the LOR matrix (27-point graph of
+ * the LOR mesh, columns ascending, Dirichlet rows included) inside the
+ * context.  If d_rowptr (int64[N+1]) and d_colidx (int32[nnz]) are non-NULL
+ * the pattern is also written there.  Idempotent. */
+int lor_build_pattern(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, void* stream);
+
+/* Step S1.2 / A1 + A4: assemble the values of the LOR matrix A_h for the
+ * current coefficient (the p = 1 stiffness matrix of the LOR mesh; each
+ * sub-hex block integrated by 2x2x2 Gauss on the sub-hex's trilinear map with
+ * kappa averaged over the high-order Gauss points inside the sub-hex), then
+ * eliminate the essential rows and columns.  Geometry (Jacobians,
+ * determinants) is always FP64; dtype selects the arithmetic and storage of
+ * the block entries (LOR_F64 or LOR_F32).  d_values: nnz entries of dtype in
+ * the order of lor_build_pattern, or NULL to assemble into the context's own
+ * matrix of that dtype (the one lor_precond_setup uses).  Requires
+ * lor_build_pattern and lor_set_coefficient. */
+int lor_assemble(lor_ctx* ctx, void* d_values, int dtype, void* stream);
+
+/* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum
+ * factorisation (B = [B(x)B(x)d; B(x)d(x)B; d(x)B(x)B] with the 1D
+ * interpolation/derivative matrices, D from lor_set_coefficient), in FP64.
+ * Dirichlet rows: y_ess = x_ess; x_ess is ignored in the free rows.
+ * d_x, d_y: f64[N], must not alias. */
+int lor_apply(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
+
+/* Backward of y = A_p(kappa) x for the cotangent d_gy (FP64):
+ *   d_gx     = A_p gy                                     (f64[N], may be NULL)
+ *   d_gkappa = d(gy^T A_p x)/d kappa = grad_ref(x)^T (D/kappa) grad_ref(gy)
+ *              at every Gauss point, x and gy taken as 0 on essential DOFs
+ *                                                          (f64[nel q^3], may be NULL).
+ * This is the gradient used by the adjoint method for dJ/dkappa. */
+int lor_apply_backward(lor_ctx* ctx, const double* d_x, const double* d_gy, double* d_gx, double* d_gkappa,
+                       void* stream);
+
+/* Load vector b_i = sum_e sum_g w_g detJ_g f_g phi_i(x_g) for f given at the
+ * Gauss points (d_f [nel][q^3] f64) or f = 1 (d_f == NULL); b_ess = 0. */
+int lor_load_vector(lor_ctx* ctx, const double* d_f, double* d_b, void* stream);
+
+/* y = A_h x with the context's assembled LOR matrix of `dtype` (x, y f64;
+ * in LOR_F32 mode x is rounded to f32 and the product accumulated in f32). */
+int lor_spmv(lor_ctx* ctx, int dtype, const double* d_x, double* d_y, void* stream);
+
+/* Preconditioner B_h on the context's assembled LOR matrix of `dtype`
+ * (Section 2.2: any preconditioner of A_h preconditions A_p):
+ *   LOR_PRECOND_JACOBI: z = D_h^-1 r, D_h = diag(A_h);
+ *   LOR_PRECOND_CHEB:   `degree` steps of the Chebyshev semi-iteration for
+ *                       A_h z = r with M = D_h from z_0 = 0 on the interval
+ *                       [lo_ratio lmax, hi_ratio lmax] (Saad, Alg. 12.1).
+ * lmax = lambda_max if > 0, else estimated by `power_iters` steps of the power
+ * iteration w = D_h^-1 A_h v, lambda = |w|/|v|, v = w/|w| from d_v0 (f64[N],
+ * device; NULL means all ones).  Returns lmax in *lambda_out (host, may be
+ * NULL); synchronises the stream when it estimates lmax.  The smoother
+ * computes in `dtype`. */
+int lor_precond_setup(lor_ctx* ctx, int kind, int dtype, int degree, double lo_ratio, double hi_ratio,
+                      double lambda_max, int power_iters, const double* d_v0, double* lambda_out, void* stream);
+
+/* z = B_h r with the preconditioner from lor_precond_setup (r, z f64[N]). */
+int lor_precond_apply(lor_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
+/* Section 3, step S2: preconditioned CG for A_p x = b with x_0 = 0, the
+ * operator of lor_apply (FP64) and the preconditioner of lor_precond_setup
+ * (identity if none).  Dot products and recurrences are FP64.  Stops when
+ * |r_k|/|b| <= rtol for the recurrence residual and the true residual
+ * b - A_p x confirms it (otherwise continues from the true residual).
+ * Returns the iteration count and final relative residual through host
+ * pointers (may be NULL), LOR_ENOCONV after maxit iterations.  Synchronises
+ * the stream (it reads the residual norm on the host). */
+int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int maxit, int* iters,
+                  double* final_rel_residual, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOR_H */

@@ -1,0 +1,244 @@
+// k_geom.cu -- Step S1.1 (high-order operator setup, partial assembly) and the
+// geometry helpers shared by it: Jacobians of the trilinear element maps at
+// Gauss points, D = kappa w detJ J^-1 J^-T, the geometry validity check, and
+// the load vector.
+//
+// GB300 notes: FP64 runs at about 2 DFMA/clk/SM on this part (1/64 of FP32),
+// so these kernels are bound by FP64 issue, not by HBM.  The FP64 work per
+// point is kept minimal: a trilinear map has dx/dxi_0 independent of xi_0 (and
+// likewise for the other columns), so each Jacobian column is tabulated once
+// per element on a q x q grid in shared memory; per point only the adjugate
+// (three cross products), the determinant and six dot products remain.
+#include "lor_internal.cuh"
+
+namespace {
+
+// Corner c = c0 + 2 c1 + 4 c2 of element e.
+__device__ __forceinline__ void element_corner(const LorMesh& m, int64_t e, int c, double X[3]) {
+  const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+  const int64_t a = ex + (c & 1), b = ey + ((c >> 1) & 1), cc = ez + ((c >> 2) & 1);
+  const double* v = m.verts + 3 * (a + (int64_t)(m.nex + 1) * (b + (int64_t)(m.ney + 1) * cc));
+  X[0] = v[0];
+  X[1] = v[1];
+  X[2] = v[2];
+}
+
+// Tabulate the three Jacobian columns of the trilinear map of element e on
+// the tensor grid of the L reference coordinates t[0..L):
+//   col[d][u + L v][comp], with (u, v) the two coordinates other than d, in
+//   increasing axis order.  E.g. col[0][g1 + L g2] = dx/dxi_0 at (., t_g1, t_g2).
+// Cooperative over the block; ends with __syncthreads().
+__device__ void jacobian_columns(const LorMesh& m, int64_t e, const double* t, int L, double* Ehalf,
+                                 double* col) {
+  // Ehalf[d][pair][comp]: half edge vectors along axis d for the 4 edges
+  // parallel to it; pair = (other0 bit) + 2 (other1 bit).
+  for (int idx = threadIdx.x; idx < 36; idx += blockDim.x) {
+    const int d = idx / 12, pair = (idx / 3) % 4, comp = idx % 3;
+    const int o0 = pair & 1, o1 = pair >> 1;
+    int lo = 0, hi = 0;
+    if (d == 0) { lo = 0 + 2 * o0 + 4 * o1; hi = lo + 1; }
+    if (d == 1) { lo = o0 + 0 + 4 * o1; hi = lo + 2; }
+    if (d == 2) { lo = o0 + 2 * o1 + 0; hi = lo + 4; }
+    double A[3], Bv[3];
+    element_corner(m, e, lo, A);
+    element_corner(m, e, hi, Bv);
+    Ehalf[idx] = 0.5 * (Bv[comp] - A[comp]);
+  }
+  __syncthreads();
+  const int L2 = L * L;
+  for (int idx = threadIdx.x; idx < 3 * L2 * 3; idx += blockDim.x) {
+    const int d = idx / (L2 * 3), uv = (idx / 3) % L2, comp = idx % 3;
+    const int u = uv % L, v = uv / L;
+    const double tu = t[u], tv = t[v];
+    const double wu0 = 0.5 * (1.0 - tu), wu1 = 0.5 * (1.0 + tu);
+    const double wv0 = 0.5 * (1.0 - tv), wv1 = 0.5 * (1.0 + tv);
+    const double* E = Ehalf + d * 12 + comp;
+    col[idx] = wv0 * (wu0 * E[0] + wu1 * E[3]) + wv1 * (wu0 * E[6] + wu1 * E[9]);
+  }
+  __syncthreads();
+}
+
+// Adjugate rows of J = [c0 c1 c2]: a0 = c1 x c2, a1 = c2 x c0, a2 = c0 x c1;
+// J^-1 has rows a_i / det, det = c0 . a0.
+__device__ __forceinline__ void cross(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
+                                               double* __restrict__ kcopy, double* __restrict__ Dq,
+                                               int* __restrict__ status) {
+  constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q;
+  __shared__ double Ehalf[36];
+  __shared__ double col[3 * Q2 * 3];
+  __shared__ double sx[Q], sw[Q];
+  if (threadIdx.x < Q) {
+    sx[threadIdx.x] = T.gx[threadIdx.x];
+    sw[threadIdx.x] = T.gw[threadIdx.x];
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
+    jacobian_columns(m, e, sx, Q, Ehalf, col);
+    for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
+      const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
+      const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
+      const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
+      const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
+      double a0[3], a1[3], a2[3];
+      cross(c1, c2, a0);
+      cross(c2, c0, a1);
+      cross(c0, c1, a2);
+      const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
+      const double k = kin[e * Q3 + pt];
+      if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
+      if (!(det > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
+      const double s = k * (sw[g0] * sw[g1] * sw[g2]) / det;
+      double* D = Dq + e * 6 * Q3 + pt;
+      D[0 * Q3] = s * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
+      D[1 * Q3] = s * (a0[0] * a1[0] + a0[1] * a1[1] + a0[2] * a1[2]);
+      D[2 * Q3] = s * (a0[0] * a2[0] + a0[1] * a2[1] + a0[2] * a2[2]);
+      D[3 * Q3] = s * (a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+      D[4 * Q3] = s * (a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2]);
+      D[5 * Q3] = s * (a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+      kcopy[e * Q3 + pt] = k;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// Jacobian determinant check at the tensor grid t[0..L) of every element.
+__global__ void __launch_bounds__(128) k_geometry_check(LorMesh m, LorTables T, int L, int use_sub,
+                                                        int* __restrict__ status) {
+  __shared__ double Ehalf[36];
+  __shared__ double col[3 * (2 * LOR_MAX_P + 2) * (2 * LOR_MAX_P + 2) * 3];
+  __shared__ double t[2 * LOR_MAX_P + 2];
+  if (threadIdx.x < L) t[threadIdx.x] = use_sub ? T.sub_t[threadIdx.x] : T.gx[threadIdx.x];
+  __syncthreads();
+  int bad = 0;
+  const int L2 = L * L;
+  for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
+    jacobian_columns(m, e, t, L, Ehalf, col);
+    for (int pt = threadIdx.x; pt < L2 * L; pt += blockDim.x) {
+      const int g0 = pt % L, g1 = (pt / L) % L, g2 = pt / L2;
+      const double* c0 = col + 0 * L2 * 3 + 3 * (g1 + L * g2);
+      const double* c1 = col + 1 * L2 * 3 + 3 * (g0 + L * g2);
+      const double* c2 = col + 2 * L2 * 3 + 3 * (g0 + L * g1);
+      double a0[3];
+      cross(c1, c2, a0);
+      const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
+      if (!(det > 0.0)) bad = LOR_FLAG_BAD_GEOM;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// Load vector: b_e = (B (x) B (x) B)^T (w detJ f) per element, scatter-added
+// into the non-essential DOFs (b must be zeroed first).
+template <int P>
+__global__ void __launch_bounds__(128) k_load_vector(LorMesh m, LorTables T, const double* __restrict__ f,
+                                                     double* __restrict__ b) {
+  constexpr int Q = P + 2, N = P + 1, Q2 = Q * Q, Q3 = Q * Q * Q;
+  __shared__ double Ehalf[36];
+  __shared__ double col[3 * Q2 * 3];
+  __shared__ double sx[Q], sw[Q], sB[Q * N];
+  __shared__ double v[Q3], t1[N * Q2];
+  double* t2 = v;  // v is dead once t1 is formed (N N Q <= Q^3)
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sB[i] = T.B[i];
+  if (threadIdx.x < Q) {
+    sx[threadIdx.x] = T.gx[threadIdx.x];
+    sw[threadIdx.x] = T.gw[threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
+    jacobian_columns(m, e, sx, Q, Ehalf, col);
+    for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
+      const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
+      const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
+      const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
+      const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
+      double a0[3];
+      cross(c1, c2, a0);
+      const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
+      const double fv = f ? f[e * Q3 + pt] : 1.0;
+      v[pt] = sw[g0] * sw[g1] * sw[g2] * det * fv;
+    }
+    __syncthreads();
+    // contract g2 -> k:  t1[k][g1][g0]
+    for (int idx = threadIdx.x; idx < N * Q2; idx += blockDim.x) {
+      const int g0 = idx % Q, g1 = (idx / Q) % Q, k = idx / Q2;
+      double s = 0.0;
+      for (int g2 = 0; g2 < Q; ++g2) s += sB[g2 * N + k] * v[g0 + Q * (g1 + Q * g2)];
+      t1[idx] = s;
+    }
+    __syncthreads();
+    // contract g1 -> j:  t2[k][j][g0]
+    for (int idx = threadIdx.x; idx < N * N * Q; idx += blockDim.x) {
+      const int g0 = idx % Q, j = (idx / Q) % N, k = idx / (Q * N);
+      double s = 0.0;
+      for (int g1 = 0; g1 < Q; ++g1) s += sB[g1 * N + j] * t1[g0 + Q * (g1 + Q * k)];
+      t2[idx] = s;
+    }
+    __syncthreads();
+    // contract g0 -> i and scatter
+    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+    for (int idx = threadIdx.x; idx < N * N * N; idx += blockDim.x) {
+      const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
+      double s = 0.0;
+      for (int g0 = 0; g0 < Q; ++g0) s += sB[g0 * N + i] * t2[g0 + Q * (j + N * k)];
+      const int64_t I = ex * P + i, J = ey * P + j, K = ez * P + k;
+      if (!lor_is_essential(I, J, K, m.nx, m.ny, m.nz)) atomicAdd(b + I + m.nx * (J + m.ny * K), s);
+    }
+    __syncthreads();
+  }
+}
+
+int grid_for(int64_t nel) {
+  const int64_t cap = 152 * 64;
+  return (int)(nel < cap ? nel : cap);
+}
+
+}  // namespace
+
+cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double* kappa_in, double* kappa_copy,
+                             double* Dq, int* d_status, cudaStream_t s) {
+  const int g = grid_for(m.nel);
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: k_setup<P><<<g, 128, 0, s>>>(m, T, kappa_in, kappa_copy, Dq, d_status); break;
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_geometry_check(const LorMesh& m, const LorTables& T, int* d_status, cudaStream_t s) {
+  const int g = grid_for(m.nel);
+  k_geometry_check<<<g, 128, 0, s>>>(m, T, T.q, 0, d_status);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  k_geometry_check<<<g, 128, 0, s>>>(m, T, 2 * T.p, 1, d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_load_vector(const LorMesh& m, const LorTables& T, const double* f, double* b,
+                                   cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(b, 0, sizeof(double) * m.ndof, s);
+  if (err != cudaSuccess) return err;
+  const int g = grid_for(m.nel);
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: k_load_vector<P><<<g, 128, 0, s>>>(m, T, f, b); break;
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}

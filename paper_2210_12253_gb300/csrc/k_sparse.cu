@@ -1,0 +1,367 @@
+// k_sparse.cu -- the solve phase on the assembled LOR matrix (Step S2.2's
+// building blocks: spmv and vector updates) and the preconditioned CG of
+// Section 3, step S2.
+//
+// The preconditioner B_h is a Chebyshev-Jacobi smoother on A_h (any uniform
+// preconditioner of the LOR matrix preconditions A_p, Section 2.2).  Each
+// Chebyshev step is one kernel: the CSR row product, the residual, the
+// direction update and the iterate update are fused per row, so a degree-k
+// smoother reads the matrix k-1 times and touches each vector once per step.
+// In the mixed-precision mode the matrix, the diagonal and the smoother's
+// vectors are FP32; PCG's vectors, dot products and recurrences stay FP64.
+#include <math.h>
+
+#include "lor_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_rows(int64_t n) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  return (int)(b < 152 * 32 ? b : 152 * 32);
+}
+
+#define LOR_GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// sum_j A_ij x_j in the matrix precision VT (x converted on the fly).
+template <typename VT, typename XT>
+__device__ __forceinline__ VT row_product(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                          const VT* __restrict__ vals, const XT* __restrict__ x, int64_t i) {
+  VT s = 0;
+  const int64_t b = rowptr[i], e = rowptr[i + 1];
+  for (int64_t j = b; j < e; ++j) s += vals[j] * (VT)x[colidx[j]];
+  return s;
+}
+
+template <typename VT>
+__global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                           const VT* __restrict__ vals, VT* __restrict__ dinv) {
+  LOR_GRID_STRIDE(i, n) {
+    VT d = 0;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j)
+      if (colidx[j] == i) d += vals[j];
+    dinv[i] = (VT)1 / d;
+  }
+}
+
+template <typename VT>
+__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                       const VT* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y) {
+  LOR_GRID_STRIDE(i, n) y[i] = (double)row_product<VT, double>(rowptr, colidx, vals, x, i);
+}
+
+// w = D^-1 A v (power iteration), FP64 vectors, VT matrix.
+template <typename VT>
+__global__ void k_dinv_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                            const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ v,
+                            double* __restrict__ w) {
+  LOR_GRID_STRIDE(i, n) w[i] = (double)(dinv[i] * row_product<VT, double>(rowptr, colidx, vals, v, i));
+}
+
+// Chebyshev step 0 from z_0 = 0: d = z = D^-1 r / theta.  If zout64 is set
+// (degree 1) the result goes straight to the FP64 output.
+template <typename VT>
+__global__ void k_cheb_first(int64_t n, const VT* __restrict__ dinv, const double* __restrict__ r, VT inv_theta,
+                             VT* __restrict__ z, VT* __restrict__ d, double* __restrict__ zout64) {
+  LOR_GRID_STRIDE(i, n) {
+    const VT v = dinv[i] * (VT)r[i] * inv_theta;
+    if (zout64) {
+      zout64[i] = (double)v;
+    } else {
+      z[i] = v;
+      d[i] = v;
+    }
+  }
+}
+
+// Chebyshev step j >= 1:  res = r - A z_in;  d = c1 d + c2 D^-1 res;
+// z_out = z_in + d (into zout64 as FP64 on the last step).
+template <typename VT>
+__global__ void k_cheb_step(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                            const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ r,
+                            const VT* __restrict__ zin, VT* __restrict__ zout, VT* __restrict__ d, VT c1, VT c2,
+                            double* __restrict__ zout64) {
+  LOR_GRID_STRIDE(i, n) {
+    const VT res = (VT)r[i] - row_product<VT, VT>(rowptr, colidx, vals, zin, i);
+    const VT dn = c1 * d[i] + c2 * dinv[i] * res;
+    const VT zn = zin[i] + dn;
+    if (zout64) {
+      zout64[i] = (double)zn;
+    } else {
+      d[i] = dn;
+      zout[i] = zn;
+    }
+  }
+}
+
+__global__ void k_fill(double* __restrict__ v, int64_t n, double a) {
+  LOR_GRID_STRIDE(i, n) v[i] = a;
+}
+
+__global__ void k_scale(double* __restrict__ v, int64_t n, double a) {
+  LOR_GRID_STRIDE(i, n) v[i] *= a;
+}
+
+template <typename VT>
+__global__ void k_jacobi(int64_t n, const VT* __restrict__ dinv, const double* __restrict__ r,
+                         double* __restrict__ z) {
+  LOR_GRID_STRIDE(i, n) z[i] = (double)(dinv[i] * (VT)r[i]);
+}
+
+// ---------------------------------------------------------------- reductions
+// Block partial sums of a.b into partial[blockIdx.x] (fixed grid, fixed
+// order: the result is deterministic).
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kThreads / 32; ++w) s += warp_part[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, const double* __restrict__ a,
+                                                          const double* __restrict__ b,
+                                                          double* __restrict__ partial) {
+  double s = 0.0;
+  LOR_GRID_STRIDE(i, n) s += a[i] * b[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_reduce_final(const double* __restrict__ partial, int np,
+                                                           double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------- PCG vector kernels
+// Device scalars (slots of ctx->red after the partials).
+enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_COUNT = 5 };
+
+// x += alpha p, r -= alpha q with alpha = rz / pq read on the device;
+// also forms the block partials of r.r.
+__global__ void __launch_bounds__(kThreads) k_pcg_xr(int64_t n, const double* __restrict__ S, int rz_slot,
+                                                     const double* __restrict__ p, const double* __restrict__ q,
+                                                     double* __restrict__ x, double* __restrict__ r,
+                                                     double* __restrict__ partial) {
+  const double alpha = S[rz_slot] / S[S_PQ];
+  double s = 0.0;
+  LOR_GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// p = z + beta p with beta = rz_new / rz_old (device scalars).
+__global__ void k_pcg_p(int64_t n, const double* __restrict__ S, int new_slot, int old_slot,
+                        const double* __restrict__ z, double* __restrict__ p) {
+  const double beta = S[new_slot] / S[old_slot];
+  LOR_GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
+                           double* __restrict__ r) {
+  LOR_GRID_STRIDE(i, n) r[i] = b[i] - Ax[i];
+}
+
+template <typename VT>
+cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
+                            cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  const int g = grid_rows(n);
+  if (c->pc_kind == LOR_PRECOND_JACOBI) {
+    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z);
+    return cudaGetLastError();
+  }
+  VT* zA = (VT*)c->pc_work;
+  VT* zB = zA + n;
+  VT* d = zB + n;
+  const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
+  const double sigma = theta / delta;
+  const int k = c->pc_degree;
+  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr);
+  double rho = 1.0 / sigma;
+  VT* zin = zA;
+  VT* zout = zB;
+  for (int j = 1; j < k; ++j) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+    k_cheb_step<VT><<<g, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
+                                          j == k - 1 ? z : nullptr);
+    rho = rho_new;
+    VT* t = zin;
+    zin = zout;
+    zout = t;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t dot_to(lor_ctx* c, const double* a, const double* b, double* out, cudaStream_t s) {
+  k_dot_partial<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(c->m.ndof, a, b, c->red);
+  k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, out);
+  return cudaGetLastError();
+}
+
+int fail(lor_ctx* c, cudaError_t err, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(err);
+  return LOR_ECUDA;
+}
+
+}  // namespace
+
+cudaError_t lor_launch_diag_inv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                                int dtype, void* dinv, cudaStream_t s) {
+  if (dtype == LOR_F64)
+    k_diag_inv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals,
+                                                             (double*)dinv);
+  else
+    k_diag_inv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals,
+                                                            (float*)dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_spmv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                            int dtype, const double* x, double* y, cudaStream_t s) {
+  if (dtype == LOR_F64)
+    k_spmv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y);
+  else
+    k_spmv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y);
+  return cudaGetLastError();
+}
+
+int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s) {
+  cudaError_t err;
+  if (c->pc_kind == LOR_PRECOND_NONE) {
+    err = cudaMemcpyAsync(z, r, sizeof(double) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
+  } else if (c->pc_dtype == LOR_F64) {
+    err = precond_apply_t<double>(c, c->vals64, c->dinv64, r, z, s);
+  } else {
+    err = precond_apply_t<float>(c, c->vals32, c->dinv32, r, z, s);
+  }
+  return err == cudaSuccess ? LOR_OK : fail(c, err, "precond_apply");
+}
+
+int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  double* v = c->pcg_work;
+  double* w = c->pcg_work + n;
+  cudaError_t err;
+  if (v0) {
+    err = cudaMemcpyAsync(v, v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  } else {
+    k_fill<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0);
+    err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) return fail(c, err, "power iteration");
+  double* S = c->red + LOR_RED_BLOCKS;
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    if (dtype == LOR_F64)
+      k_dinv_spmv<double><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w);
+    else
+      k_dinv_spmv<float><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w);
+    dot_to(c, w, w, S + 0, s);
+    dot_to(c, v, v, S + 1, s);
+    err = cudaMemcpyAsync(c->h_scalar, S, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return fail(c, err, "power iteration");
+    const double nw = sqrt(c->h_scalar[0]), nv = sqrt(c->h_scalar[1]);
+    if (!(nw > 0.0) || !(nv > 0.0)) {
+      c->err = "power iteration: zero vector";
+      return LOR_EINVAL;
+    }
+    lam = nw / nv;
+    // v = w / |w|
+    double* tmp = v;
+    v = w;
+    w = tmp;
+    k_scale<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0 / nw);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(c, err, "power iteration");
+  }
+  *lambda = lam;
+  return LOR_OK;
+}
+
+int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+                 cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  double* r = c->pcg_work;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* S = c->red + LOR_RED_BLOCKS;
+  double* hs = c->h_scalar;
+  const int g = grid_rows(n);
+  cudaError_t err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (err == cudaSuccess) err = dot_to(c, b, b, S + S_BB, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_BB, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return fail(c, err, "pcg");
+  const double nb = sqrt(hs[0]);
+  int it = 0;
+  double rel = 0.0;
+  int status = LOR_ENOCONV;
+  if (nb == 0.0) {
+    status = LOR_OK;
+  } else {
+    int rc = lor_precond_apply_impl(c, r, z, s);
+    if (rc) return rc;
+    cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    int cur = S_RZ0;
+    dot_to(c, r, z, S + cur, s);
+    while (it < maxit) {
+      err = lor_launch_apply(c->m, c->T, c->Dq, p, q, s);
+      if (err != cudaSuccess) return fail(c, err, "pcg apply");
+      dot_to(c, p, q, S + S_PQ, s);
+      k_pcg_xr<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(n, S, cur, p, q, x, r, c->red);
+      k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, S + S_RR);
+      err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err != cudaSuccess) return fail(c, err, "pcg");
+      ++it;
+      rel = sqrt(hs[0]) / nb;
+      if (rel <= rtol) {
+        // confirm on the true residual b - A x
+        err = lor_launch_apply(c->m, c->T, c->Dq, x, q, s);
+        if (err == cudaSuccess) {
+          k_residual<<<g, kThreads, 0, s>>>(n, b, q, r);
+          err = dot_to(c, r, r, S + S_RR, s);
+        }
+        if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) return fail(c, err, "pcg");
+        rel = sqrt(hs[0]) / nb;
+        if (rel <= rtol) {
+          status = LOR_OK;
+          break;
+        }
+      }
+      rc = lor_precond_apply_impl(c, r, z, s);
+      if (rc) return rc;
+      const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
+      dot_to(c, r, z, S + nxt, s);
+      k_pcg_p<<<g, kThreads, 0, s>>>(n, S, nxt, cur, z, p);
+      cur = nxt;
+    }
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(c, err, "pcg");
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  if (status == LOR_ENOCONV) c->err = "pcg: no convergence within maxit";
+  return status;
+}

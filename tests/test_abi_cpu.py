@@ -1,0 +1,61 @@
+"""Host-side checks of the C-ABI boundary (no GPU needed): the library builds
+for sm_103a, loads, and exports every entry point that include/lor.h
+declares; the Python binding names the same set; and the product path
+refuses to run without CUDA tensors (no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "lor.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lor_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2210_12253_gb300.build import build
+    return build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ("lor_create", "lor_destroy", "lor_set_coefficient", "lor_build_pattern", "lor_assemble",
+                     "lor_apply", "lor_apply_backward", "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_entry_points() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2210_12253_gb300.lor import EXPORTED
+    assert sorted(EXPORTED) == declared_entry_points()
+
+
+def test_create_error_without_context_is_reported(libpath):
+    """lor_create rejects bad configurations before touching the GPU."""
+    from paper_2210_12253_gb300 import lor as B
+    L = B.load_library(libpath)
+    h = ctypes.c_void_p()
+    for p, ne in ((0, 2), (B.LOR_MAX_P + 1, 2), (3, 0)):
+        cfg = B.lor_config(p, ne, ne, ne)
+        rc = L.lor_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None)
+        assert rc == B.LOR_EINVAL
+        assert L.lor_last_error(None)
+    assert L.lor_create(None, None, None, None) == B.LOR_EINVAL
+
+
+def test_product_path_needs_cuda_tensors(libpath):
+    from paper_2210_12253_gb300 import LOR
+    with pytest.raises(TypeError):
+        LOR(2, 1, 1, 1, torch.zeros(8 * 3, dtype=torch.float64))
