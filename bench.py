@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the LOR hot path on one GB300 (or N replicas, one per GPU).
+
+One step = one pass of the hot path over the 16^3-element, p = 4 workload
+(274,625 DOFs, jittered mesh, lognormal kappa, FP64):
+  operator setup (D at the Gauss points) -> LOR assembly into CSR (FP64) ->
+  high-order apply -> Chebyshev-Jacobi preconditioner (degree 3, FP64, with
+  its diagonal) -> backward of the apply (gx and gkappa).
+value = DOFs processed per second over the timed steps (GDOF/s), summed over
+ranks.  The PCG time to 1e-8 (FP64 vs mixed precision) is measured on the
+32^3-element, p = 6 workload (7,189,057 DOFs) and reported under "pcg".
+
+Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
+every rank solves its own replica; no data-path collective).  With
+`--impl reference` it times the CPU oracle instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LOR assembly & HO apply GDOF/s (%HBM peak); PCG s to 1e-8, mixed vs FP64"
+UNIT = "GDOF/s"
+STEP_WORKLOAD = "c2_16x16x16_p4"
+PCG_WORKLOAD = "c3_32x32x32_p6"
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value, world):
+    """Max of a float over all ranks (identity for a single process)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, world):
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, max_seconds, world):
+    """Whole-job throughput: units processed by all ranks / max-over-ranks time."""
+    return sum_over_ranks(units_per_rank, world) / max_seconds
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                     stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def kernel_roofline(name, ms, work, hbm_peak, hbm_src):
+    flops, nbytes = work
+    out = {"ms": ms, "gflops_fp64": flops / (ms * 1e-3) / 1e9, "gbs": nbytes / (ms * 1e-3) / 1e9}
+    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS
+    out["frac_fp64"] = out["gflops_fp64"] / (FP64_PEAK_TFLOPS * 1e3)
+    out["frac_hbm"] = out["gbs"] / hbm_peak
+    return out
+
+
+def read_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary of `kernel`, or None
+    when the summary is missing or was taken on a different source file."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(prof):
+        return None
+    for fn in sorted(os.listdir(prof)):
+        if not fn.startswith(kernel) or not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(prof, fn)).read()
+        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        s = re.search(r"source_sha256:\s*([0-9a-f]+)\s+(\S+)", txt)
+        if not m or not s:
+            continue
+        src = os.path.join(ROOT, s.group(2))
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != s.group(1):
+            return None
+        return float(m.group(1))
+    return None
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.build import build
+    from paper_2210_12253_gb300.inputs import power_start_vector, workload
+    from paper_2210_12253_gb300.lor import launch_count
+    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
+
+    if rank == 0:
+        build()
+    barrier(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hbm_peak, hbm_src = hbm_peak_gbs()
+
+    prob = workload(STEP_WORKLOAD)
+    p = prob.p
+    op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    kappa_h = torch.tensor(prob.kappa.reshape(-1)).pin_memory()
+    kappa = kappa_h.to(dev)
+    rng = np.random.default_rng(100 + rank)
+    x_h = torch.tensor(rng.standard_normal(op.ndof)).pin_memory()
+    gy_h = torch.tensor(rng.standard_normal(op.ndof)).pin_memory()
+    r_h = torch.tensor(prob.rhs).pin_memory()
+    x, gy, r = x_h.to(dev), gy_h.to(dev), r_h.to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    gx = torch.empty_like(x)
+    gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # one-time setup: pattern (A2, once per mesh) and the smoother's lambda_max
+    op.set_coefficient(kappa, check=True)
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float64)
+    lam = op.precond_setup("cheb", torch.float64, degree=3, power_iters=20,
+                           v0=torch.tensor(power_start_vector(op.ndof), device=dev))
+    names = ["setup", "assemble", "apply", "precond", "backward"]
+
+    def step(ev):
+        ev[0].record()
+        op.set_coefficient(kappa)
+        ev[1].record()
+        op.assemble_internal(torch.float64)
+        ev[2].record()
+        op.apply(x, out=y)
+        ev[3].record()
+        op.precond_setup("cheb", torch.float64, degree=3, lambda_max=lam)
+        op.precond_apply(r, out=z)
+        ev[4].record()
+        op.apply_backward(x, gy, gx_out=gx, gk_out=gk)
+        ev[5].record()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps (outside the step's events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    launches = launch_count() - launches0
+    per_kernel = {n: [] for n in names}
+    step_ms = []
+    for ev in evs:
+        for i, n in enumerate(names):
+            per_kernel[n].append(ev[i].elapsed_time(ev[i + 1]))
+        step_ms.append(ev[0].elapsed_time(ev[5]))
+    dev_s = sum(step_ms) / 1e3
+    max_s = max_over_ranks(dev_s, world)
+    value = aggregate_rate(op.ndof * args.steps, max_s, world) / 1e9
+
+    # end to end through the public API: pinned host inputs in, results out
+    e2e_steps = max(3, args.steps // 4)
+    hy, hz, hgx = (torch.empty(op.ndof, dtype=torch.float64).pin_memory() for _ in range(3))
+    hgk = torch.empty(op.nqpt, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(e2e_steps):
+        kappa.copy_(kappa_h, non_blocking=True)
+        x.copy_(x_h, non_blocking=True)
+        gy.copy_(gy_h, non_blocking=True)
+        r.copy_(r_h, non_blocking=True)
+        step([torch.cuda.Event(enable_timing=True) for _ in range(6)])
+        hy.copy_(y, non_blocking=True)
+        hz.copy_(z, non_blocking=True)
+        hgx.copy_(gx, non_blocking=True)
+        hgk.copy_(gk, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    e2e_value = aggregate_rate(op.ndof * e2e_steps, e2e_s, world) / 1e9
+    h2d = 8 * (op.nqpt + 3 * op.ndof)
+    d2h = 8 * (3 * op.ndof + op.nqpt)
+
+    kernels = {}
+    for n in names:
+        ms = statistics.mean(per_kernel[n])
+        work = kernel_work(n, p, op.ndof, op.nel, op.nnz, vbytes=8, degree=3)
+        kernels[n] = kernel_roofline(n, ms, work, hbm_peak, hbm_src)
+        kernels[n]["gdofs"] = op.ndof / (ms * 1e-3) / 1e9
+    dominant = max(names, key=lambda n: kernels[n]["ms"])
+    dk = kernels[dominant]
+    traffic = read_traffic("k_" + dominant)
+    roofline = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops_fp64"] / 1e3,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": dk["gflops_fp64"] / 1e3 / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64; no FP64 entry in "
+                               "MEASURED_PEAKS.json)",
+                "traffic": traffic,
+                "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                        "frac": dk["frac_hbm"]}}
+    clk = clocks.stop()
+
+    pcg = None
+    if not args.no_pcg:
+        pcg = run_pcg(args, dev, rank)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": STEP_WORKLOAD + ": unit cube 16^3 hexes, p=4, 274,625 DOFs, +-10% h jitter (seed 1),"
+                                  " kappa lognormal(0,1) at 6^3 Gauss points/element",
+                      "step": "setup(D) + LOR assembly(f64, CSR) + HO apply + Chebyshev-Jacobi deg 3 (f64) + "
+                              "apply backward (gx, gkappa)",
+                      "ndof": op.ndof, "nnz": op.nnz, "elements": op.nel, "p": p,
+                      "l2": "flushed between steps (512 MB write, outside the step events)",
+                      "parallelism": "replicas x%d (one independent problem per GPU)" % world,
+                      "wall_s": wall},
+           "kernels": kernels, "roofline": roofline,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "steps": e2e_steps},
+           "gpu_launches": int(launches), "clocks": clk, "pcg": pcg}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    op.close()
+    return out
+
+
+def run_pcg(args, dev, rank):
+    """PCG to 1e-8 on the 32^3, p = 6 workload: FP64 vs mixed precision."""
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import power_start_vector, workload
+
+    prob = workload(PCG_WORKLOAD)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    b = torch.tensor(prob.rhs, device=dev)
+    v0 = torch.tensor(power_start_vector(op.ndof), device=dev)
+    res = {"workload": PCG_WORKLOAD + ": 32^3 hexes, p=6, 7,189,057 DOFs, +-10% h jitter (seed 2), kappa "
+                                      "lognormal(0,1); Chebyshev-Jacobi deg 3 on [lmax/30, 1.1 lmax], rtol 1e-8 "
+                                      "confirmed on the true FP64 residual"}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for label, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        ev[0].record()
+        op.set_coefficient(torch.tensor(prob.kappa.reshape(-1), device=dev))
+        op.build_pattern_internal()
+        ev[1].record()
+        op.assemble_internal(dt)
+        lam = op.precond_setup("cheb", dt, degree=3, power_iters=20, v0=v0)
+        ev[2].record()
+        torch.cuda.synchronize()
+        op.pcg_solve(b, 1e-8, 3, raise_on_noconv=False)  # warm-up of the solve kernels
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        u, it, rel = op.pcg_solve(b, 1e-8, 20000)
+        e1.record()
+        torch.cuda.synchronize()
+        solve_s = e0.elapsed_time(e1) / 1e3
+        res[label] = {"solve_s": solve_s, "wall_s": time.perf_counter() - t0, "iterations": it,
+                      "final_rel_residual": rel, "lambda_max": lam,
+                      "setup_s": ev[0].elapsed_time(ev[2]) / 1e3,
+                      "s_per_iteration": solve_s / max(it, 1)}
+    res["mixed_speedup"] = res["fp64"]["solve_s"] / res["mixed"]["solve_s"]
+    op.close()
+    return res
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+SAMPLE = "8x8x8 elements, p=4 (35,937 DOFs): the 16^3 p=4 workload's recipe on an 8^3 sub-box (seed 1)"
+
+
+def oracle_step(sample):
+    """One pass of the oracle over the sample: LOR assembly (which also forms
+    the geometry), high-order apply, Chebyshev-Jacobi (degree 3) and the
+    backward of the apply.  Returns DOFs processed."""
+    import oracle
+    prob, mesh, x, gy, lam = sample
+    p, q = prob.p, prob.q
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
+    oracle.ho_apply(mesh, p, q, prob.kappa, x)
+    oracle.chebyshev(*csr, prob.rhs, 3, lam / 30, 1.1 * lam)
+    oracle.ho_apply_backward(mesh, p, q, prob.kappa, x, gy)
+    return prob.ndof
+
+
+def make_sample():
+    import numpy as np
+
+    import oracle
+    from paper_2210_12253_gb300.inputs import make_problem
+    prob = make_problem("sample", 8, 8, 8, 4, seed=1, kappa="lognormal", rhs="normal")
+    mesh = oracle.Mesh(8, 8, 8, prob.vertices)
+    rng = np.random.default_rng(100)
+    x, gy = rng.standard_normal(prob.ndof), rng.standard_normal(prob.ndof)
+    csr = oracle.lor_assemble(mesh, prob.p, prob.q, prob.kappa, True)
+    lam = oracle.power_lambda_max(*csr, np.ones(prob.ndof), 20)
+    return prob, mesh, x, gy, lam
+
+
+def cpu_baseline(seconds):
+    sample = make_sample()
+    t0 = time.perf_counter()
+    dofs = 0
+    n = 0
+    while True:
+        dofs += oracle_step(sample)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": dofs / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": SAMPLE + "; %d oracle steps in %.1f s, single-threaded FP64 C" % (n, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sample = make_sample()
+    for _ in range(args.warmup):
+        oracle_step(sample)
+    t0 = time.perf_counter()
+    dofs = 0
+    for _ in range(args.steps):
+        dofs += oracle_step(sample)
+    dt = time.perf_counter() - t0
+    value = dofs / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": STEP_WORKLOAD + " recipe, bounded sample: " + SAMPLE,
+                       "step": "oracle: LOR assembly + HO apply + Chebyshev-Jacobi deg 3 + apply backward"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["liblor", "reference"], default="liblor")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_info()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

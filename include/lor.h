@@ -95,6 +95,10 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
  * work of the context first.  NULL is accepted. */
 int lor_destroy(lor_ctx* ctx);
 
+/* Number of CUDA kernels liblor has launched in this process so far (all
+ * contexts, all threads).  Host-only; for instrumentation. */
+int lor_launch_count(int64_t* count);
+
 /* Sizes: DOFs N = nx ny nz, LOR nonzeros (3nx-2)(3ny-2)(3nz-2), elements,
  * quadrature points nel q^3.  Any pointer may be NULL. */
 int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int64_t* nqpt);

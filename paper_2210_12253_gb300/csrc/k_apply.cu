@@ -250,7 +250,7 @@ __global__ void k_init_output(LorMesh m, const double* __restrict__ x, double* _
 
 cudaError_t init_output(const LorMesh& m, const double* x, double* y, cudaStream_t s) {
   const int64_t blocks = (m.ndof + 255) / 256;
-  k_init_output<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(m, x, y);
+  k_init_output<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(m, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -266,7 +266,7 @@ cudaError_t apply_p(const LorMesh& m, const LorTables& T, const double* Dq, cons
     if (err != cudaSuccess) return err;
     configured |= 1u << dev;
   }
-  k_apply<P><<<(unsigned)m.nel, kApplyThreads, bytes, s>>>(m, T, Dq, x, y);
+  k_apply<P><<<(unsigned)m.nel, kApplyThreads, bytes, s>>>(m, T, Dq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -283,7 +283,7 @@ cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, c
     if (err != cudaSuccess) return err;
     configured |= 1u << dev;
   }
-  k_apply_backward<P><<<(unsigned)m.nel, kApplyThreads, bytes, s>>>(m, T, Dq, kappa, x, gy, gx, gk);
+  k_apply_backward<P><<<(unsigned)m.nel, kApplyThreads, bytes, s>>>(m, T, Dq, kappa, x, gy, gx, gk); lor_count_launch();
   return cudaGetLastError();
 }
 

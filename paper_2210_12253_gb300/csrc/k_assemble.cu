@@ -162,11 +162,11 @@ cudaError_t launch(const LorMesh& m, const LorTables& T, const double* kappa, VT
   if (err != cudaSuccess) return err;
   {
     const int64_t blocks = (m.ndof + 255) / 256;
-    k_essential_diagonal<VT><<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(m, vals);
+    k_essential_diagonal<VT><<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(m, vals); lor_count_launch();
   }
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: k_assemble<P, VT><<<(unsigned)m.nel, kAsmThreads<P>, 0, s>>>(m, T, kappa, vals); break;
+  case P: k_assemble<P, VT><<<(unsigned)m.nel, kAsmThreads<P>, 0, s>>>(m, T, kappa, vals); lor_count_launch(); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

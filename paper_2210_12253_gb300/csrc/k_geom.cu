@@ -209,7 +209,7 @@ cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double*
   const int g = grid_for(m.nel);
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: k_setup<P><<<g, 128, 0, s>>>(m, T, kappa_in, kappa_copy, Dq, d_status); break;
+  case P: k_setup<P><<<g, 128, 0, s>>>(m, T, kappa_in, kappa_copy, Dq, d_status); lor_count_launch(); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE
@@ -220,10 +220,10 @@ cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double*
 
 cudaError_t lor_launch_geometry_check(const LorMesh& m, const LorTables& T, int* d_status, cudaStream_t s) {
   const int g = grid_for(m.nel);
-  k_geometry_check<<<g, 128, 0, s>>>(m, T, T.q, 0, d_status);
+  k_geometry_check<<<g, 128, 0, s>>>(m, T, T.q, 0, d_status); lor_count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  k_geometry_check<<<g, 128, 0, s>>>(m, T, 2 * T.p, 1, d_status);
+  k_geometry_check<<<g, 128, 0, s>>>(m, T, 2 * T.p, 1, d_status); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -234,7 +234,7 @@ cudaError_t lor_launch_load_vector(const LorMesh& m, const LorTables& T, const d
   const int g = grid_for(m.nel);
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: k_load_vector<P><<<g, 128, 0, s>>>(m, T, f, b); break;
+  case P: k_load_vector<P><<<g, 128, 0, s>>>(m, T, f, b); lor_count_launch(); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

@@ -40,6 +40,6 @@ __global__ void __launch_bounds__(256) k_pattern(int64_t nx, int64_t ny, int64_t
 cudaError_t lor_launch_pattern(const LorMesh& m, int64_t* rowptr, int32_t* colidx, cudaStream_t s) {
   const int64_t blocks = (m.ndof + 255) / 256;
   const int g = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-  k_pattern<<<g, 256, 0, s>>>(m.nx, m.ny, m.nz, rowptr, colidx);
+  k_pattern<<<g, 256, 0, s>>>(m.nx, m.ny, m.nz, rowptr, colidx); lor_count_launch();
   return cudaGetLastError();
 }

@@ -182,7 +182,7 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
   const int64_t n = c->m.ndof;
   const int g = grid_rows(n);
   if (c->pc_kind == LOR_PRECOND_JACOBI) {
-    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z);
+    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
     return cudaGetLastError();
   }
   VT* zA = (VT*)c->pc_work;
@@ -191,7 +191,7 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
   const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
   const double sigma = theta / delta;
   const int k = c->pc_degree;
-  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr);
+  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr); lor_count_launch();
   double rho = 1.0 / sigma;
   VT* zin = zA;
   VT* zout = zB;
@@ -199,7 +199,7 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
     k_cheb_step<VT><<<g, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
-                                          j == k - 1 ? z : nullptr);
+                                          j == k - 1 ? z : nullptr); lor_count_launch();
     rho = rho_new;
     VT* t = zin;
     zin = zout;
@@ -209,8 +209,8 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
 }
 
 cudaError_t dot_to(lor_ctx* c, const double* a, const double* b, double* out, cudaStream_t s) {
-  k_dot_partial<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(c->m.ndof, a, b, c->red);
-  k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, out);
+  k_dot_partial<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(c->m.ndof, a, b, c->red); lor_count_launch();
+  k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, out); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -223,21 +223,23 @@ int fail(lor_ctx* c, cudaError_t err, const char* what) {
 
 cudaError_t lor_launch_diag_inv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
                                 int dtype, void* dinv, cudaStream_t s) {
-  if (dtype == LOR_F64)
+  if (dtype == LOR_F64) {
     k_diag_inv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals,
-                                                             (double*)dinv);
-  else
+                                                             (double*)dinv); lor_count_launch();
+  } else {
     k_diag_inv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals,
-                                                            (float*)dinv);
+                                                            (float*)dinv); lor_count_launch();
+  }
   return cudaGetLastError();
 }
 
 cudaError_t lor_launch_spmv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
                             int dtype, const double* x, double* y, cudaStream_t s) {
-  if (dtype == LOR_F64)
-    k_spmv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y);
-  else
-    k_spmv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y);
+  if (dtype == LOR_F64) {
+    k_spmv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y); lor_count_launch();
+  } else {
+    k_spmv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y); lor_count_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -261,17 +263,18 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
   if (v0) {
     err = cudaMemcpyAsync(v, v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   } else {
-    k_fill<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0);
+    k_fill<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0); lor_count_launch();
     err = cudaGetLastError();
   }
   if (err != cudaSuccess) return fail(c, err, "power iteration");
   double* S = c->red + LOR_RED_BLOCKS;
   double lam = 0.0;
   for (int it = 0; it < iters; ++it) {
-    if (dtype == LOR_F64)
-      k_dinv_spmv<double><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w);
-    else
-      k_dinv_spmv<float><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w);
+    if (dtype == LOR_F64) {
+      k_dinv_spmv<double><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w); lor_count_launch();
+    } else {
+      k_dinv_spmv<float><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w); lor_count_launch();
+    }
     dot_to(c, w, w, S + 0, s);
     dot_to(c, v, v, S + 1, s);
     err = cudaMemcpyAsync(c->h_scalar, S, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -287,7 +290,7 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
     double* tmp = v;
     v = w;
     w = tmp;
-    k_scale<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0 / nw);
+    k_scale<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0 / nw); lor_count_launch();
     err = cudaGetLastError();
     if (err != cudaSuccess) return fail(c, err, "power iteration");
   }
@@ -327,8 +330,8 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
       err = lor_launch_apply(c->m, c->T, c->Dq, p, q, s);
       if (err != cudaSuccess) return fail(c, err, "pcg apply");
       dot_to(c, p, q, S + S_PQ, s);
-      k_pcg_xr<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(n, S, cur, p, q, x, r, c->red);
-      k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, S + S_RR);
+      k_pcg_xr<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(n, S, cur, p, q, x, r, c->red); lor_count_launch();
+      k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, S + S_RR); lor_count_launch();
       err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (err == cudaSuccess) err = cudaStreamSynchronize(s);
       if (err != cudaSuccess) return fail(c, err, "pcg");
@@ -338,7 +341,7 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
         // confirm on the true residual b - A x
         err = lor_launch_apply(c->m, c->T, c->Dq, x, q, s);
         if (err == cudaSuccess) {
-          k_residual<<<g, kThreads, 0, s>>>(n, b, q, r);
+          k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
           err = dot_to(c, r, r, S + S_RR, s);
         }
         if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -354,7 +357,7 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
       if (rc) return rc;
       const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
       dot_to(c, r, z, S + nxt, s);
-      k_pcg_p<<<g, kThreads, 0, s>>>(n, S, nxt, cur, z, p);
+      k_pcg_p<<<g, kThreads, 0, s>>>(n, S, nxt, cur, z, p); lor_count_launch();
       cur = nxt;
     }
     err = cudaGetLastError();

@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -23,6 +24,7 @@
 namespace {
 
 thread_local std::string g_create_error;
+std::atomic<long long> g_launches{0};
 
 typedef long double ld;
 
@@ -199,6 +201,8 @@ int read_status(lor_ctx* c, cudaStream_t s, int* flags) {
 
 }  // namespace
 
+void lor_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 extern "C" {
 
 const char* lor_last_error(const lor_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -265,6 +269,12 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
     return rc;
   }
   *out = c;
+  return LOR_OK;
+}
+
+int lor_launch_count(int64_t* count) {
+  if (!count) return LOR_EINVAL;
+  *count = g_launches.load(std::memory_order_relaxed);
   return LOR_OK;
 }
 

@@ -65,6 +65,9 @@ struct lor_ctx {
   double* h_scalar = nullptr;  // pinned host scalars
 };
 
+// Process-wide count of kernels launched by liblor (reported by lor_launch_count).
+void lor_count_launch();
+
 // Device error flags (bit mask in ctx->d_status[0]).
 #define LOR_FLAG_BAD_KAPPA 1
 #define LOR_FLAG_BAD_GEOM 2

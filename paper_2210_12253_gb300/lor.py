@@ -20,7 +20,7 @@ LOR_MAX_P = 10
 EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
-    "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve",
+    "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
 ]
 
 
@@ -75,10 +75,19 @@ def load_library(path=LIB):
     L.lor_precond_setup.argtypes = [vp, i, i, i, d, d, d, i, vp, C.POINTER(d), vp]
     L.lor_precond_apply.restype = i
     L.lor_precond_apply.argtypes = [vp, vp, vp, vp]
+    L.lor_launch_count.restype = i
+    L.lor_launch_count.argtypes = [C.POINTER(i64)]
     L.lor_pcg_solve.restype = i
     L.lor_pcg_solve.argtypes = [vp, vp, vp, d, i, C.POINTER(i), C.POINTER(d), vp]
     _lib = L
     return L
+
+
+def launch_count():
+    """Kernels liblor has launched in this process."""
+    n = C.c_int64(0)
+    load_library().lor_launch_count(C.byref(n))
+    return n.value
 
 
 def _stream():
@@ -203,13 +212,16 @@ class LOR:
         self._call("lor_apply", _ptr(x), _ptr(y))
         return y
 
-    def apply_backward(self, x, gy, want_gx=True, want_gkappa=True):
+    def apply_backward(self, x, gy, want_gx=True, want_gkappa=True, gx_out=None, gk_out=None):
         """(A_p gy, d(gy^T A_p x)/d kappa)."""
         _dev(gy, torch.float64, self.ndof, "gy")
         if want_gkappa:
             _dev(x, torch.float64, self.ndof, "x")
-        gx = self._new(self.ndof) if want_gx else None
-        gk = self._new(self.nqpt) if want_gkappa else None
+        gx = gk = None
+        if want_gx:
+            gx = self._new(self.ndof) if gx_out is None else _dev(gx_out, torch.float64, self.ndof, "gx_out")
+        if want_gkappa:
+            gk = self._new(self.nqpt) if gk_out is None else _dev(gk_out, torch.float64, self.nqpt, "gk_out")
         self._call("lor_apply_backward", _ptr(x if want_gkappa else None), _ptr(gy), _ptr(gx), _ptr(gk))
         return gx, gk
 
@@ -240,9 +252,9 @@ class LOR:
                    float(lambda_max) if lambda_max else 0.0, int(power_iters), _ptr(v0), C.byref(lam))
         return lam.value
 
-    def precond_apply(self, r):
+    def precond_apply(self, r, out=None):
         _dev(r, torch.float64, self.ndof, "r")
-        z = self._new(self.ndof)
+        z = self._new(self.ndof) if out is None else _dev(out, torch.float64, self.ndof, "out")
         self._call("lor_precond_apply", _ptr(r), _ptr(z))
         return z
 

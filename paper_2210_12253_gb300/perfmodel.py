@@ -1,0 +1,81 @@
+"""Algorithmic work per launch of each liblor kernel (roofline numerators).
+
+Flops are FP64 (an FMA counts 2), counted from the formulas each kernel
+evaluates, not from what the hardware issues; bytes are the minimum HBM
+traffic (every input read once, every output written once).  N = DOFs,
+E = elements, nq = E (p+2)^3 Gauss points, S = E p^3 LOR sub-hexes.
+
+Peaks: FP64 has no entry in MEASURED_PEAKS.json, so the FP64 peak is derived
+from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz =
+1.2586 TFLOP/s (an own DFMA loop measured 1.19 TFLOP/s, 1.90 DFMA/clk/SM).
+The HBM peak is MEASURED_PEAKS.json's copy bandwidth.
+"""
+import json
+import os
+
+SMS, DFMA_PER_CLK_SM, MAX_SM_GHZ = 152, 2, 2.07
+FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * MAX_SM_GHZ / 1e3  # 1.2586
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak_gbs():
+    """(GB/s, source) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def sumfact_fma(p):
+    """FMAs of one forward pass grad_ref(u) at the Gauss points of an element:
+    x-stage 2 q n^3, y-stage 3 q^2 n^2, z-stage 3 q^3 n (n = p+1, q = p+2)."""
+    q, n = p + 2, p + 1
+    return 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
+
+
+def setup_flops_per_point():
+    """Adjugate (3 cross products, 27), det (5), weight (2), kappa w / det (2),
+    six scaled dot products (36)."""
+    return 72
+
+
+def assemble_flops_per_subhex():
+    """2x2x2 Gauss on one sub-hex, per point: Jacobian columns (81), adjugate
+    (27), det (5), 1/det (1), G (42), G grad(phi_i) for 8 i (120), the 36
+    upper-triangle entries (216): 492 flops x 8 points."""
+    return 8 * 492
+
+
+def apply_flops_per_element(p):
+    """Forward and transpose sum factorisation (2 flops per FMA each) plus the
+    symmetric 3x3 D product (15 flops) per Gauss point."""
+    return 4 * sumfact_fma(p) + 15 * (p + 2) ** 3
+
+
+def backward_flops_per_element(p):
+    """Two forward passes (x and gy), one transpose pass, and per point the
+    D product (15), the gkappa contraction x^T (D gy) / kappa (21)."""
+    return 6 * sumfact_fma(p) + 36 * (p + 2) ** 3
+
+
+def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
+    """(flops, bytes) of one launch of `kind` on the given sizes."""
+    q = p + 2
+    nq = nel * q ** 3
+    nsub = nel * p ** 3
+    if kind == "setup":
+        return setup_flops_per_point() * nq, 64 * nq  # kappa in, D (48) + kappa copy out
+    if kind == "assemble":
+        return assemble_flops_per_subhex() * nsub, vbytes * nnz + 8 * nq
+    if kind == "apply":
+        return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
+    if kind == "backward":
+        return backward_flops_per_element(p) * nel, 24 * ndof + 64 * nq
+    if kind == "precond":
+        # degree-1 SpMV passes over the matrix (values + int32 columns + row
+        # pointers) and ~6 vector streams per step
+        spmv = nnz * (vbytes + 4) + 8 * (ndof + 1)
+        return 2 * nnz * (degree - 1), (degree - 1) * (spmv + 6 * vbytes * ndof) + 3 * 8 * ndof
+    raise KeyError(kind)
