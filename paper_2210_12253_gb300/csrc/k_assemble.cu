@@ -20,131 +20,205 @@
 
 namespace {
 
-// Trilinear basis on the sub-hex reference cube at the 2x2x2 Gauss points
-// tau = +-1/sqrt(3): l_0(tau) = (1 - tau)/2, l_1(tau) = (1 + tau)/2.
-constexpr double kLa = 0.78867513459481288225;  // (1 + 1/sqrt(3)) / 2: l_i at the Gauss point on its own side
-constexpr double kLb = 0.21132486540518711775;  // (1 - 1/sqrt(3)) / 2
-__device__ __forceinline__ constexpr double lval(int i, int g) { return i == g ? kLa : kLb; }
-__device__ __forceinline__ constexpr double dval(int i) { return i ? 0.5 : -0.5; }
-// d phi_i / d tau_d at Gauss point g (vertex i = i0 + 2 i1 + 4 i2, g likewise).
-__device__ __forceinline__ constexpr double dphi(int g, int i, int d) {
-  return d == 0 ? dval(i & 1) * lval((i >> 1) & 1, (g >> 1) & 1) * lval(i >> 2, g >> 2)
-       : d == 1 ? lval(i & 1, g & 1) * dval((i >> 1) & 1) * lval(i >> 2, g >> 2)
-                : lval(i & 1, g & 1) * lval((i >> 1) & 1, (g >> 1) & 1) * dval(i >> 2);
+// ---------------------------------------------------------------------------
+// Sub-hex stiffness block in the modal basis.
+//
+// On the sub-hex reference cube tau in [-1,1]^3 the trilinear nodal basis is
+// phi_i = prod_k l_{i_k}(tau_k), l_0 = (1 - t)/2, l_1 = (1 + t)/2.  In the
+// modal basis psi_m = prod_k psi_{m_k}(tau_k), psi_0 = 1, psi_1 = t, one has
+// phi = (1/8) H psi with H_im = prod_k s(i_k)^{m_k}, s(0) = -1, s(1) = +1.
+// At the 2x2x2 Gauss points tau_k = eps_k / sqrt(3), eps_k = +-1,
+//   d_a psi_m = [m_a = 1] prod_{k != a} (eps_k / sqrt(3))^{m_k},
+// so the modal stiffness
+//   Kt_mn = sum_g sum_ab G^ab(g) d_a psi_m(g) d_b psi_n(g)
+//         = sum_{a in m} sum_{b in n} 3^{-(|m|+|n|-2)/2} Ghat^ab(w(m,n,a,b)),
+// where Ghat^ab is the Walsh-Hadamard transform of G^ab over the 8 points,
+//   Ghat(w) = sum_g G(g) prod_k eps_k^{w_k},  w = (m without a) xor (n without b).
+// The nodal block is K = H Kt H^T / 64, applied axis by axis.  FP64 work per
+// sub-hex: 6 x 24 additions (transforms), 84 products (Kt), about 200
+// additions (H . H^T on the 36 symmetric entries), instead of 8 x 180
+// operations for the nodal formula at each Gauss point.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+__device__ __forceinline__ constexpr int pair_index(int a, int b) {  // (00,01,02,11,12,22)
+  return a <= b ? (a == 0 ? b : a == 1 ? 2 + b : 5) : (b == 0 ? a : b == 1 ? 2 + a : 5);
+}
+__device__ __forceinline__ constexpr int walsh_index(int m, int n, int a, int b) {
+  return (m & ~(1 << a)) ^ (n & ~(1 << b));
+}
+__device__ __forceinline__ constexpr double inv_sqrt3_pow(int p) {
+  return p == 0 ? 1.0
+       : p == 1 ? 0.57735026918962576451
+       : p == 2 ? 0.33333333333333333333
+       : p == 3 ? 0.19245008972987525484
+                : 0.11111111111111111111;
+}
+__device__ __forceinline__ constexpr int sym(int i, int j) { return i <= j ? i * 8 + j : j * 8 + i; }
+
+template <typename VT>
+__device__ __forceinline__ void walsh8(VT* v) {  // v(w) = sum_g v(g) prod_k eps_k^{w_k}
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      if (!((g >> k) & 1)) {
+        const VT lo = v[g], hi = v[g | (1 << k)];
+        v[g] = lo + hi;
+        v[g | (1 << k)] = hi - lo;
+      }
 }
 
-__device__ __forceinline__ int upper(int i, int j) {  // packed index of (min, max) in an 8x8 upper triangle
-  const int a = i < j ? i : j, b = i < j ? j : i;
-  return a * 8 - (a * (a - 1)) / 2 + (b - a);
+// K <- (H_k (x) H_k) K for axis k, on a symmetric 8x8 matrix stored at
+// K[sym(i,j)]; H_k maps (m_k = 0, m_k = 1) to (i_k = 0: a - b, i_k = 1: a + b).
+template <typename VT, int k>
+__device__ __forceinline__ void hadamard_axis(VT* K) {
+  VT out[64];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = i; j < 8; ++j) {
+      const int i0 = i & ~(1 << k), i1 = i | (1 << k), j0 = j & ~(1 << k), j1 = j | (1 << k);
+      const VT a = K[sym(i0, j0)], b = K[sym(i0, j1)], c = K[sym(i1, j0)], d = K[sym(i1, j1)];
+      const VT u = ((i >> k) & 1) ? a + c : a - c;
+      const VT v = ((i >> k) & 1) ? b + d : b - d;
+      out[sym(i, j)] = ((j >> k) & 1) ? u + v : u - v;
+    }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = i; j < 8; ++j) K[sym(i, j)] = out[sym(i, j)];
 }
 
 template <int P>
-constexpr int kAsmThreads = ((P * P * P + 31) / 32) * 32 < 256 ? ((P * P * P + 31) / 32) * 32 : 256;
+constexpr int kElemsPerCta = P * P * P >= 64 ? 1 : 64 / (P * P * P);
+template <int P>
+constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
+                                            : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
 
 template <typename VT>
-__device__ __forceinline__ void atomic_add(VT* p, double v);
-template <>
-__device__ __forceinline__ void atomic_add<double>(double* p, double v) { atomicAdd(p, v); }
-template <>
-__device__ __forceinline__ void atomic_add<float>(float* p, double v) { atomicAdd(p, (float)v); }
+__device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
 
 template <int P, typename VT>
 __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTables T,
-                                                                          const double* __restrict__ kappa,
-                                                                          VT* __restrict__ vals) {
-  constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P;
-  __shared__ double Ehalf[36];
-  const int64_t e = blockIdx.x;
-  const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
-  for (int idx = threadIdx.x; idx < 36; idx += blockDim.x) {
-    const int d = idx / 12, pair = (idx / 3) % 4, comp = idx % 3;
-    const int o0 = pair & 1, o1 = pair >> 1;
-    const int lo = d == 0 ? 2 * o0 + 4 * o1 : d == 1 ? o0 + 4 * o1 : o0 + 2 * o1;
-    const int hi = lo + (1 << d);
-    auto corner = [&](int c) {
-      const int64_t va = ex + (c & 1), vb = ey + ((c >> 1) & 1), vc = ez + ((c >> 2) & 1);
-      return m.verts[3 * (va + (int64_t)(m.nex + 1) * (vb + (int64_t)(m.ney + 1) * vc)) + comp];
-    };
-    Ehalf[idx] = 0.5 * (corner(hi) - corner(lo));
-  }
+                                                             const double* __restrict__ kappa,
+                                                             VT* __restrict__ vals) {
+  constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kElemsPerCta<P>;
+  constexpr int TAB = 3 * L * L * 3;  // three Jacobian-column tables per element
+  __shared__ double Ehalf[EPB][36];
+  __shared__ double tab[EPB][TAB];
+  __shared__ double st[L];
+  if (threadIdx.x < L) st[threadIdx.x] = T.sub_t[threadIdx.x];
   __syncthreads();
-  for (int s = threadIdx.x; s < P3; s += blockDim.x) {
-  const int a = s % P, b = (s / P) % P, c = s / (P * P);
+  const int64_t e_first = (int64_t)blockIdx.x * EPB;
+  // Jacobian columns of each element at the sub-hex Gauss coordinates.
+  for (int le = 0; le < EPB; ++le) {
+    const int64_t e = e_first + le;
+    if (e < m.nel) lor_jacobian_columns(m, e, st, L, Ehalf[le], tab[le]);
+  }
+  const int nwork = EPB * P3;
+  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+    const int le = w / P3, s = w % P3;
+    const int64_t e = e_first + le;
+    if (e >= m.nel) break;
+    const int a = s % P, b = (s / P) % P, c = s / (P * P);
 
-  // kappa_s: Gauss-weight average over the high-order points in the sub-hex.
-  double ks = 0.0;
-  for (int g2 = T.bin_first[c]; g2 < T.bin_first[c] + T.bin_count[c]; ++g2)
-    for (int g1 = T.bin_first[b]; g1 < T.bin_first[b] + T.bin_count[b]; ++g1)
-      for (int g0 = T.bin_first[a]; g0 < T.bin_first[a] + T.bin_count[a]; ++g0)
-        ks += T.bin_w[g0] * T.bin_w[g1] * T.bin_w[g2] * kappa[e * Q3 + g0 + Q * (g1 + Q * g2)];
+    // kappa_s: Gauss-weight average over the high-order points in the sub-hex
+    double ks = 0.0;
+    for (int g2 = T.bin_first[c]; g2 < T.bin_first[c] + T.bin_count[c]; ++g2)
+      for (int g1 = T.bin_first[b]; g1 < T.bin_first[b] + T.bin_count[b]; ++g1) {
+        const double w12 = T.bin_w[g1] * T.bin_w[g2];
+        for (int g0 = T.bin_first[a]; g0 < T.bin_first[a] + T.bin_count[a]; ++g0)
+          ks += (w12 * T.bin_w[g0]) * kappa[e * Q3 + g0 + Q * (g1 + Q * g2)];
+      }
 
-  const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
-  // G_sub^{ab} = (r_a r_b r_c)/(r_a r_b) (adj_a . adj_b) / det_e
-  const double F00 = rb * rc / ra, F11 = ra * rc / rb, F22 = ra * rb / rc;
-  const double F01 = rc, F02 = rb, F12 = ra;
-  double K[36];
+    // G_sub^{ab}(g) = F_ab (A_a . A_b) / det_e with A the adjugate rows of the
+    // element Jacobian, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64 (the 1/64
+    // of the modal-to-nodal transform folded in).
+    const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
+    const double k64 = ks * (1.0 / 64.0);
+    const double F00 = k64 * rb * rc / ra, F01 = k64 * rc, F02 = k64 * rb;
+    const double F11 = k64 * ra * rc / rb, F12 = k64 * ra, F22 = k64 * ra * rb / rc;
+    VT G[6][8];
+    const double* t0 = tab[le];
+    const double* t1 = tab[le] + L * L * 3;
+    const double* t2 = tab[le] + 2 * L * L * 3;
 #pragma unroll
-  for (int i = 0; i < 36; ++i) K[i] = 0.0;
-
+    for (int g = 0; g < 8; ++g) {
+      const int u0 = 2 * a + (g & 1), u1 = 2 * b + ((g >> 1) & 1), u2 = 2 * c + (g >> 2);
+      const double* c0 = t0 + 3 * (u1 + L * u2);
+      const double* c1 = t1 + 3 * (u0 + L * u2);
+      const double* c2 = t2 + 3 * (u0 + L * u1);
+      double A[3][3];
+      lor_cross(c1, c2, A[0]);
+      lor_cross(c2, c0, A[1]);
+      lor_cross(c0, c1, A[2]);
+      const double det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
+      const double r = lor_rcp(det);
+      if constexpr (sizeof(VT) == sizeof(double)) {
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    const int t0 = 2 * a + (g & 1), t1 = 2 * b + ((g >> 1) & 1), t2 = 2 * c + (g >> 2);
-    const double u0 = T.sub_l0[t0], u1 = T.sub_l1[t0];
-    const double v0 = T.sub_l0[t1], v1 = T.sub_l1[t1];
-    const double w0 = T.sub_l0[t2], w1 = T.sub_l1[t2];
-    double col[3][3];
+        for (int ab = 0; ab < 6; ++ab) {
+          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
+          const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
+          G[ab][g] = (Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]);
+        }
+      } else {
+        float Af[3][3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      col[0][q] = w0 * (v0 * Ehalf[0 + q] + v1 * Ehalf[3 + q]) + w1 * (v0 * Ehalf[6 + q] + v1 * Ehalf[9 + q]);
-      col[1][q] = w0 * (u0 * Ehalf[12 + q] + u1 * Ehalf[15 + q]) + w1 * (u0 * Ehalf[18 + q] + u1 * Ehalf[21 + q]);
-      col[2][q] = v0 * (u0 * Ehalf[24 + q] + u1 * Ehalf[27 + q]) + v1 * (u0 * Ehalf[30 + q] + u1 * Ehalf[33 + q]);
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) Af[i][j] = (float)A[i][j];
+#pragma unroll
+        for (int ab = 0; ab < 6; ++ab) {
+          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
+          const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
+          G[ab][g] = (float)(Fab * r) * (Af[pa][0] * Af[pb][0] + Af[pa][1] * Af[pb][1] + Af[pa][2] * Af[pb][2]);
+        }
+      }
     }
-    double A0[3], A1[3], A2[3];
-    A0[0] = col[1][1] * col[2][2] - col[1][2] * col[2][1];
-    A0[1] = col[1][2] * col[2][0] - col[1][0] * col[2][2];
-    A0[2] = col[1][0] * col[2][1] - col[1][1] * col[2][0];
-    A1[0] = col[2][1] * col[0][2] - col[2][2] * col[0][1];
-    A1[1] = col[2][2] * col[0][0] - col[2][0] * col[0][2];
-    A1[2] = col[2][0] * col[0][1] - col[2][1] * col[0][0];
-    A2[0] = col[0][1] * col[1][2] - col[0][2] * col[1][1];
-    A2[1] = col[0][2] * col[1][0] - col[0][0] * col[1][2];
-    A2[2] = col[0][0] * col[1][1] - col[0][1] * col[1][0];
-    const double det = col[0][0] * A0[0] + col[0][1] * A0[1] + col[0][2] * A0[2];
-    const double f = ks / det;
-    const double G00 = f * F00 * (A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2]);
-    const double G01 = f * F01 * (A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2]);
-    const double G02 = f * F02 * (A0[0] * A2[0] + A0[1] * A2[1] + A0[2] * A2[2]);
-    const double G11 = f * F11 * (A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
-    const double G12 = f * F12 * (A1[0] * A2[0] + A1[1] * A2[1] + A1[2] * A2[2]);
-    const double G22 = f * F22 * (A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const double d0 = dphi(g, i, 0), d1 = dphi(g, i, 1), d2 = dphi(g, i, 2);
-      const double t0v = G00 * d0 + G01 * d1 + G02 * d2;
-      const double t1v = G01 * d0 + G11 * d1 + G12 * d2;
-      const double t2v = G02 * d0 + G12 * d1 + G22 * d2;
+    for (int ab = 0; ab < 6; ++ab) walsh8<VT>(G[ab]);
+
+    // modal block (row/column 0 vanish: psi_0 has no gradient)
+    VT K[64];
 #pragma unroll
-      for (int j = i; j < 8; ++j) K[upper(i, j)] += dphi(g, j, 0) * t0v + dphi(g, j, 1) * t1v + dphi(g, j, 2) * t2v;
+    for (int i = 0; i < 64; ++i) K[i] = (VT)0;
+#pragma unroll
+    for (int mm = 1; mm < 8; ++mm)
+#pragma unroll
+      for (int nn = mm; nn < 8; ++nn) {
+        VT acc = (VT)0;
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa)
+          if ((mm >> aa) & 1)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+              if ((nn >> bb) & 1)
+                acc += (VT)inv_sqrt3_pow(popc3(mm) + popc3(nn) - 2) * G[pair_index(aa, bb)][walsh_index(mm, nn, aa, bb)];
+        K[sym(mm, nn)] = acc;
+      }
+    hadamard_axis<VT, 0>(K);
+    hadamard_axis<VT, 1>(K);
+    hadamard_axis<VT, 2>(K);
+
+    // Scatter into the CSR values (closed-form positions), skipping essential
+    // rows and columns (their diagonal was pre-set to 1).
+    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+    const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
+      if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
+      const int64_t base = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
+      const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
+        if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
+        const int di = (t & 1) - (r & 1), dj = ((t >> 1) & 1) - ((r >> 1) & 1), dk = (t >> 2) - (r >> 2);
+        atomic_add<VT>(vals + base + (dk * cy + dj) * cx + di, K[sym(r, t)]);
+      }
     }
   }
-
-  // Scatter into the CSR values (closed-form positions), skipping essential
-  // rows and columns (their diagonal was pre-set to 1).
-  const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
-    if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
-      if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
-      const int64_t pos = lor_entry_pos(I, J, Kk, (t & 1) - (r & 1), ((t >> 1) & 1) - ((r >> 1) & 1),
-                                        (t >> 2) - (r >> 2), m.nx, m.ny, m.nz);
-      atomic_add<VT>(vals + pos, K[upper(r, t)]);
-    }
-  }
-  }  // sub-hex loop
 }
 
 // Diagonal of every essential row = 1 (the values are zeroed before).
@@ -166,7 +240,7 @@ cudaError_t launch(const LorMesh& m, const LorTables& T, const double* kappa, VT
   }
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: k_assemble<P, VT><<<(unsigned)m.nel, kAsmThreads<P>, 0, s>>>(m, T, kappa, vals); lor_count_launch(); break;
+  case P: k_assemble<P, VT><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(m, T, kappa, vals); lor_count_launch(); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

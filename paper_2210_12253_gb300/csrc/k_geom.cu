@@ -13,59 +13,6 @@
 
 namespace {
 
-// Corner c = c0 + 2 c1 + 4 c2 of element e.
-__device__ __forceinline__ void element_corner(const LorMesh& m, int64_t e, int c, double X[3]) {
-  const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
-  const int64_t a = ex + (c & 1), b = ey + ((c >> 1) & 1), cc = ez + ((c >> 2) & 1);
-  const double* v = m.verts + 3 * (a + (int64_t)(m.nex + 1) * (b + (int64_t)(m.ney + 1) * cc));
-  X[0] = v[0];
-  X[1] = v[1];
-  X[2] = v[2];
-}
-
-// Tabulate the three Jacobian columns of the trilinear map of element e on
-// the tensor grid of the L reference coordinates t[0..L):
-//   col[d][u + L v][comp], with (u, v) the two coordinates other than d, in
-//   increasing axis order.  E.g. col[0][g1 + L g2] = dx/dxi_0 at (., t_g1, t_g2).
-// Cooperative over the block; ends with __syncthreads().
-__device__ void jacobian_columns(const LorMesh& m, int64_t e, const double* t, int L, double* Ehalf,
-                                 double* col) {
-  // Ehalf[d][pair][comp]: half edge vectors along axis d for the 4 edges
-  // parallel to it; pair = (other0 bit) + 2 (other1 bit).
-  for (int idx = threadIdx.x; idx < 36; idx += blockDim.x) {
-    const int d = idx / 12, pair = (idx / 3) % 4, comp = idx % 3;
-    const int o0 = pair & 1, o1 = pair >> 1;
-    int lo = 0, hi = 0;
-    if (d == 0) { lo = 0 + 2 * o0 + 4 * o1; hi = lo + 1; }
-    if (d == 1) { lo = o0 + 0 + 4 * o1; hi = lo + 2; }
-    if (d == 2) { lo = o0 + 2 * o1 + 0; hi = lo + 4; }
-    double A[3], Bv[3];
-    element_corner(m, e, lo, A);
-    element_corner(m, e, hi, Bv);
-    Ehalf[idx] = 0.5 * (Bv[comp] - A[comp]);
-  }
-  __syncthreads();
-  const int L2 = L * L;
-  for (int idx = threadIdx.x; idx < 3 * L2 * 3; idx += blockDim.x) {
-    const int d = idx / (L2 * 3), uv = (idx / 3) % L2, comp = idx % 3;
-    const int u = uv % L, v = uv / L;
-    const double tu = t[u], tv = t[v];
-    const double wu0 = 0.5 * (1.0 - tu), wu1 = 0.5 * (1.0 + tu);
-    const double wv0 = 0.5 * (1.0 - tv), wv1 = 0.5 * (1.0 + tv);
-    const double* E = Ehalf + d * 12 + comp;
-    col[idx] = wv0 * (wu0 * E[0] + wu1 * E[3]) + wv1 * (wu0 * E[6] + wu1 * E[9]);
-  }
-  __syncthreads();
-}
-
-// Adjugate rows of J = [c0 c1 c2]: a0 = c1 x c2, a1 = c2 x c0, a2 = c0 x c1;
-// J^-1 has rows a_i / det, det = c0 . a0.
-__device__ __forceinline__ void cross(const double* u, const double* v, double* w) {
-  w[0] = u[1] * v[2] - u[2] * v[1];
-  w[1] = u[2] * v[0] - u[0] * v[2];
-  w[2] = u[0] * v[1] - u[1] * v[0];
-}
-
 template <int P>
 __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
                                                double* __restrict__ kcopy, double* __restrict__ Dq,
@@ -81,21 +28,21 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   __syncthreads();
   int bad = 0;
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    jacobian_columns(m, e, sx, Q, Ehalf, col);
+    lor_jacobian_columns(m, e, sx, Q, Ehalf, col);
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
       const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
       const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
       const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
       double a0[3], a1[3], a2[3];
-      cross(c1, c2, a0);
-      cross(c2, c0, a1);
-      cross(c0, c1, a2);
+      lor_cross(c1, c2, a0);
+      lor_cross(c2, c0, a1);
+      lor_cross(c0, c1, a2);
       const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
       const double k = kin[e * Q3 + pt];
       if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
       if (!(det > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
-      const double s = k * (sw[g0] * sw[g1] * sw[g2]) / det;
+      const double s = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rcp(det);
       double* D = Dq + e * 6 * Q3 + pt;
       D[0 * Q3] = s * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
       D[1 * Q3] = s * (a0[0] * a1[0] + a0[1] * a1[1] + a0[2] * a1[2]);
@@ -121,14 +68,14 @@ __global__ void __launch_bounds__(128) k_geometry_check(LorMesh m, LorTables T, 
   int bad = 0;
   const int L2 = L * L;
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    jacobian_columns(m, e, t, L, Ehalf, col);
+    lor_jacobian_columns(m, e, t, L, Ehalf, col);
     for (int pt = threadIdx.x; pt < L2 * L; pt += blockDim.x) {
       const int g0 = pt % L, g1 = (pt / L) % L, g2 = pt / L2;
       const double* c0 = col + 0 * L2 * 3 + 3 * (g1 + L * g2);
       const double* c1 = col + 1 * L2 * 3 + 3 * (g0 + L * g2);
       const double* c2 = col + 2 * L2 * 3 + 3 * (g0 + L * g1);
       double a0[3];
-      cross(c1, c2, a0);
+      lor_cross(c1, c2, a0);
       const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
       if (!(det > 0.0)) bad = LOR_FLAG_BAD_GEOM;
     }
@@ -155,14 +102,14 @@ __global__ void __launch_bounds__(128) k_load_vector(LorMesh m, LorTables T, con
   }
   __syncthreads();
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    jacobian_columns(m, e, sx, Q, Ehalf, col);
+    lor_jacobian_columns(m, e, sx, Q, Ehalf, col);
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
       const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
       const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
       const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
       double a0[3];
-      cross(c1, c2, a0);
+      lor_cross(c1, c2, a0);
       const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
       const double fv = f ? f[e * Q3 + pt] : 1.0;
       v[pt] = sw[g0] * sw[g1] * sw[g2] * det * fv;

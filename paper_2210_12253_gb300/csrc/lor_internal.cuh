@@ -108,6 +108,73 @@ __host__ __device__ __forceinline__ bool lor_is_essential(int64_t I, int64_t J, 
 }
 
 // -------------------------------------------------------------------------
+// Device helpers shared by the geometry and assembly kernels.
+// -------------------------------------------------------------------------
+// Corner c = c0 + 2 c1 + 4 c2 of element e.
+__device__ __forceinline__ void lor_element_corner(const LorMesh& m, int64_t e, int c, double X[3]) {
+  const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+  const int64_t a = ex + (c & 1), b = ey + ((c >> 1) & 1), cc = ez + ((c >> 2) & 1);
+  const double* v = m.verts + 3 * (a + (int64_t)(m.nex + 1) * (b + (int64_t)(m.ney + 1) * cc));
+  X[0] = v[0];
+  X[1] = v[1];
+  X[2] = v[2];
+}
+
+// Tabulate the three Jacobian columns of the trilinear map of element e on
+// the tensor grid of the L reference coordinates t[0..L):
+//   col[d][u + L v][comp], with (u, v) the two coordinates other than d, in
+//   increasing axis order.  E.g. col[0][g1 + L g2] = dx/dxi_0 at (., t_g1, t_g2).
+// Cooperative over the block; ends with __syncthreads().
+__device__ __forceinline__ void lor_jacobian_columns(const LorMesh& m, int64_t e, const double* t, int L, double* Ehalf,
+                                 double* col) {
+  // Ehalf[d][pair][comp]: half edge vectors along axis d for the 4 edges
+  // parallel to it; pair = (other0 bit) + 2 (other1 bit).
+  for (int idx = threadIdx.x; idx < 36; idx += blockDim.x) {
+    const int d = idx / 12, pair = (idx / 3) % 4, comp = idx % 3;
+    const int o0 = pair & 1, o1 = pair >> 1;
+    int lo = 0, hi = 0;
+    if (d == 0) { lo = 0 + 2 * o0 + 4 * o1; hi = lo + 1; }
+    if (d == 1) { lo = o0 + 0 + 4 * o1; hi = lo + 2; }
+    if (d == 2) { lo = o0 + 2 * o1 + 0; hi = lo + 4; }
+    double A[3], Bv[3];
+    lor_element_corner(m, e, lo, A);
+    lor_element_corner(m, e, hi, Bv);
+    Ehalf[idx] = 0.5 * (Bv[comp] - A[comp]);
+  }
+  __syncthreads();
+  const int L2 = L * L;
+  for (int idx = threadIdx.x; idx < 3 * L2 * 3; idx += blockDim.x) {
+    const int d = idx / (L2 * 3), uv = (idx / 3) % L2, comp = idx % 3;
+    const int u = uv % L, v = uv / L;
+    const double tu = t[u], tv = t[v];
+    const double wu0 = 0.5 * (1.0 - tu), wu1 = 0.5 * (1.0 + tu);
+    const double wv0 = 0.5 * (1.0 - tv), wv1 = 0.5 * (1.0 + tv);
+    const double* E = Ehalf + d * 12 + comp;
+    col[idx] = wv0 * (wu0 * E[0] + wu1 * E[3]) + wv1 * (wu0 * E[6] + wu1 * E[9]);
+  }
+  __syncthreads();
+}
+
+// Adjugate rows of J = [c0 c1 c2]: a0 = c1 x c2, a1 = c2 x c0, a2 = c0 x c1;
+// J^-1 has rows a_i / det, det = c0 . a0.
+__device__ __forceinline__ void lor_cross(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+// Reciprocal by Newton-Raphson iteration r <- r + r (1 - x r) from an FP32
+// seed (24 correct bits); each step doubles the correct bits, two steps
+// reach FP64 precision (within 1 ulp).  Valid for |x| in the FP32 range.
+__device__ __forceinline__ double lor_rcp(double x) {
+  double r = (double)(1.0f / (float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// -------------------------------------------------------------------------
 // Host-side launchers (defined in the k_*.cu files).  Each returns a
 // cudaError_t from the launch.
 // -------------------------------------------------------------------------

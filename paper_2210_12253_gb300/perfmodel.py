@@ -42,10 +42,13 @@ def setup_flops_per_point():
 
 
 def assemble_flops_per_subhex():
-    """2x2x2 Gauss on one sub-hex, per point: Jacobian columns (81), adjugate
-    (27), det (5), 1/det (1), G (42), G grad(phi_i) for 8 i (120), the 36
-    upper-triangle entries (216): 492 flops x 8 points."""
-    return 8 * 492
+    """One sub-hex block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form:
+    per Gauss point adjugate (27), det (5), 1/det (1), the six scaled metric
+    entries (42) = 75 x 8; six 8-point Walsh transforms (144); the 84-term
+    modal block (168); the modal-to-nodal transform on the 36 symmetric
+    entries, 3 additions per entry and axis (324); kappa_s and scales (20).
+    (The direct nodal formula costs 3,936 flops per sub-hex.)"""
+    return 8 * 75 + 144 + 168 + 324 + 20
 
 
 def apply_flops_per_element(p):
