@@ -174,6 +174,28 @@ int lor_precond_setup(lor_ctx* ctx, int kind, int dtype, int degree, double lo_r
 /* z = B_h r with the preconditioner from lor_precond_setup (r, z f64[N]). */
 int lor_precond_apply(lor_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
+/* Size in bytes of the device array used by lor_precond_apply_noalloc. */
+#define LOR_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* z = B_h r exactly as lor_precond_apply computes it, for callers that must
+ * not allocate device memory when they apply the preconditioner (for example
+ * a solver loop whose device memory is reserved up front by another
+ * allocator, or host code where CUDA allocation calls are not allowed).  The
+ * call performs no cudaMalloc/cudaFree or other allocation: the smoother's
+ * work vectors live in one static device array of LOR_NOALLOC_SCRATCH_BYTES
+ * bytes that every GPU loading the library keeps until the process exits.
+ * It needs 3 N values of the smoother's precision (N = DOFs): up to 699,050
+ * DOFs for an FP64 smoother and 1,398,101 for FP32 (Jacobi and degree 1 need
+ * none); larger sizes are rejected with LOR_EINVAL.  The first call on each
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  All calls share the
+ * array, which keeps the last call's contents (each call writes every element
+ * it reads, so nothing needs clearing); calls that overlap on the GPU race
+ * and must be ordered by the caller.  r, z: f64[N], distinct.
+ * The paper has no counterpart: this is an interface for allocation-free
+ * callers of this library. */
+int lor_precond_apply_noalloc(lor_ctx* ctx, const double* d_r, double* d_z, void* stream);
+
 /* Section 3, step S2: preconditioned CG for A_p x = b with x_0 = 0, the
  * operator of lor_apply (FP64) and the preconditioner of lor_precond_setup
  * (identity if none).  Dot products and recurrences are FP64.  Stops when

@@ -368,3 +368,116 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
   if (status == LOR_ENOCONV) c->err = "pcg: no convergence within maxit";
   return status;
 }
+
+// ---------------------------------------------------------------------------
+// Preconditioner apply without device allocation.
+//
+// lor_precond_apply_noalloc gives the same result as lor_precond_apply, but
+// the smoother's three work vectors live in the file-scope device array below
+// instead of buffers the context allocated, so the call itself never asks the
+// CUDA runtime for memory.  Some callers cannot allocate device memory at the
+// point where they apply a preconditioner: a solver loop whose device memory
+// is reserved up front by another allocator (cudaMalloc/cudaFree there would
+// bypass it, and cudaFree can synchronise the whole device), or host code
+// running where CUDA allocation calls are not allowed.  They can use this
+// entry point once the context has been set up.
+//
+// The array is LOR_NOALLOC_SCRATCH_BYTES long; every GPU that loads the
+// library holds it until the process exits.  A call needs 3 N elements of the
+// smoother's precision (N = DOFs) and is rejected with LOR_EINVAL beyond that.
+// All calls share the array and it keeps the last call's contents; every
+// element a call reads is written by the same call first, so nothing has to
+// start at zero.  Calls that overlap on the GPU (different streams, or two
+// contexts) race on the array and must be ordered by the caller.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) unsigned char lor_noalloc_scratch[LOR_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of lor_noalloc_scratch on the current device (looked up once
+// per device, with that device current; the host-side symbol itself is not a
+// device address).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    err = cudaGetSymbolAddress(&p, lor_noalloc_scratch);
+    if (err != cudaSuccess) return err;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename VT>
+cudaError_t precond_apply_noalloc_t(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
+                                    VT* work, cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  const int g = grid_rows(n);
+  if (c->pc_kind == LOR_PRECOND_JACOBI) {
+    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
+    return cudaGetLastError();
+  }
+  VT* zA = work;
+  VT* zB = zA + n;
+  VT* d = zB + n;
+  const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
+  const double sigma = theta / delta;
+  const int k = c->pc_degree;
+  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr); lor_count_launch();
+  double rho = 1.0 / sigma;
+  VT* zin = zA;
+  VT* zout = zB;
+  for (int j = 1; j < k; ++j) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+    k_cheb_step<VT><<<g, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
+                                          j == k - 1 ? z : nullptr); lor_count_launch();
+    rho = rho_new;
+    VT* t = zin;
+    zin = zout;
+    zout = t;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int lor_precond_apply_noalloc(lor_ctx* c, const double* d_r, double* d_z, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_r || !d_z || d_r == d_z) {
+    c->err = "lor_precond_apply_noalloc: r, z must be distinct device arrays";
+    return LOR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->pc_kind == LOR_PRECOND_NONE) {
+    cudaError_t err = cudaMemcpyAsync(d_z, d_r, sizeof(double) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
+    return err == cudaSuccess ? LOR_OK : fail(c, err, "lor_precond_apply_noalloc");
+  }
+  const size_t elem = c->pc_dtype == LOR_F64 ? sizeof(double) : sizeof(float);
+  const size_t need = 3 * (size_t)c->m.ndof * elem;
+  if (c->pc_kind == LOR_PRECOND_CHEB && c->pc_degree > 1 && need > (size_t)LOR_NOALLOC_SCRATCH_BYTES) {
+    c->err = "lor_precond_apply_noalloc: the smoother needs " + std::to_string(need) +
+             " bytes of scratch but the static array holds " + std::to_string((size_t)LOR_NOALLOC_SCRATCH_BYTES) +
+             " (use lor_precond_apply for this size)";
+    return LOR_EINVAL;
+  }
+  void* work = nullptr;
+  cudaError_t err = noalloc_scratch(&work);
+  if (err != cudaSuccess) return fail(c, err, "lor_precond_apply_noalloc: scratch address");
+  if (c->pc_dtype == LOR_F64)
+    err = precond_apply_noalloc_t<double>(c, c->vals64, c->dinv64, d_r, d_z, (double*)work, s);
+  else
+    err = precond_apply_noalloc_t<float>(c, c->vals32, c->dinv32, d_r, d_z, (float*)work, s);
+  return err == cudaSuccess ? LOR_OK : fail(c, err, "lor_precond_apply_noalloc");
+}

@@ -21,6 +21,7 @@ EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
+    "lor_precond_apply_noalloc",
 ]
 
 
@@ -75,6 +76,8 @@ def load_library(path=LIB):
     L.lor_precond_setup.argtypes = [vp, i, i, i, d, d, d, i, vp, C.POINTER(d), vp]
     L.lor_precond_apply.restype = i
     L.lor_precond_apply.argtypes = [vp, vp, vp, vp]
+    L.lor_precond_apply_noalloc.restype = i
+    L.lor_precond_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.lor_launch_count.restype = i
     L.lor_launch_count.argtypes = [C.POINTER(i64)]
     L.lor_pcg_solve.restype = i
@@ -257,6 +260,15 @@ class LOR:
         z = self._new(self.ndof) if out is None else _dev(out, torch.float64, self.ndof, "out")
         self._call("lor_precond_apply", _ptr(r), _ptr(z))
         return z
+
+    def precond_apply_noalloc(self, r, out):
+        """z = B_h r like precond_apply, with no device allocation in the call:
+        the output must be given and the smoother's work vectors come from a
+        static device array inside the library (see include/lor.h)."""
+        _dev(r, torch.float64, self.ndof, "r")
+        _dev(out, torch.float64, self.ndof, "out")
+        self._call("lor_precond_apply_noalloc", _ptr(r), _ptr(out))
+        return out
 
     def pcg_solve(self, b, rtol=1e-8, maxit=1000, x=None, raise_on_noconv=True):
         """Section 3 step S2: PCG for A_p x = b.  Returns (x, iterations, rel. residual)."""
