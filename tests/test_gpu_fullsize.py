@@ -1,0 +1,158 @@
+"""Parity at the measured sizes, in the launch configuration bench.py times.
+
+* 16^3 elements, p = 4 (274,625 DOFs; the benchmark step): sparsity and LOR
+  values on sampled rows (the oracle computes each row alone), the full
+  high-order apply and backward, SpMV and the Chebyshev-Jacobi smoother
+  against the oracle's own assembled CSR.
+* 32^3 elements, p = 6 (7,189,057 DOFs; the PCG workload): sampled LOR rows,
+  the full apply, and PCG to 1e-8 in FP64 and mixed precision whose true
+  residual is re-checked with the oracle's operator.
+* 24^3 elements, p = 5 (1,771,561 DOFs; the gradient workload): dJ/dtheta by
+  the adjoint against central differences on 16 random directions, and the
+  gradient kernel against the oracle's on the same fields.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2210_12253_gb300.inputs import power_start_vector, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2210_12253_gb300.build import build
+    build()
+
+
+def t(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def setup(name):
+    from paper_2210_12253_gb300 import LOR
+    prob = workload(name)
+    mesh = oracle.Mesh(prob.nex, prob.ney, prob.nez, prob.vertices)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, t(prob.vertices))
+    op.set_coefficient(t(prob.kappa.reshape(-1)), check=True)
+    return prob, mesh, op
+
+
+def sample_rows(prob, n, seed):
+    """Random rows plus every corner/edge/face class of row."""
+    nx, ny, nz = (prob.nex * prob.p + 1, prob.ney * prob.p + 1, prob.nez * prob.p + 1)
+    rng = np.random.default_rng(seed)
+    rows = set(rng.integers(0, nx * ny * nz, n).tolist())
+    for I in (0, 1, prob.p, nx // 2, nx - 2, nx - 1):
+        for J in (0, 1, prob.p, ny - 1):
+            for K in (0, prob.p + 1, nz - 2, nz - 1):
+                rows.add(I + nx * (J + ny * K))
+    return np.array(sorted(rows), dtype=np.int64)
+
+
+def check_rows(prob, mesh, op, rows, tol, dtype):
+    rp, ci = op.build_pattern()
+    rp, ci = rp.cpu().numpy(), ci.cpu().numpy()
+    v = op.assemble(dtype).cpu().numpy().astype(np.float64)
+    cnt, cols, vals = oracle.lor_rows(mesh, prob.p, prob.q, prob.kappa, rows, True)
+    for k, r in enumerate(rows):
+        a, b = rp[r], rp[r + 1]
+        assert b - a == cnt[k]
+        np.testing.assert_array_equal(ci[a:b].astype(np.int64), cols[k, :cnt[k]])
+        ref = vals[k, :cnt[k]]
+        assert np.abs(v[a:b] - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_step_workload_16x16x16_p4():
+    prob, mesh, op = setup("c2_16x16x16_p4")
+    p, q = prob.p, prob.q
+    rows = sample_rows(prob, 3000, 1)
+    check_rows(prob, mesh, op, rows, 1e-12, torch.float64)
+    check_rows(prob, mesh, op, rows, 1e-5, torch.float32)
+    rng = np.random.default_rng(2)
+    x, gy = rng.standard_normal(op.ndof), rng.standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ry = oracle.ho_apply(mesh, p, q, prob.kappa, x)
+    assert np.abs(y - ry).max() <= 1e-12 * np.abs(ry).max()
+    gx, gk = op.apply_backward(t(x), t(gy))
+    rgx, rgk = oracle.ho_apply_backward(mesh, p, q, prob.kappa, x, gy)
+    assert np.abs(gx.cpu().numpy() - rgx).max() <= 1e-12 * np.abs(rgx).max()
+    assert np.abs(gk.cpu().numpy() - rgk.ravel()).max() <= 1e-12 * np.abs(rgk).max()
+    # smoother and SpMV against the oracle's own CSR
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float64)
+    v0 = power_start_vector(op.ndof)
+    lam_ref = oracle.power_lambda_max(*csr, v0, 20)
+    lam = op.precond_setup("cheb", torch.float64, degree=3, power_iters=20, v0=t(v0))
+    assert abs(lam - lam_ref) <= 1e-10 * lam_ref
+    op.precond_setup("cheb", torch.float64, degree=3, lambda_max=lam_ref)
+    z = op.precond_apply(t(prob.rhs)).cpu().numpy()
+    zr = oracle.chebyshev(*csr, prob.rhs, 3, lam_ref / 30, 1.1 * lam_ref)
+    assert np.abs(z - zr).max() <= 1e-12 * np.abs(zr).max()
+    s = op.spmv(t(x), torch.float64).cpu().numpy()
+    sr = oracle.csr_spmv(*csr, x)
+    assert np.abs(s - sr).max() <= 1e-13 * np.abs(sr).max()
+    op.close()
+
+
+def test_pcg_workload_32x32x32_p6():
+    prob, mesh, op = setup("c3_32x32x32_p6")
+    p, q = prob.p, prob.q
+    rows = sample_rows(prob, 2000, 3)
+    check_rows(prob, mesh, op, rows, 1e-12, torch.float64)
+    check_rows(prob, mesh, op, rows, 1e-5, torch.float32)
+    x = np.random.default_rng(4).standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ry = oracle.ho_apply(mesh, p, q, prob.kappa, x)
+    assert np.abs(y - ry).max() <= 1e-12 * np.abs(ry).max()
+    b = t(prob.rhs)
+    v0 = t(power_start_vector(op.ndof))
+    op.build_pattern_internal()
+    its = {}
+    for dt in (torch.float64, torch.float32):
+        op.assemble_internal(dt)
+        op.precond_setup("cheb", dt, degree=3, power_iters=20, v0=v0)
+        u, it, rel = op.pcg_solve(b, 1e-8, 20000)
+        its[dt] = it
+        r = prob.rhs - oracle.ho_apply(mesh, p, q, prob.kappa, u.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.000001e-8 * np.linalg.norm(prob.rhs), dt
+    # mixed precision reaches the same tolerance with a similar iteration count
+    assert its[torch.float32] <= 1.25 * its[torch.float64]
+    op.close()
+
+
+def test_gradient_workload_24x24x24_p5():
+    from paper_2210_12253_gb300 import LOR, solve, solve_with_adjoint
+    prob = workload("c4_24x24x24_p5")
+    mesh = oracle.Mesh(prob.nex, prob.ney, prob.nez, prob.vertices)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, t(prob.vertices))
+    opts = dict(rtol=1e-12, maxit=50000, precond="cheb", dtype=torch.float64)
+    b = t(prob.rhs)
+    ustar = solve(op, torch.exp(t(prob.theta_star.ravel())), b, **opts).detach()
+    th = t(prob.theta.ravel())
+    J, g = solve_with_adjoint(op, th, b, ustar, **opts)
+    g = g.cpu().numpy()
+    # the gradient kernel against the oracle's on the same u and adjoint
+    u = solve(op, torch.exp(th), b, **opts)
+    lam, _, _ = op.pcg_solve((u - ustar).contiguous(), 1e-12, 50000)
+    _, gk_ref = oracle.ho_apply_backward(mesh, prob.p, prob.q, np.exp(prob.theta), u.detach().cpu().numpy(),
+                                         lam.cpu().numpy(), want_gx=False)
+    gref = -np.exp(prob.theta).ravel() * gk_ref.ravel()
+    assert np.abs(g - gref).max() <= 1e-8 * np.abs(gref).max()
+    # central differences on 16 random directions; the step 1e-4 |theta| keeps
+    # the difference quotient above the solver's forward error (relative
+    # residual 1e-12 times the condition number) while the O(step^2)
+    # truncation error stays near 1e-8
+    rng = np.random.default_rng(6)
+    for _ in range(16):
+        v = rng.standard_normal(th.numel())
+        eps = 1e-4 * np.linalg.norm(prob.theta) / np.linalg.norm(v)
+        dv = t(eps * v)
+        Jp = 0.5 * float(((solve(op, torch.exp(th + dv), b, **opts) - ustar) ** 2).sum())
+        Jm = 0.5 * float(((solve(op, torch.exp(th - dv), b, **opts) - ustar) ** 2).sum())
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - float(g @ v)) <= 2e-6 * abs(fd)
+    op.close()
