@@ -336,7 +336,7 @@ def run_pcg(args, dev, rank):
         t0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        u, it, rel = op.pcg_solve(b, 1e-8, 20000)
+        u, it, rel = op.pcg_solve(b, 1e-8, args.pcg_maxit, raise_on_noconv=args.pcg_maxit >= 20000)
         e1.record()
         torch.cuda.synchronize()
         solve_s = e0.elapsed_time(e1) / 1e3
@@ -427,6 +427,9 @@ def main(argv=None):
     ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pcg-maxit", type=int, default=20000,
+                    help="iteration cap of the PCG comparison (a small cap is for profiling only)")
+    ap.add_argument("--pcg-only", action="store_true", help="run only the PCG comparison (profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -441,6 +444,13 @@ def main(argv=None):
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    if args.pcg_only:
+        import torch
+        from paper_2210_12253_gb300.build import build
+        build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"pcg": run_pcg(args, torch.device("cuda", local_rank), rank)}))
+        return 0
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out))

@@ -25,15 +25,34 @@ int grid_rows(int64_t n) {
 #define LOR_GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// sum_j A_ij x_j in the matrix precision VT (x converted on the fly).
+// sum_j A_ij x_j in the matrix precision VT (x converted on the fly), with kLanes lanes per row: lane l takes entries
+// rowptr[i] + l, + 2 kLanes, ... (consecutive lanes read consecutive
+// entries, so a warp reads 32/kLanes row segments of kLanes entries per
+// instruction) and the lanes combine by shuffles; every lane returns the sum.
+// All 32 lanes of the warp must call it (rows past n pass valid = false).
+constexpr int kLanes = 4;
 template <typename VT, typename XT>
-__device__ __forceinline__ VT row_product(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                          const VT* __restrict__ vals, const XT* __restrict__ x, int64_t i) {
+__device__ __forceinline__ VT row_product_lanes(const int64_t* __restrict__ rowptr,
+                                                const int32_t* __restrict__ colidx, const VT* __restrict__ vals,
+                                                const XT* __restrict__ x, int64_t i, bool valid) {
   VT s = 0;
-  const int64_t b = rowptr[i], e = rowptr[i + 1];
-  for (int64_t j = b; j < e; ++j) s += vals[j] * (VT)x[colidx[j]];
+  if (valid) {
+    const int lane = threadIdx.x & (kLanes - 1);
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    for (int64_t j = b + lane; j < e; j += kLanes) s += vals[j] * (VT)x[colidx[j]];
+  }
+#pragma unroll
+  for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
+
+// One (row, lane) per thread; the grid covers all rows exactly.
+#define LOR_ROW_LANES(i, valid, n)                                                        \
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kLanes;            \
+  const bool valid = i < (n);                                                             \
+  const bool lead = valid && (threadIdx.x & (kLanes - 1)) == 0;
+
+unsigned grid_row_lanes(int64_t n) { return (unsigned)((n * kLanes + kThreads - 1) / kThreads); }
 
 template <typename VT>
 __global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
@@ -49,7 +68,9 @@ __global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ rowptr, const 
 template <typename VT>
 __global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                        const VT* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y) {
-  LOR_GRID_STRIDE(i, n) y[i] = (double)row_product<VT, double>(rowptr, colidx, vals, x, i);
+  LOR_ROW_LANES(i, valid, n)
+  const VT s = row_product_lanes<VT, double>(rowptr, colidx, vals, x, i, valid);
+  if (lead) y[i] = (double)s;
 }
 
 // w = D^-1 A v (power iteration), FP64 vectors, VT matrix.
@@ -57,7 +78,9 @@ template <typename VT>
 __global__ void k_dinv_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                             const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ v,
                             double* __restrict__ w) {
-  LOR_GRID_STRIDE(i, n) w[i] = (double)(dinv[i] * row_product<VT, double>(rowptr, colidx, vals, v, i));
+  LOR_ROW_LANES(i, valid, n)
+  const VT s = row_product_lanes<VT, double>(rowptr, colidx, vals, v, i, valid);
+  if (lead) w[i] = (double)(dinv[i] * s);
 }
 
 // Chebyshev step 0 from z_0 = 0: d = z = D^-1 r / theta.  If zout64 is set
@@ -83,8 +106,10 @@ __global__ void k_cheb_step(int64_t n, const int64_t* __restrict__ rowptr, const
                             const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ r,
                             const VT* __restrict__ zin, VT* __restrict__ zout, VT* __restrict__ d, VT c1, VT c2,
                             double* __restrict__ zout64) {
-  LOR_GRID_STRIDE(i, n) {
-    const VT res = (VT)r[i] - row_product<VT, VT>(rowptr, colidx, vals, zin, i);
+  LOR_ROW_LANES(i, valid, n)
+  const VT az = row_product_lanes<VT, VT>(rowptr, colidx, vals, zin, i, valid);
+  if (lead) {
+    const VT res = (VT)r[i] - az;
     const VT dn = c1 * d[i] + c2 * dinv[i] * res;
     const VT zn = zin[i] + dn;
     if (zout64) {
@@ -198,7 +223,7 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
   for (int j = 1; j < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
-    k_cheb_step<VT><<<g, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
+    k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
                                           j == k - 1 ? z : nullptr); lor_count_launch();
     rho = rho_new;
     VT* t = zin;
@@ -236,9 +261,9 @@ cudaError_t lor_launch_diag_inv(const LorMesh& m, const int64_t* rowptr, const i
 cudaError_t lor_launch_spmv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
                             int dtype, const double* x, double* y, cudaStream_t s) {
   if (dtype == LOR_F64) {
-    k_spmv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y); lor_count_launch();
+    k_spmv<double><<<grid_row_lanes(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y); lor_count_launch();
   } else {
-    k_spmv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y); lor_count_launch();
+    k_spmv<float><<<grid_row_lanes(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y); lor_count_launch();
   }
   return cudaGetLastError();
 }
@@ -271,9 +296,9 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
   double lam = 0.0;
   for (int it = 0; it < iters; ++it) {
     if (dtype == LOR_F64) {
-      k_dinv_spmv<double><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w); lor_count_launch();
+      k_dinv_spmv<double><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w); lor_count_launch();
     } else {
-      k_dinv_spmv<float><<<grid_rows(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w); lor_count_launch();
+      k_dinv_spmv<float><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w); lor_count_launch();
     }
     dot_to(c, w, w, S + 0, s);
     dot_to(c, v, v, S + 1, s);
@@ -441,7 +466,7 @@ cudaError_t precond_apply_noalloc_t(lor_ctx* c, const VT* vals, const VT* dinv, 
   for (int j = 1; j < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
-    k_cheb_step<VT><<<g, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
+    k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
                                           j == k - 1 ? z : nullptr); lor_count_launch();
     rho = rho_new;
     VT* t = zin;
