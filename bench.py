@@ -349,6 +349,68 @@ def run_pcg(args, dev, rank):
     return res
 
 
+def run_sweep(args, dev):
+    """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
+    JSON object per degree (setup, FP64 and FP32 assembly, apply, backward,
+    one FP32 Chebyshev-Jacobi degree-3 application), CUDA-event timed, median
+    of `--sweep-reps` after one warm-up, L2 flushed before each launch."""
+    import numpy as np
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import workload
+    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
+
+    hbm_peak, _ = hbm_peak_gbs()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = []
+    for p in args.sweep_p:
+        prob = workload("c5_p%d" % p)
+        op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+        kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
+        del prob.kappa
+        x = torch.tensor(np.random.default_rng(5).standard_normal(op.ndof), device=dev)
+        y, z, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
+        op.set_coefficient(kappa, check=True)
+        op.build_pattern_internal()
+        op.assemble_internal(torch.float32)
+        lam = op.precond_setup("cheb", torch.float32, degree=3, power_iters=20)
+        calls = {
+            "setup": lambda: op.set_coefficient(kappa),
+            "assemble_f64": lambda: op.assemble_internal(torch.float64),
+            "assemble_f32": lambda: op.assemble_internal(torch.float32),
+            "apply": lambda: op.apply(x, out=y),
+            "backward": lambda: op.apply_backward(x, x, gx_out=gx, gk_out=gk),
+            "precond_f32": lambda: op.precond_apply(x, out=z),
+        }
+        res = {"p": p, "elements": op.nel, "ndof": op.ndof, "nnz": op.nnz, "lambda_max": lam}
+        for name, fn in calls.items():
+            fn()
+            times = []
+            for _ in range(args.sweep_reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            kind = {"assemble_f64": "assemble", "assemble_f32": "assemble", "precond_f32": "precond"}.get(name, name)
+            vb = 4 if name.endswith("f32") else 8
+            flops, nbytes = kernel_work(kind, p, op.ndof, op.nel, op.nnz, vbytes=vb, degree=3)
+            res[name] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
+                         "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        op.close()
+        del op, kappa, x, y, z, gx, gk
+        torch.cuda.empty_cache()
+        print(json.dumps(res), flush=True)
+        out.append(res)
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 SAMPLE = "8x8x8 elements, p=4 (35,937 DOFs): the 16^3 p=4 workload's recipe on an 8^3 sub-box (seed 1)"
 
@@ -430,6 +492,9 @@ def main(argv=None):
     ap.add_argument("--pcg-maxit", type=int, default=20000,
                     help="iteration cap of the PCG comparison (a small cap is for profiling only)")
     ap.add_argument("--pcg-only", action="store_true", help="run only the PCG comparison (profiling)")
+    ap.add_argument("--sweep", action="store_true", help="per-kernel throughput versus p at ~20M DOFs")
+    ap.add_argument("--sweep-p", type=int, nargs="*", default=list(range(2, 11)))
+    ap.add_argument("--sweep-reps", type=int, default=5)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -444,6 +509,13 @@ def main(argv=None):
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    if args.sweep:
+        import torch
+        from paper_2210_12253_gb300.build import build
+        build()
+        torch.cuda.set_device(local_rank)
+        run_sweep(args, torch.device("cuda", local_rank))
+        return 0
     if args.pcg_only:
         import torch
         from paper_2210_12253_gb300.build import build

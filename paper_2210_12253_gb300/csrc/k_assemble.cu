@@ -104,16 +104,27 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
                                                              VT* __restrict__ vals) {
   constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kElemsPerCta<P>;
   constexpr int TAB = 3 * L * L * 3;  // three Jacobian-column tables per element
+  constexpr bool F32 = sizeof(VT) == sizeof(float);
   __shared__ double Ehalf[EPB][36];
   __shared__ double tab[EPB][TAB];
-  __shared__ double st[L];
-  if (threadIdx.x < L) st[threadIdx.x] = T.sub_t[threadIdx.x];
+  __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
+  __shared__ double sl0[L], sl1[L];
+  if (threadIdx.x < L) {
+    sl0[threadIdx.x] = T.sub_l0[threadIdx.x];
+    sl1[threadIdx.x] = T.sub_l1[threadIdx.x];
+  }
   __syncthreads();
   const int64_t e_first = (int64_t)blockIdx.x * EPB;
-  // Jacobian columns of each element at the sub-hex Gauss coordinates.
+  // Jacobian columns of each element at the sub-hex Gauss coordinates (FP64;
+  // the FP32 mode also keeps a rounded copy, converted once per element:
+  // conversions share the FP64 pipe on this GPU).
   for (int le = 0; le < EPB; ++le) {
     const int64_t e = e_first + le;
-    if (e < m.nel) lor_jacobian_columns(m, e, st, L, Ehalf[le], tab[le]);
+    if (e < m.nel) lor_jacobian_columns(m, e, sl0, sl1, L, Ehalf[le], tab[le]);
+  }
+  if constexpr (F32) {
+    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
+    __syncthreads();
   }
   const int nwork = EPB * P3;
   for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
@@ -134,44 +145,73 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
     // G_sub^{ab}(g) = F_ab (A_a . A_b) / det_e with A the adjugate rows of the
     // element Jacobian, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64 (the 1/64
     // of the modal-to-nodal transform folded in).
-    const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
-    const double k64 = ks * (1.0 / 64.0);
-    const double F00 = k64 * rb * rc / ra, F01 = k64 * rc, F02 = k64 * rb;
-    const double F11 = k64 * ra * rc / rb, F12 = k64 * ra, F22 = k64 * ra * rb / rc;
     VT G[6][8];
-    const double* t0 = tab[le];
-    const double* t1 = tab[le] + L * L * 3;
-    const double* t2 = tab[le] + 2 * L * L * 3;
+    const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
+    if constexpr (!F32) {
+      const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
+      const double k64 = ks * (1.0 / 64.0);
+      const double F00 = k64 * rb * rc * T.sub_rinv[a], F01 = k64 * rc, F02 = k64 * rb;
+      const double F11 = k64 * ra * rc * T.sub_rinv[b], F12 = k64 * ra, F22 = k64 * ra * rb * T.sub_rinv[c];
+      const double* t0 = tab[le];
+      const double* t1 = tab[le] + L * L * 3;
+      const double* t2 = tab[le] + 2 * L * L * 3;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int u0 = 2 * a + (g & 1), u1 = 2 * b + ((g >> 1) & 1), u2 = 2 * c + (g >> 2);
-      const double* c0 = t0 + 3 * (u1 + L * u2);
-      const double* c1 = t1 + 3 * (u0 + L * u2);
-      const double* c2 = t2 + 3 * (u0 + L * u1);
-      double A[3][3];
-      lor_cross(c1, c2, A[0]);
-      lor_cross(c2, c0, A[1]);
-      lor_cross(c0, c1, A[2]);
-      const double det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
-      const double r = lor_rcp(det);
-      if constexpr (sizeof(VT) == sizeof(double)) {
+      for (int g = 0; g < 8; ++g) {
+        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
+        const double* c0 = t0 + 3 * (u1 + L * u2);
+        const double* c1 = t1 + 3 * (u0 + L * u2);
+        const double* c2 = t2 + 3 * (u0 + L * u1);
+        double A[3][3];
+        lor_cross(c1, c2, A[0]);
+        lor_cross(c2, c0, A[1]);
+        lor_cross(c0, c1, A[2]);
+        const double det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
+        const double r = lor_rcp(det);
 #pragma unroll
         for (int ab = 0; ab < 6; ++ab) {
           const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
           const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
-          G[ab][g] = (Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]);
+          G[ab][g] = (VT)((Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]));
         }
-      } else {
-        float Af[3][3];
+      }
+    } else {
+      // FP64: the first adjugate row and the determinant; FP32: the rest.
+      const float ra = (float)T.sub_r[a], rb = (float)T.sub_r[b], rc = (float)T.sub_r[c];
+      const float k64 = (float)ks * (1.0f / 64.0f);
+      const float F00 = k64 * rb * rc / ra, F01 = k64 * rc, F02 = k64 * rb;
+      const float F11 = k64 * ra * rc / rb, F12 = k64 * ra, F22 = k64 * ra * rb / rc;
+      const double* t0 = tab[le];
+      const double* t1 = tab[le] + L * L * 3;
+      const double* t2 = tab[le] + 2 * L * L * 3;
+      const float* f0 = tabf[le];
+      const float* f1 = tabf[le] + L * L * 3;
+      const float* f2 = tabf[le] + 2 * L * L * 3;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) Af[i][j] = (float)A[i][j];
+      for (int g = 0; g < 8; ++g) {
+        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
+        const int o0 = 3 * (u1 + L * u2), o1 = 3 * (u0 + L * u2), o2 = 3 * (u0 + L * u1);
+        double A0[3];
+        lor_cross(t1 + o1, t2 + o2, A0);
+        const double det = t0[o0] * A0[0] + t0[o0 + 1] * A0[1] + t0[o0 + 2] * A0[2];
+        const float r = 1.0f / (float)det;
+        const float* c0 = f0 + o0;
+        const float* c1 = f1 + o1;
+        const float* c2 = f2 + o2;
+        float A[3][3];
+        A[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
+        A[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
+        A[0][2] = c1[0] * c2[1] - c1[1] * c2[0];
+        A[1][0] = c2[1] * c0[2] - c2[2] * c0[1];
+        A[1][1] = c2[2] * c0[0] - c2[0] * c0[2];
+        A[1][2] = c2[0] * c0[1] - c2[1] * c0[0];
+        A[2][0] = c0[1] * c1[2] - c0[2] * c1[1];
+        A[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
+        A[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
 #pragma unroll
         for (int ab = 0; ab < 6; ++ab) {
           const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
-          const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
-          G[ab][g] = (float)(Fab * r) * (Af[pa][0] * Af[pb][0] + Af[pa][1] * Af[pb][1] + Af[pa][2] * Af[pb][2]);
+          const float Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
+          G[ab][g] = (VT)((Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]));
         }
       }
     }

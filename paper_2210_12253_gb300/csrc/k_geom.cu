@@ -20,15 +20,16 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ double Ehalf[36];
   __shared__ double col[3 * Q2 * 3];
-  __shared__ double sx[Q], sw[Q];
+  __shared__ double sw[Q], s0[Q], s1[Q];
   if (threadIdx.x < Q) {
-    sx[threadIdx.x] = T.gx[threadIdx.x];
     sw[threadIdx.x] = T.gw[threadIdx.x];
+    s0[threadIdx.x] = T.gl0[threadIdx.x];
+    s1[threadIdx.x] = T.gl1[threadIdx.x];
   }
   __syncthreads();
   int bad = 0;
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    lor_jacobian_columns(m, e, sx, Q, Ehalf, col);
+    lor_jacobian_columns(m, e, s0, s1, Q, Ehalf, col);
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
       const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
@@ -62,13 +63,16 @@ __global__ void __launch_bounds__(128) k_geometry_check(LorMesh m, LorTables T, 
                                                         int* __restrict__ status) {
   __shared__ double Ehalf[36];
   __shared__ double col[3 * (2 * LOR_MAX_P + 2) * (2 * LOR_MAX_P + 2) * 3];
-  __shared__ double t[2 * LOR_MAX_P + 2];
-  if (threadIdx.x < L) t[threadIdx.x] = use_sub ? T.sub_t[threadIdx.x] : T.gx[threadIdx.x];
+  __shared__ double t0[2 * LOR_MAX_P + 2], t1[2 * LOR_MAX_P + 2];
+  if (threadIdx.x < L) {
+    t0[threadIdx.x] = use_sub ? T.sub_l0[threadIdx.x] : T.gl0[threadIdx.x];
+    t1[threadIdx.x] = use_sub ? T.sub_l1[threadIdx.x] : T.gl1[threadIdx.x];
+  }
   __syncthreads();
   int bad = 0;
   const int L2 = L * L;
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    lor_jacobian_columns(m, e, t, L, Ehalf, col);
+    lor_jacobian_columns(m, e, t0, t1, L, Ehalf, col);
     for (int pt = threadIdx.x; pt < L2 * L; pt += blockDim.x) {
       const int g0 = pt % L, g1 = (pt / L) % L, g2 = pt / L2;
       const double* c0 = col + 0 * L2 * 3 + 3 * (g1 + L * g2);
@@ -92,17 +96,18 @@ __global__ void __launch_bounds__(128) k_load_vector(LorMesh m, LorTables T, con
   constexpr int Q = P + 2, N = P + 1, Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ double Ehalf[36];
   __shared__ double col[3 * Q2 * 3];
-  __shared__ double sx[Q], sw[Q], sB[Q * N];
+  __shared__ double s0[Q], s1[Q], sw[Q], sB[Q * N];
   __shared__ double v[Q3], t1[N * Q2];
   double* t2 = v;  // v is dead once t1 is formed (N N Q <= Q^3)
   for (int i = threadIdx.x; i < Q * N; i += blockDim.x) sB[i] = T.B[i];
   if (threadIdx.x < Q) {
-    sx[threadIdx.x] = T.gx[threadIdx.x];
+    s0[threadIdx.x] = T.gl0[threadIdx.x];
+    s1[threadIdx.x] = T.gl1[threadIdx.x];
     sw[threadIdx.x] = T.gw[threadIdx.x];
   }
   __syncthreads();
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
-    lor_jacobian_columns(m, e, sx, Q, Ehalf, col);
+    lor_jacobian_columns(m, e, s0, s1, Q, Ehalf, col);
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
       const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);

@@ -107,6 +107,10 @@ void build_tables(int p, LorTables* T) {
   gauss_legendre_rule(q, T->gx, T->gw);
   gauss_lobatto_nodes(p, T->gll);
   for (int g = 0; g < q; ++g) {
+    T->gl0[g] = (double)(0.5L * (1.0L - (ld)T->gx[g]));
+    T->gl1[g] = (double)(0.5L * (1.0L + (ld)T->gx[g]));
+  }
+  for (int g = 0; g < q; ++g) {
     ld phi[64], dphi[64];
     lagrange_barycentric(n, T->gll, (ld)T->gx[g], phi, dphi);
     for (int i = 0; i < n; ++i) {
@@ -119,6 +123,7 @@ void build_tables(int p, LorTables* T) {
     const ld lo = T->gll[a], hi = T->gll[a + 1];
     const ld r = 0.5L * (hi - lo), mid = 0.5L * (hi + lo);
     T->sub_r[a] = (double)r;
+    T->sub_rinv[a] = (double)(1.0L / r);
     for (int s = 0; s < 2; ++s) {
       const ld t = mid + (s ? 1.0L : -1.0L) * r * inv_sqrt3;
       T->sub_t[2 * a + s] = (double)t;

@@ -22,9 +22,12 @@ struct LorTables {
   double gll[LOR_MAX_N];                // Gauss-Lobatto nodes
   // LOR sub-hexes: interval a = [gll[a], gll[a+1]] of each axis
   double sub_r[LOR_MAX_P];              // half width (gll[a+1]-gll[a])/2
+  double sub_rinv[LOR_MAX_P];           // 1 / sub_r
   double sub_t[2 * LOR_MAX_P];          // element reference coordinate of the 2 Gauss points of each interval
   double sub_l0[2 * LOR_MAX_P];         // (1 - t)/2 at the 2 Gauss points of each interval
   double sub_l1[2 * LOR_MAX_P];         // (1 + t)/2 at the same points
+  double gl0[LOR_MAX_Q];                // (1 - x_g)/2 at the high-order Gauss points
+  double gl1[LOR_MAX_Q];                // (1 + x_g)/2
   int bin_first[LOR_MAX_P];             // high-order Gauss points of interval a:
   int bin_count[LOR_MAX_P];             //   g = bin_first[a] .. bin_first[a]+bin_count[a]-1
   double bin_w[LOR_MAX_Q];              // w_g / sum_{g' in bin(g)} w_g'
@@ -121,12 +124,15 @@ __device__ __forceinline__ void lor_element_corner(const LorMesh& m, int64_t e, 
 }
 
 // Tabulate the three Jacobian columns of the trilinear map of element e on
-// the tensor grid of the L reference coordinates t[0..L):
+// the tensor grid of L reference coordinates t[0..L), given the bilinear
+// weights w0[i] = (1 - t_i)/2, w1[i] = (1 + t_i)/2:
 //   col[d][u + L v][comp], with (u, v) the two coordinates other than d, in
 //   increasing axis order.  E.g. col[0][g1 + L g2] = dx/dxi_0 at (., t_g1, t_g2).
+// dx/dxi_d = sum over the 4 edges along d of w(t_u) w(t_v) (X_hi - X_lo)/2,
+// evaluated separably (2 FP64 operations per table entry).
 // Cooperative over the block; ends with __syncthreads().
-__device__ __forceinline__ void lor_jacobian_columns(const LorMesh& m, int64_t e, const double* t, int L, double* Ehalf,
-                                 double* col) {
+__device__ __forceinline__ void lor_jacobian_columns(const LorMesh& m, int64_t e, const double* w0, const double* w1,
+                                                     int L, double* Ehalf, double* col) {
   // Ehalf[d][pair][comp]: half edge vectors along axis d for the 4 edges
   // parallel to it; pair = (other0 bit) + 2 (other1 bit).
   for (int idx = threadIdx.x; idx < 36; idx += blockDim.x) {
@@ -143,14 +149,13 @@ __device__ __forceinline__ void lor_jacobian_columns(const LorMesh& m, int64_t e
   }
   __syncthreads();
   const int L2 = L * L;
-  for (int idx = threadIdx.x; idx < 3 * L2 * 3; idx += blockDim.x) {
-    const int d = idx / (L2 * 3), uv = (idx / 3) % L2, comp = idx % 3;
-    const int u = uv % L, v = uv / L;
-    const double tu = t[u], tv = t[v];
-    const double wu0 = 0.5 * (1.0 - tu), wu1 = 0.5 * (1.0 + tu);
-    const double wv0 = 0.5 * (1.0 - tv), wv1 = 0.5 * (1.0 + tv);
+  for (int idx = threadIdx.x; idx < 9 * L; idx += blockDim.x) {
+    const int d = idx / (3 * L), u = (idx / 3) % L, comp = idx % 3;
     const double* E = Ehalf + d * 12 + comp;
-    col[idx] = wv0 * (wu0 * E[0] + wu1 * E[3]) + wv1 * (wu0 * E[6] + wu1 * E[9]);
+    const double a = w0[u] * E[0] + w1[u] * E[3];  // v-bit 0 edges, interpolated in u
+    const double b = w0[u] * E[6] + w1[u] * E[9];  // v-bit 1 edges
+    double* cd = col + d * L2 * 3 + comp;
+    for (int v = 0; v < L; ++v) cd[3 * (u + L * v)] = w0[v] * a + w1[v] * b;
   }
   __syncthreads();
 }
