@@ -483,8 +483,8 @@ def run_reference(args, rank, world):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["liblor", "reference"], default="liblor")
     ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
