@@ -8,7 +8,9 @@ One step = one pass of the hot path over the 16^3-element, p = 4 workload
   its diagonal) -> backward of the apply (gx and gkappa).
 value = DOFs processed per second over the timed steps (GDOF/s), summed over
 ranks.  The PCG time to 1e-8 (FP64 vs mixed precision) is measured on the
-32^3-element, p = 6 workload (7,189,057 DOFs) and reported under "pcg".
+32^3-element, p = 6 workload (7,189,057 DOFs) and reported under "pcg"; the
+adjoint gradient dJ/dtheta (forward solve, adjoint solve, gradient kernel) on
+the 24^3-element, p = 5 workload under "gradient".
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
@@ -32,6 +34,7 @@ METRIC = "LOR assembly & HO apply GDOF/s (%HBM peak); PCG s to 1e-8, mixed vs FP
 UNIT = "GDOF/s"
 STEP_WORKLOAD = "c2_16x16x16_p4"
 PCG_WORKLOAD = "c3_32x32x32_p6"
+GRAD_WORKLOAD = "c4_24x24x24_p5"
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -285,6 +288,9 @@ def run_gpu(args, rank, world, local_rank):
     pcg = None
     if not args.no_pcg:
         pcg = run_pcg(args, dev, rank)
+    grad = None
+    if not args.no_grad:
+        grad = run_gradient(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -300,7 +306,7 @@ def run_gpu(args, rank, world, local_rank):
            "kernels": kernels, "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps},
-           "gpu_launches": int(launches), "clocks": clk, "pcg": pcg}
+           "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     op.close()
@@ -345,6 +351,52 @@ def run_pcg(args, dev, rank):
                       "setup_s": ev[0].elapsed_time(ev[2]) / 1e3,
                       "s_per_iteration": solve_s / max(it, 1)}
     res["mixed_speedup"] = res["fp64"]["solve_s"] / res["mixed"]["solve_s"]
+    op.close()
+    return res
+
+
+def run_gradient(args, dev):
+    """dJ/dtheta on the 24^3, p = 5 workload (1,771,561 DOFs): forward PCG
+    solve, adjoint PCG solve with the same preconditioner, and the gradient
+    kernel, each timed with CUDA events (rtol 1e-8, FP64)."""
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import power_start_vector, workload
+
+    prob = workload(GRAD_WORKLOAD)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    b = torch.tensor(prob.rhs, device=dev)
+    v0 = torch.tensor(power_start_vector(op.ndof), device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    theta = torch.tensor(prob.theta.reshape(-1), device=dev)
+    kstar = torch.exp(torch.tensor(prob.theta_star.reshape(-1), device=dev))
+    op.set_coefficient(kstar)
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float64)
+    op.precond_setup("cheb", torch.float64, degree=3, power_iters=20, v0=v0)
+    ustar, _, _ = op.pcg_solve(b, 1e-8, 20000)
+    torch.cuda.synchronize()
+    ev[0].record()
+    kappa = torch.exp(theta)
+    op.set_coefficient(kappa)
+    op.assemble_internal(torch.float64)
+    op.precond_setup("cheb", torch.float64, degree=3, power_iters=20, v0=v0)
+    ev[1].record()
+    u, it_f, _ = op.pcg_solve(b, 1e-8, 20000)
+    ev[2].record()
+    lam, it_a, _ = op.pcg_solve((u - ustar).contiguous(), 1e-8, 20000)
+    ev[3].record()
+    _, gk = op.apply_backward(u, lam, want_gx=False)
+    grad = -kappa * gk
+    ev[4].record()
+    torch.cuda.synchronize()
+    res = {"workload": GRAD_WORKLOAD + ": 24^3 hexes, p=5, 1,771,561 DOFs, +-10% h jitter (seed 3), "
+                                       "theta ~ N(0, 0.5^2), J = |u - u*|^2 / 2, PCG rtol 1e-8 (FP64)",
+           "setup_s": ev[0].elapsed_time(ev[1]) / 1e3, "forward_s": ev[1].elapsed_time(ev[2]) / 1e3,
+           "adjoint_s": ev[2].elapsed_time(ev[3]) / 1e3, "gradient_kernel_ms": ev[3].elapsed_time(ev[4]),
+           "forward_iterations": it_f, "adjoint_iterations": it_a,
+           "total_s": ev[0].elapsed_time(ev[4]) / 1e3, "grad_norm": float(grad.norm())}
     op.close()
     return res
 
@@ -488,6 +540,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["liblor", "reference"], default="liblor")
     ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the 24^3 p=5 adjoint-gradient timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pcg-maxit", type=int, default=20000,
                     help="iteration cap of the PCG comparison (a small cap is for profiling only)")

@@ -22,8 +22,6 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-
 template <int P>
 struct Sz {
   static constexpr int N = P + 1, Q = P + 2, NH = N / 2, QH = Q / 2;
@@ -32,11 +30,13 @@ struct Sz {
   static constexpr int A1 = 2 * N * N * Q;      // [c][k][j][g0], c in {B, d} of the x stage
   static constexpr int A2 = 3 * N * Q * Q;      // [c][k][g1][g0]
   static constexpr int PER_ELEM = A1 + A2;
-  // elements per CTA (apply; the backward holds two fields and uses half)
-  // (chosen so that the z stage, the heaviest, has close to one line per thread)
-  static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 4
+  // elements per CTA and CTA size: the z stage (the heaviest) gets about one
+  // line per thread, and high-degree CTAs stay small so that several share an
+  // SM (the FP64 pipe then stays busy while one CTA waits at a barrier)
+  static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 3 : P == 6 ? 2
                          : P == 7 ? 3 : P <= 9 ? 2 : 1;
   static constexpr int EB = E;
+  static constexpr int T = ((E * Q * Q + 31) / 32) * 32;
   // folded tables in shared memory (doubles)
   static constexpr int TB = Q * N;                  // B_1D, d_1D
   static constexpr int TF = Q * (NH > 0 ? NH : 1);  // BE, BO, DE, DO: [g][i], g < Q, i < NH
@@ -382,7 +382,7 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_apply(LorMesh m, LorTables T, const double* __restrict__ Dq,
+__global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const double* __restrict__ Dq,
                                                     const double* __restrict__ x, double* __restrict__ y) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(LorMesh m, LorTables T, cons
 // next EB); gkappa = grad(x)^T (D / kappa) grad(gy) on each z line, and
 // gx = A_p gy through the same transposed stages as the apply.
 template <int P>
-__global__ void __launch_bounds__(kThreads, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
+__global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
                                                              const double* __restrict__ Dq,
                                                              const double* __restrict__ kappa,
                                                              const double* __restrict__ x,
@@ -516,7 +516,7 @@ cudaError_t apply_p(const LorMesh& m, const LorTables& T, const double* Dq, cons
   cudaError_t err = configure(k_apply<P>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply<P><<<(unsigned)blocks, kThreads, bytes, s>>>(m, T, Dq, x, y); lor_count_launch();
+  k_apply<P><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -529,7 +529,7 @@ cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, c
   cudaError_t err = configure(k_apply_backward<P>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::EB - 1) / Z::EB;
-  k_apply_backward<P><<<(unsigned)blocks, kThreads, bytes, s>>>(m, T, Dq, kappa, x, gy, gx, gk); lor_count_launch();
+  k_apply_backward<P><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, kappa, x, gy, gx, gk); lor_count_launch();
   return cudaGetLastError();
 }
 
