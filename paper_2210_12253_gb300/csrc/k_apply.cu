@@ -539,6 +539,11 @@ cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double*
                              cudaStream_t s) {
   cudaError_t err = init_output(m, x, y, s);
   if (err != cudaSuccess) return err;
+  return lor_launch_apply_accumulate(m, T, Dq, x, y, s);
+}
+
+cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* x,
+                                        double* y, cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
   case P: return apply_p<P>(m, T, Dq, x, y, s);

@@ -171,31 +171,6 @@ __global__ void __launch_bounds__(kThreads) k_reduce_final(const double* __restr
 // Device scalars (slots of ctx->red after the partials).
 enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_COUNT = 5 };
 
-// x += alpha p, r -= alpha q with alpha = rz / pq read on the device;
-// also forms the block partials of r.r.
-__global__ void __launch_bounds__(kThreads) k_pcg_xr(int64_t n, const double* __restrict__ S, int rz_slot,
-                                                     const double* __restrict__ p, const double* __restrict__ q,
-                                                     double* __restrict__ x, double* __restrict__ r,
-                                                     double* __restrict__ partial) {
-  const double alpha = S[rz_slot] / S[S_PQ];
-  double s = 0.0;
-  LOR_GRID_STRIDE(i, n) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    s += ri * ri;
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// p = z + beta p with beta = rz_new / rz_old (device scalars).
-__global__ void k_pcg_p(int64_t n, const double* __restrict__ S, int new_slot, int old_slot,
-                        const double* __restrict__ z, double* __restrict__ p) {
-  const double beta = S[new_slot] / S[old_slot];
-  LOR_GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
-}
-
 __global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
                            double* __restrict__ r) {
   LOR_GRID_STRIDE(i, n) r[i] = b[i] - Ax[i];
@@ -323,6 +298,193 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
   return LOR_OK;
 }
 
+namespace {
+
+// ---------------------------------------------------------------- fused PCG kernels
+// Each dot product finishes in the last CTA to arrive (arrival counted with
+// an atomic after a fence; that CTA sums the per-CTA partials in index order,
+// so the result does not depend on which CTA finishes last, and resets the
+// counter).  No CTA waits for another.
+__device__ __forceinline__ void finish_sums(double s0, double s1, int nsum, double* __restrict__ partial,
+                                            unsigned* __restrict__ counter, double* __restrict__ out0,
+                                            double* __restrict__ out1) {
+  __shared__ bool last;
+  s0 = block_sum(s0);
+  if (nsum > 1) s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s0;
+    if (nsum > 1) partial[gridDim.x + blockIdx.x] = s1;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const volatile double* vp = partial;
+  double t0 = 0.0, t1 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    t0 += vp[i];
+    if (nsum > 1) t1 += vp[gridDim.x + i];
+  }
+  t0 = block_sum(t0);
+  if (nsum > 1) t1 = block_sum(t1);
+  if (threadIdx.x == 0) {
+    *out0 = t0;
+    if (nsum > 1) *out1 = t1;
+    *counter = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const double* __restrict__ a,
+                                                      const double* __restrict__ b, double* __restrict__ partial,
+                                                      unsigned* __restrict__ counter, double* __restrict__ out) {
+  double s = 0.0;
+  LOR_GRID_STRIDE(i, n) s += a[i] * b[i];
+  finish_sums(s, 0.0, 1, partial, counter, out, nullptr);
+}
+
+// x += alpha p, r -= alpha q (alpha = rz / pq on the device), r.r, and the
+// first step of the preconditioner on the updated r:
+//   mode 0 (none): z = r;  mode 1 (Jacobi): z = D^-1 r;
+//   mode 2 (Chebyshev, degree 1): z = D^-1 r / theta;
+//   mode 3 (Chebyshev, degree >= 2): zA = d = D^-1 r / theta (smoother precision).
+// Modes 0-2 also form r.z (z is final there).
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double* __restrict__ S, int rz_slot,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         double* __restrict__ x, double* __restrict__ r, int mode,
+                                                         const VT* __restrict__ dinv, VT inv_theta,
+                                                         double* __restrict__ z, VT* __restrict__ zA,
+                                                         VT* __restrict__ d, double* __restrict__ partial,
+                                                         unsigned* __restrict__ counter, double* __restrict__ out_rr,
+                                                         double* __restrict__ out_rz) {
+  const double alpha = S[rz_slot] / S[S_PQ];
+  double srr = 0.0, srz = 0.0;
+  LOR_GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    srr += ri * ri;
+    if (mode == 0) {
+      z[i] = ri;
+      srz += ri * ri;
+    } else if (mode == 1 || mode == 2) {
+      const VT zi = mode == 1 ? dinv[i] * (VT)ri : dinv[i] * (VT)ri * inv_theta;
+      z[i] = (double)zi;
+      srz += ri * (double)zi;
+    } else {
+      const VT zi = dinv[i] * (VT)ri * inv_theta;
+      zA[i] = zi;
+      d[i] = zi;
+    }
+  }
+  finish_sums(srr, srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz);
+}
+
+// Last Chebyshev step fused with r.z: z = z_in + (c1 d + c2 D^-1 (r - A z_in))
+// written as FP64, and the partial sums of r.z.  kLanes lanes per row; every
+// warp runs the same number of row rounds so that its shuffles stay uniform.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_pcg_cheb_last(int64_t n, const int64_t* __restrict__ rowptr,
+                                                            const int32_t* __restrict__ colidx,
+                                                            const VT* __restrict__ vals, const VT* __restrict__ dinv,
+                                                            const double* __restrict__ r,
+                                                            const VT* __restrict__ zin, const VT* __restrict__ d,
+                                                            VT c1, VT c2, double* __restrict__ z,
+                                                            double* __restrict__ partial,
+                                                            unsigned* __restrict__ counter, double* __restrict__ out) {
+  const int64_t rows_per_round = (int64_t)gridDim.x * blockDim.x / kLanes;
+  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kLanes;
+  const int group = (threadIdx.x & 31) / kLanes;
+  double srz = 0.0;
+  for (int64_t base = warp_first; base < n; base += rows_per_round) {
+    const int64_t i = base + group;
+    const bool valid = i < n;
+    const VT az = row_product_lanes<VT, VT>(rowptr, colidx, vals, zin, i, valid);
+    if (valid && (threadIdx.x & (kLanes - 1)) == 0) {
+      const double ri = r[i];
+      const VT zn = zin[i] + (c1 * d[i] + c2 * dinv[i] * ((VT)ri - az));
+      z[i] = (double)zn;
+      srz += ri * (double)zn;
+    }
+  }
+  finish_sums(srz, 0.0, 1, partial, counter, out, nullptr);
+}
+
+// p = z + beta p (beta = rz_new / rz_old; first: p = z) and the output of
+// the next apply initialised: q = p on essential DOFs, 0 elsewhere.
+__global__ void k_pcg_direction(LorMesh m, const double* __restrict__ S, int new_slot, int old_slot, int first,
+                                const double* __restrict__ z, double* __restrict__ p, double* __restrict__ q) {
+  const double beta = first ? 0.0 : S[new_slot] / S[old_slot];
+  LOR_GRID_STRIDE(i, m.ndof) {
+    const double pi = first ? z[i] : z[i] + beta * p[i];
+    p[i] = pi;
+    const int64_t I = i % m.nx, J = (i / m.nx) % m.ny, K = i / (m.nx * m.ny);
+    q[i] = lor_is_essential(I, J, K, m.nx, m.ny, m.nz) ? pi : 0.0;
+  }
+}
+
+// two partial sums per CTA, after the scalars
+double* pcg_partials(lor_ctx* c) { return c->red + LOR_RED_BLOCKS + 16; }
+
+// Grid of a reducing PCG kernel: every SM filled to the kernel's occupancy
+// (the loops are grid-stride), at most LOR_PCG_MAX_BLOCKS CTAs.
+template <typename K>
+int pcg_grid(K kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+  const int g = sms * (per_sm > 0 ? per_sm : 1);
+  return g < 1 ? 1 : g > LOR_PCG_MAX_BLOCKS ? LOR_PCG_MAX_BLOCKS : g;
+}
+
+template <typename VT>
+cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
+                             double* out_rz, int grid, cudaStream_t s) {
+  // Chebyshev steps 1 .. k-1 after k_pcg_update's step 0 (degree >= 2)
+  const int64_t n = c->m.ndof;
+  VT* zA = (VT*)c->pc_work;
+  VT* zB = zA + n;
+  VT* d = zB + n;
+  const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
+  const double sigma = theta / delta;
+  const int k = c->pc_degree;
+  double rho = 1.0 / sigma;
+  VT* zin = zA;
+  VT* zout = zB;
+  for (int j = 1; j < k; ++j) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+    if (j < k - 1) {
+      k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d,
+                                                            (VT)c1, (VT)c2, nullptr); lor_count_launch();
+    } else {
+      k_pcg_cheb_last<VT><<<grid, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, d, (VT)c1,
+                                                        (VT)c2, z, pcg_partials(c), c->red_count, out_rz); lor_count_launch();
+    }
+    rho = rho_new;
+    VT* t = zin;
+    zin = zout;
+    zout = t;
+  }
+  return cudaGetLastError();
+}
+
+template <typename VT>
+cudaError_t pcg_update(lor_ctx* c, const VT* dinv, double* S, int cur, const double* p, const double* q, double* x,
+                       double* r, double* z, int mode, double* out_rz, int grid, cudaStream_t s) {
+  const double theta = 0.5 * (c->pc_hi + c->pc_lo);
+  VT* zA = (VT*)c->pc_work;
+  VT* d = zA ? zA + 2 * c->m.ndof : nullptr;
+  k_pcg_update<VT><<<grid, kThreads, 0, s>>>(c->m.ndof, S, cur, p, q, x, r, mode, dinv,
+                                                   (VT)(theta > 0 ? 1.0 / theta : 1.0), z, zA, d, pcg_partials(c),
+                                                   c->red_count, S + S_RR, out_rz); lor_count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                  cudaStream_t s) {
   const int64_t n = c->m.ndof;
@@ -330,13 +492,24 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
   double* z = r + n;
   double* p = z + n;
   double* q = p + n;
-  double* S = c->red + LOR_RED_BLOCKS;
+  double* S = c->red + LOR_RED_BLOCKS;  // S[0] = p.q, S[1] = r.r, S[2] = b.b, S[3], S[4] = r.z (alternating)
   double* hs = c->h_scalar;
   const int g = grid_rows(n);
+  const bool f64 = c->pc_dtype == LOR_F64;
+  // preconditioner mode of the fused update (see k_pcg_update)
+  const int mode = c->pc_kind == LOR_PRECOND_NONE ? 0 : c->pc_kind == LOR_PRECOND_JACOBI ? 1 : c->pc_degree == 1 ? 2 : 3;
+  const int g_dot = pcg_grid(k_pcg_dot);
+  const int g_upd = f64 ? pcg_grid(k_pcg_update<double>) : pcg_grid(k_pcg_update<float>);
+  const int g_last = f64 ? pcg_grid(k_pcg_cheb_last<double>) : pcg_grid(k_pcg_cheb_last<float>);
+  auto dot = [&](const double* a, const double* bb, double* out) {
+    k_pcg_dot<<<g_dot, kThreads, 0, s>>>(n, a, bb, pcg_partials(c), c->red_count, out); lor_count_launch();
+  };
   cudaError_t err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  if (err == cudaSuccess) err = dot_to(c, b, b, S + S_BB, s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_BB, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) {
+    dot(b, b, S + S_BB);
+    err = cudaMemcpyAsync(hs, S + S_BB, sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return fail(c, err, "pcg");
   const double nb = sqrt(hs[0]);
@@ -348,28 +521,30 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
   } else {
     int rc = lor_precond_apply_impl(c, r, z, s);
     if (rc) return rc;
-    cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
     int cur = S_RZ0;
-    dot_to(c, r, z, S + cur, s);
+    dot(r, z, S + cur);
+    k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
     while (it < maxit) {
-      err = lor_launch_apply(c->m, c->T, c->Dq, p, q, s);
+      err = lor_launch_apply_accumulate(c->m, c->T, c->Dq, p, q, s);
       if (err != cudaSuccess) return fail(c, err, "pcg apply");
-      dot_to(c, p, q, S + S_PQ, s);
-      k_pcg_xr<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(n, S, cur, p, q, x, r, c->red); lor_count_launch();
-      k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, S + S_RR); lor_count_launch();
-      err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+      dot(p, q, S + S_PQ);
+      const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
+      err = f64 ? pcg_update<double>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s)
+                : pcg_update<float>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s);
+      if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (err == cudaSuccess) err = cudaStreamSynchronize(s);
       if (err != cudaSuccess) return fail(c, err, "pcg");
       ++it;
       rel = sqrt(hs[0]) / nb;
+      bool restarted = false;
       if (rel <= rtol) {
         // confirm on the true residual b - A x
         err = lor_launch_apply(c->m, c->T, c->Dq, x, q, s);
         if (err == cudaSuccess) {
           k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
-          err = dot_to(c, r, r, S + S_RR, s);
+          dot(r, r, S + S_RR);
+          err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
-        if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return fail(c, err, "pcg");
         rel = sqrt(hs[0]) / nb;
@@ -377,12 +552,18 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
           status = LOR_OK;
           break;
         }
+        // continue from the true residual: precondition it afresh
+        rc = lor_precond_apply_impl(c, r, z, s);
+        if (rc) return rc;
+        dot(r, z, S + nxt);
+        restarted = true;
       }
-      rc = lor_precond_apply_impl(c, r, z, s);
-      if (rc) return rc;
-      const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
-      dot_to(c, r, z, S + nxt, s);
-      k_pcg_p<<<g, kThreads, 0, s>>>(n, S, nxt, cur, z, p); lor_count_launch();
+      if (!restarted && mode == 3) {
+        err = f64 ? pcg_precond_rest<double>(c, c->vals64, c->dinv64, r, z, S + nxt, g_last, s)
+                  : pcg_precond_rest<float>(c, c->vals32, c->dinv32, r, z, S + nxt, g_last, s);
+        if (err != cudaSuccess) return fail(c, err, "pcg precond");
+      }
+      k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q); lor_count_launch();
       cur = nxt;
     }
     err = cudaGetLastError();

@@ -193,6 +193,7 @@ void free_all(lor_ctx* c) {
   cudaFree(c->pc_work);
   cudaFree(c->pcg_work);
   cudaFree(c->red);
+  cudaFree(c->red_count);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
 }
 
@@ -243,7 +244,8 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
   int rc = LOR_OK;
   if (!rc) rc = alloc(c, &c->verts, 3 * nv, "vertices");
   if (!rc) rc = alloc(c, &c->d_status, 4, "status");
-  if (!rc) rc = alloc(c, &c->red, LOR_RED_BLOCKS + 16, "reduction");
+  if (!rc) rc = alloc(c, &c->red, LOR_RED_BLOCKS + 16 + 2 * LOR_PCG_MAX_BLOCKS, "reduction");
+  if (!rc) rc = alloc(c, &c->red_count, 8, "reduction counters");
   if (!rc) rc = alloc(c, &c->pcg_work, 4 * m.ndof, "pcg work");
   if (!rc && cudaMallocHost((void**)&c->h_scalar, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -259,6 +261,7 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
   m.verts = c->verts;
   cudaError_t e = cudaMemcpyAsync(c->verts, d_vertices, sizeof(double) * 3 * nv, cudaMemcpyDeviceToDevice, S(stream));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), S(stream));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->red_count, 0, 8 * sizeof(unsigned), S(stream));
   if (e == cudaSuccess) e = lor_launch_geometry_check(m, c->T, c->d_status, S(stream));
   int flags = 0;
   if (e == cudaSuccess) {

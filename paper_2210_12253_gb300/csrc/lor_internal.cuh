@@ -64,7 +64,8 @@ struct lor_ctx {
   void* pc_work = nullptr;     // 3 vectors of the smoother dtype
   // PCG work
   double* pcg_work = nullptr;  // r, z, p, Ap: 4 N
-  double* red = nullptr;       // reduction partials + scalars
+  double* red = nullptr;       // reduction partials (LOR_RED_BLOCKS), 16 scalars, 2 x LOR_PCG_MAX_BLOCKS fused-PCG partials
+  unsigned* red_count = nullptr;  // arrival counters of the last-block reductions (kept at 0 between uses)
   double* h_scalar = nullptr;  // pinned host scalars
 };
 
@@ -77,6 +78,7 @@ void lor_count_launch();
 
 // Number of CTAs used by the reduction kernels (multiple of the 152 SMs).
 #define LOR_RED_BLOCKS 608
+#define LOR_PCG_MAX_BLOCKS 2048  // grid cap of the fused PCG reductions (two partials per CTA)
 #define LOR_RED_THREADS 256
 
 // -------------------------------------------------------------------------
@@ -193,6 +195,10 @@ cudaError_t lor_launch_assemble(const LorMesh& m, const LorTables& T, const doub
                                 int dtype, cudaStream_t s);
 cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double* Dq, const double* x, double* y,
                              cudaStream_t s);
+// The apply without its output initialisation: adds A_free x into y (y must
+// already hold x on essential DOFs and 0 elsewhere).
+cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* x,
+                                        double* y, cudaStream_t s);
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* kappa,
                                       const double* x, const double* gy, double* gx, double* gkappa,
                                       cudaStream_t s);
