@@ -61,6 +61,9 @@ enum lor_status {
   LOR_ENOMEM = 3,   /* device allocation failed */
   LOR_ECUDA = 4,    /* CUDA runtime error (message in lor_last_error) */
   LOR_ENOCONV = 5,  /* PCG hit maxit before reaching the tolerance */
+  LOR_ETIMEOUT = 6, /* a bounded device-side wait expired (a bulk copy into shared
+                       memory did not complete within 1 s); results of the
+                       calls since the last check are invalid */
   LOR_ESTATE = 7    /* call out of order (e.g. apply before set_coefficient) */
 };
 
@@ -112,7 +115,9 @@ int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int
 int lor_set_coefficient(lor_ctx* ctx, const double* d_kappa, void* stream);
 
 /* Synchronise the stream and report any error recorded by earlier device
- * work of this context (LOR_EINVAL for a bad coefficient). */
+ * work of this context (LOR_EINVAL for a bad coefficient, LOR_ETIMEOUT when
+ * an SpMV-type kernel gave up waiting for its bulk copy of matrix values;
+ * lor_precond_setup and lor_pcg_solve check the latter themselves). */
 int lor_check(lor_ctx* ctx, void* stream);
 
 /* Step S1.2 / A2: build the CSR sparsity of the LOR matrix (27-point graph of
@@ -154,7 +159,9 @@ int lor_apply_backward(lor_ctx* ctx, const double* d_x, const double* d_gy, doub
 int lor_load_vector(lor_ctx* ctx, const double* d_f, double* d_b, void* stream);
 
 /* y = A_h x with the context's assembled LOR matrix of `dtype` (x, y f64;
- * in LOR_F32 mode x is rounded to f32 and the product accumulated in f32). */
+ * in LOR_F32 mode x is rounded to f32 and the product accumulated in f32).
+ * The kernel reads the CSR values only; the columns of the 27-point pattern
+ * that lor_build_pattern writes are recomputed from the grid. */
 int lor_spmv(lor_ctx* ctx, int dtype, const double* d_x, double* d_y, void* stream);
 
 /* Preconditioner B_h on the context's assembled LOR matrix of `dtype`

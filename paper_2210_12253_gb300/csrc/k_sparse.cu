@@ -10,6 +10,7 @@
 // In the mixed-precision mode the matrix, the diagonal and the smoother's
 // vectors are FP32; PCG's vectors, dot products and recurrences stay FP64.
 #include <math.h>
+#include <string.h>
 
 #include "lor_internal.cuh"
 
@@ -25,64 +26,6 @@ int grid_rows(int64_t n) {
 #define LOR_GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// sum_j A_ij x_j in the matrix precision VT (x converted on the fly), with kLanes lanes per row: lane l takes entries
-// rowptr[i] + l, + 2 kLanes, ... (consecutive lanes read consecutive
-// entries, so a warp reads 32/kLanes row segments of kLanes entries per
-// instruction) and the lanes combine by shuffles; every lane returns the sum.
-// All 32 lanes of the warp must call it (rows past n pass valid = false).
-constexpr int kLanes = 4;
-template <typename VT, typename XT>
-__device__ __forceinline__ VT row_product_lanes(const int64_t* __restrict__ rowptr,
-                                                const int32_t* __restrict__ colidx, const VT* __restrict__ vals,
-                                                const XT* __restrict__ x, int64_t i, bool valid) {
-  VT s = 0;
-  if (valid) {
-    const int lane = threadIdx.x & (kLanes - 1);
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
-    for (int64_t j = b + lane; j < e; j += kLanes) s += vals[j] * (VT)x[colidx[j]];
-  }
-#pragma unroll
-  for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// One (row, lane) per thread; the grid covers all rows exactly.
-#define LOR_ROW_LANES(i, valid, n)                                                        \
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kLanes;            \
-  const bool valid = i < (n);                                                             \
-  const bool lead = valid && (threadIdx.x & (kLanes - 1)) == 0;
-
-unsigned grid_row_lanes(int64_t n) { return (unsigned)((n * kLanes + kThreads - 1) / kThreads); }
-
-template <typename VT>
-__global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                           const VT* __restrict__ vals, VT* __restrict__ dinv) {
-  LOR_GRID_STRIDE(i, n) {
-    VT d = 0;
-    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j)
-      if (colidx[j] == i) d += vals[j];
-    dinv[i] = (VT)1 / d;
-  }
-}
-
-template <typename VT>
-__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                       const VT* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y) {
-  LOR_ROW_LANES(i, valid, n)
-  const VT s = row_product_lanes<VT, double>(rowptr, colidx, vals, x, i, valid);
-  if (lead) y[i] = (double)s;
-}
-
-// w = D^-1 A v (power iteration), FP64 vectors, VT matrix.
-template <typename VT>
-__global__ void k_dinv_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                            const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ v,
-                            double* __restrict__ w) {
-  LOR_ROW_LANES(i, valid, n)
-  const VT s = row_product_lanes<VT, double>(rowptr, colidx, vals, v, i, valid);
-  if (lead) w[i] = (double)(dinv[i] * s);
-}
-
 // Chebyshev step 0 from z_0 = 0: d = z = D^-1 r / theta.  If zout64 is set
 // (degree 1) the result goes straight to the FP64 output.
 template <typename VT>
@@ -95,28 +38,6 @@ __global__ void k_cheb_first(int64_t n, const VT* __restrict__ dinv, const doubl
     } else {
       z[i] = v;
       d[i] = v;
-    }
-  }
-}
-
-// Chebyshev step j >= 1:  res = r - A z_in;  d = c1 d + c2 D^-1 res;
-// z_out = z_in + d (into zout64 as FP64 on the last step).
-template <typename VT>
-__global__ void k_cheb_step(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                            const VT* __restrict__ vals, const VT* __restrict__ dinv, const double* __restrict__ r,
-                            const VT* __restrict__ zin, VT* __restrict__ zout, VT* __restrict__ d, VT c1, VT c2,
-                            double* __restrict__ zout64) {
-  LOR_ROW_LANES(i, valid, n)
-  const VT az = row_product_lanes<VT, VT>(rowptr, colidx, vals, zin, i, valid);
-  if (lead) {
-    const VT res = (VT)r[i] - az;
-    const VT dn = c1 * d[i] + c2 * dinv[i] * res;
-    const VT zn = zin[i] + dn;
-    if (zout64) {
-      zout64[i] = (double)zn;
-    } else {
-      d[i] = dn;
-      zout[i] = zn;
     }
   }
 }
@@ -167,140 +88,6 @@ __global__ void __launch_bounds__(kThreads) k_reduce_final(const double* __restr
   if (threadIdx.x == 0) *out = s;
 }
 
-// ---------------------------------------------------------------- PCG vector kernels
-// Device scalars (slots of ctx->red after the partials).
-enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_COUNT = 5 };
-
-__global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
-                           double* __restrict__ r) {
-  LOR_GRID_STRIDE(i, n) r[i] = b[i] - Ax[i];
-}
-
-template <typename VT>
-cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
-                            cudaStream_t s) {
-  const int64_t n = c->m.ndof;
-  const int g = grid_rows(n);
-  if (c->pc_kind == LOR_PRECOND_JACOBI) {
-    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
-    return cudaGetLastError();
-  }
-  VT* zA = (VT*)c->pc_work;
-  VT* zB = zA + n;
-  VT* d = zB + n;
-  const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
-  const double sigma = theta / delta;
-  const int k = c->pc_degree;
-  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr); lor_count_launch();
-  double rho = 1.0 / sigma;
-  VT* zin = zA;
-  VT* zout = zB;
-  for (int j = 1; j < k; ++j) {
-    const double rho_new = 1.0 / (2.0 * sigma - rho);
-    const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
-    k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
-                                          j == k - 1 ? z : nullptr); lor_count_launch();
-    rho = rho_new;
-    VT* t = zin;
-    zin = zout;
-    zout = t;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t dot_to(lor_ctx* c, const double* a, const double* b, double* out, cudaStream_t s) {
-  k_dot_partial<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(c->m.ndof, a, b, c->red); lor_count_launch();
-  k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, out); lor_count_launch();
-  return cudaGetLastError();
-}
-
-int fail(lor_ctx* c, cudaError_t err, const char* what) {
-  c->err = std::string(what) + ": " + cudaGetErrorString(err);
-  return LOR_ECUDA;
-}
-
-}  // namespace
-
-cudaError_t lor_launch_diag_inv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
-                                int dtype, void* dinv, cudaStream_t s) {
-  if (dtype == LOR_F64) {
-    k_diag_inv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals,
-                                                             (double*)dinv); lor_count_launch();
-  } else {
-    k_diag_inv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals,
-                                                            (float*)dinv); lor_count_launch();
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t lor_launch_spmv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
-                            int dtype, const double* x, double* y, cudaStream_t s) {
-  if (dtype == LOR_F64) {
-    k_spmv<double><<<grid_row_lanes(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const double*)vals, x, y); lor_count_launch();
-  } else {
-    k_spmv<float><<<grid_row_lanes(m.ndof), kThreads, 0, s>>>(m.ndof, rowptr, colidx, (const float*)vals, x, y); lor_count_launch();
-  }
-  return cudaGetLastError();
-}
-
-int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s) {
-  cudaError_t err;
-  if (c->pc_kind == LOR_PRECOND_NONE) {
-    err = cudaMemcpyAsync(z, r, sizeof(double) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
-  } else if (c->pc_dtype == LOR_F64) {
-    err = precond_apply_t<double>(c, c->vals64, c->dinv64, r, z, s);
-  } else {
-    err = precond_apply_t<float>(c, c->vals32, c->dinv32, r, z, s);
-  }
-  return err == cudaSuccess ? LOR_OK : fail(c, err, "precond_apply");
-}
-
-int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s) {
-  const int64_t n = c->m.ndof;
-  double* v = c->pcg_work;
-  double* w = c->pcg_work + n;
-  cudaError_t err;
-  if (v0) {
-    err = cudaMemcpyAsync(v, v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  } else {
-    k_fill<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0); lor_count_launch();
-    err = cudaGetLastError();
-  }
-  if (err != cudaSuccess) return fail(c, err, "power iteration");
-  double* S = c->red + LOR_RED_BLOCKS;
-  double lam = 0.0;
-  for (int it = 0; it < iters; ++it) {
-    if (dtype == LOR_F64) {
-      k_dinv_spmv<double><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals64, c->dinv64, v, w); lor_count_launch();
-    } else {
-      k_dinv_spmv<float><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, c->vals32, c->dinv32, v, w); lor_count_launch();
-    }
-    dot_to(c, w, w, S + 0, s);
-    dot_to(c, v, v, S + 1, s);
-    err = cudaMemcpyAsync(c->h_scalar, S, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-    if (err != cudaSuccess) return fail(c, err, "power iteration");
-    const double nw = sqrt(c->h_scalar[0]), nv = sqrt(c->h_scalar[1]);
-    if (!(nw > 0.0) || !(nv > 0.0)) {
-      c->err = "power iteration: zero vector";
-      return LOR_EINVAL;
-    }
-    lam = nw / nv;
-    // v = w / |w|
-    double* tmp = v;
-    v = w;
-    w = tmp;
-    k_scale<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0 / nw); lor_count_launch();
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return fail(c, err, "power iteration");
-  }
-  *lambda = lam;
-  return LOR_OK;
-}
-
-namespace {
-
-// ---------------------------------------------------------------- fused PCG kernels
 // Each dot product finishes in the last CTA to arrive (arrival counted with
 // an atomic after a fence; that CTA sums the per-CTA partials in index order,
 // so the result does not depend on which CTA finishes last, and resets the
@@ -335,6 +122,450 @@ __device__ __forceinline__ void finish_sums(double s0, double s1, int nsum, doub
   }
 }
 
+
+// ---------------------------------------------------------------- the LOR pattern as a stencil
+// The LOR matrix has the 27-point pattern of the GLL grid (Section 2.1):
+// row i = (I, J, K) holds the columns (I+di, J+dj, K+dk), |d| <= 1, inside
+// the grid, in increasing column order (dk slowest, di fastest), and its
+// first value sits at lor_row_start(I, J, K).  lor_build_pattern writes
+// exactly this pattern as CSR; the kernels below read only the CSR values and
+// recompute each row's columns instead of loading column indices and row
+// pointers (a third of an FP64 SpMV's bytes, half of an FP32 one's).
+//
+// A CTA takes kThreads consecutive rows.  Their values are contiguous in CSR,
+// so the CTA copies the segment into shared memory with 16-byte loads and
+// each thread forms its own row's product from there, in column order; for
+// one offset (di, dj, dk) the rows of a warp read consecutive entries of x.
+// CTAs loop over tiles (a persistent grid), so that the reducing variant can
+// finish its sum in the last CTA.
+
+__device__ __forceinline__ void grid_index(const LorMesh& m, int64_t i, int64_t& I, int64_t& J, int64_t& K) {
+  if (m.ndof <= (int64_t)0xffffffff) {  // 32-bit division where it suffices
+    const uint32_t u = (uint32_t)i, nx = (uint32_t)m.nx, ny = (uint32_t)m.ny;
+    const uint32_t jk = u / nx, k = jk / ny;
+    I = u - jk * nx;
+    J = jk - k * ny;
+    K = k;
+  } else {
+    const int64_t jk = i / m.nx;
+    I = i - jk * m.nx;
+    K = jk / m.ny;
+    J = jk - K * m.ny;
+  }
+}
+
+// First CSR position of row i (nnz for i = N).
+__device__ __forceinline__ int64_t stencil_row_start(const LorMesh& m, int64_t i) {
+  if (i >= m.ndof) return m.nnz;
+  int64_t I, J, K;
+  grid_index(m, i, I, J, K);
+  return lor_row_start(I, J, K, m.nx, m.ny, m.nz);
+}
+
+struct StencilRow {
+  int64_t i, start;
+  bool xm, xp, ym, yp, zm, zp;  // neighbour present below / above on each axis
+};
+
+__device__ __forceinline__ StencilRow stencil_row(const LorMesh& m, int64_t i) {
+  StencilRow r;
+  int64_t I, J, K;
+  grid_index(m, i, I, J, K);
+  r.i = i;
+  r.start = lor_row_start(I, J, K, m.nx, m.ny, m.nz);
+  r.xm = I > 0;
+  r.xp = I < m.nx - 1;
+  r.ym = J > 0;
+  r.yp = J < m.ny - 1;
+  r.zm = K > 0;
+  r.zp = K < m.nz - 1;
+  return r;
+}
+
+// sum_j A_ij x_j from the row's values v[0..) in column order, in the matrix
+// precision VT (x converted on the fly).
+template <typename VT, typename XT>
+__device__ __forceinline__ VT stencil_product(const LorMesh& m, const StencilRow& r, const VT* v,
+                                              const XT* __restrict__ x) {
+  const XT* xc = x + r.i;
+  const int64_t sy = m.nx, sz = m.nx * m.ny;
+  VT s = 0;
+  int k = 0;
+#pragma unroll
+  for (int dk = -1; dk <= 1; ++dk) {
+    const bool vk = dk < 0 ? r.zm : (dk > 0 ? r.zp : true);
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const bool vj = vk && (dj < 0 ? r.ym : (dj > 0 ? r.yp : true));
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const bool ok = vj && (di < 0 ? r.xm : (di > 0 ? r.xp : true));
+        if (ok) {
+          s += v[k] * (VT)xc[di + dj * sy + dk * sz];
+          ++k;
+        }
+      }
+    }
+  }
+  return s;
+}
+
+// ---- TMA staging.  Thread 0 of the CTA copies a tile's value segment into
+// shared memory with one bulk asynchronous copy (cp.async.bulk, completion
+// counted in bytes on an mbarrier); the CTA double-buffers, so the copy of
+// its next tile runs while it computes the current one.  Every wait on an
+// mbarrier is bounded (1 s of %globaltimer); on expiry the CTA records
+// LOR_FLAG_TIMEOUT in the context's status word and stops.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for phase `parity` of bar, at most 1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+
+// Copy bytes (a multiple of 16; both addresses 16-byte aligned) from global
+// src to shared dst, completing on bar, which expects exactly these bytes.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// One tile's buffer: its at most 27 kThreads values plus the slack of
+// starting at the 16-byte boundary below the segment and ending on one.
+// The value arrays carry 16 bytes of padding after nnz for that last round-up.
+template <typename VT>
+constexpr uint32_t tile_bytes() {
+  return (uint32_t)(sizeof(VT) * 27 * kThreads + 16);
+}
+template <typename VT>
+constexpr size_t stencil_smem() {
+  return 2 * (size_t)tile_bytes<VT>();
+}
+
+// Start the copy of tile t's values into buf; returns the CSR position of buf[0].
+template <typename VT>
+__device__ __forceinline__ int64_t issue_tile(const LorMesh& m, const VT* __restrict__ vals, int64_t t, VT* buf,
+                                              uint64_t* bar) {
+  const int64_t r0 = t * kThreads;
+  const int64_t v0 = stencil_row_start(m, r0);
+  const int64_t v1 = stencil_row_start(m, r0 + kThreads < m.ndof ? r0 + kThreads : m.ndof);
+  const int64_t a0 = v0 & ~(int64_t)(16 / sizeof(VT) - 1);
+  const uint32_t bytes = (uint32_t)(((v1 - a0) * (int64_t)sizeof(VT) + 15) & ~(int64_t)15);
+  tma_load_1d(buf, vals + a0, bytes, bar);
+  return a0;
+}
+
+enum StencilMode {
+  ST_SPMV = 0,       // y = A x
+  ST_DINV_SPMV = 1,  // y = D^-1 A x
+  ST_CHEB = 2,       // Chebyshev step: d = c1 d + c2 D^-1 (r - A z_in), z_out = z_in + d (or y = that, FP64)
+  ST_CHEB_DOT = 3    // the same step writing y (FP64) and finishing r.y into *out
+};
+
+template <typename VT, typename XT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __restrict__ vals,
+                                                      const VT* __restrict__ dinv, const XT* __restrict__ x,
+                                                      const double* __restrict__ r, VT* __restrict__ d, VT c1, VT c2,
+                                                      VT* __restrict__ zout, double* __restrict__ y,
+                                                      double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                      double* __restrict__ out, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int64_t base[2];  // CSR position of each buffer's first element
+  __shared__ int abort_flag;
+  VT* buf0 = reinterpret_cast<VT*>(smem_raw);
+  VT* buf1 = reinterpret_cast<VT*>(smem_raw + tile_bytes<VT>());
+  const int64_t ntiles = (m.ndof + kThreads - 1) / kThreads;
+  const int64_t stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+    if ((int64_t)blockIdx.x < ntiles) base[0] = issue_tile<VT>(m, vals, blockIdx.x, buf0, &bar[0]);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += stride, ++it) {
+    const int b = it & 1;
+    // prefetch the next tile into the other buffer (its readers finished at
+    // the barrier that ended the previous iteration)
+    if (threadIdx.x == 0 && t + stride < ntiles)
+      base[b ^ 1] = issue_tile<VT>(m, vals, t + stride, b ? buf0 : buf1, &bar[b ^ 1]);
+    if (!mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const VT* sv = b ? buf1 : buf0;
+    const int64_t i = t * kThreads + threadIdx.x;
+    if (i < m.ndof) {
+      const StencilRow row = stencil_row(m, i);
+      const VT s = stencil_product<VT, XT>(m, row, sv + (row.start - base[b]), x);
+      if constexpr (MODE == ST_SPMV) {
+        y[i] = (double)s;
+      } else if constexpr (MODE == ST_DINV_SPMV) {
+        y[i] = (double)(dinv[i] * s);
+      } else {
+        const double ri = r[i];
+        const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
+        const VT zn = (VT)x[i] + dn;
+        if constexpr (MODE == ST_CHEB_DOT) {
+          y[i] = (double)zn;
+          acc += ri * (double)zn;
+        } else if (y) {
+          y[i] = (double)zn;
+        } else {
+          d[i] = dn;
+          zout[i] = zn;
+        }
+      }
+    }
+    __syncthreads();  // every read of this buffer is done before it is refilled
+  }
+  if (abort_flag && threadIdx.x == 0) {
+    atomicOr(status, LOR_FLAG_TIMEOUT);
+    // let a prefetch that is still in flight land before the CTA exits
+    const int b = it & 1;
+    if (blockIdx.x + (int64_t)(it + 1) * stride < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+  }
+  if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
+}
+
+// Persistent grid: every SM filled to the kernel's occupancy (at most one CTA
+// per tile; the reducing mode at most LOR_PCG_MAX_BLOCKS CTAs).  The shared
+// memory limit is raised once per device.
+template <typename VT, typename XT, int MODE>
+cudaError_t stencil_grid(const LorMesh& m, int* grid) {
+  static int per_device[64] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!per_device[dev]) {
+    err = cudaFuncSetAttribute(k_stencil<VT, XT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stencil_smem<VT>());
+    int sms = 0, occ = 0;
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil<VT, XT, MODE>, kThreads,
+                                                          stencil_smem<VT>());
+    if (err != cudaSuccess) return err;
+    per_device[dev] = sms * (occ > 0 ? occ : 1);
+  }
+  const int64_t ntiles = (m.ndof + kThreads - 1) / kThreads;
+  int64_t g = per_device[dev] < ntiles ? per_device[dev] : ntiles;
+  if (MODE == ST_CHEB_DOT && g > LOR_PCG_MAX_BLOCKS) g = LOR_PCG_MAX_BLOCKS;
+  *grid = (int)(g > 0 ? g : 1);
+  return cudaSuccess;
+}
+
+template <typename VT, typename XT, int MODE>
+cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, const XT* x, const double* r, VT* d,
+                           double c1, double c2, VT* zout, double* y, double* partial, unsigned* counter,
+                           double* out, int* status, cudaStream_t s) {
+  int grid = 0;
+  cudaError_t err = stencil_grid<VT, XT, MODE>(m, &grid);
+  if (err != cudaSuccess) return err;
+  k_stencil<VT, XT, MODE><<<grid, kThreads, stencil_smem<VT>(), s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y,
+                                                                    partial, counter, out, status); lor_count_launch();
+  return cudaGetLastError();
+}
+
+// D^-1 from the diagonal entries (closed-form positions).
+template <typename VT>
+__global__ void k_diag_inv(LorMesh m, const VT* __restrict__ vals, VT* __restrict__ dinv) {
+  LOR_GRID_STRIDE(i, m.ndof) {
+    int64_t I, J, K;
+    grid_index(m, i, I, J, K);
+    dinv[i] = (VT)1 / vals[lor_entry_pos(I, J, K, 0, 0, 0, m.nx, m.ny, m.nz)];
+  }
+}
+
+// One Chebyshev step j >= 1 (see ST_CHEB); the last one writes z64.
+template <typename VT>
+cudaError_t cheb_step(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, const VT* zin, VT* zout, VT* d,
+                      double c1, double c2, double* z64, cudaStream_t s) {
+  return launch_stencil<VT, VT, ST_CHEB>(c->m, vals, dinv, zin, r, d, c1, c2, zout, z64, nullptr, nullptr, nullptr,
+                                         c->d_status, s);
+}
+
+// ---------------------------------------------------------------- PCG vector kernels
+// Device scalars (slots of ctx->red after the partials).
+enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_COUNT = 5 };
+
+__global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
+                           double* __restrict__ r) {
+  LOR_GRID_STRIDE(i, n) r[i] = b[i] - Ax[i];
+}
+
+template <typename VT>
+cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
+                            cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  const int g = grid_rows(n);
+  if (c->pc_kind == LOR_PRECOND_JACOBI) {
+    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
+    return cudaGetLastError();
+  }
+  VT* zA = (VT*)c->pc_work;
+  VT* zB = zA + n;
+  VT* d = zB + n;
+  const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
+  const double sigma = theta / delta;
+  const int k = c->pc_degree;
+  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr); lor_count_launch();
+  double rho = 1.0 / sigma;
+  VT* zin = zA;
+  VT* zout = zB;
+  for (int j = 1; j < k; ++j) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+    const cudaError_t err = cheb_step<VT>(c, vals, dinv, r, zin, zout, d, c1, c2, j == k - 1 ? z : nullptr, s);
+    if (err != cudaSuccess) return err;
+    rho = rho_new;
+    VT* t = zin;
+    zin = zout;
+    zout = t;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t dot_to(lor_ctx* c, const double* a, const double* b, double* out, cudaStream_t s) {
+  k_dot_partial<<<LOR_RED_BLOCKS, kThreads, 0, s>>>(c->m.ndof, a, b, c->red); lor_count_launch();
+  k_reduce_final<<<1, kThreads, 0, s>>>(c->red, LOR_RED_BLOCKS, out); lor_count_launch();
+  return cudaGetLastError();
+}
+
+int fail(lor_ctx* c, cudaError_t err, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(err);
+  return LOR_ECUDA;
+}
+
+// The status word rides along with each synchronising scalar read (into the
+// last pinned slot); a set LOR_FLAG_TIMEOUT ends the solve.
+double* status_slot(lor_ctx* c) { return c->h_scalar + 15; }
+cudaError_t queue_status_read(lor_ctx* c, cudaStream_t s) {
+  return cudaMemcpyAsync(status_slot(c), c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+int timed_out(lor_ctx* c, const char* what) {
+  int flags = 0;
+  memcpy(&flags, status_slot(c), sizeof(int));
+  if (!(flags & LOR_FLAG_TIMEOUT)) return LOR_OK;
+  c->err = std::string(what) + ": a bounded device wait expired (a bulk copy into shared memory never completed)";
+  return LOR_ETIMEOUT;
+}
+
+}  // namespace
+
+cudaError_t lor_launch_diag_inv(const LorMesh& m, const void* vals, int dtype, void* dinv, cudaStream_t s) {
+  if (dtype == LOR_F64) {
+    k_diag_inv<double><<<grid_rows(m.ndof), kThreads, 0, s>>>(m, (const double*)vals, (double*)dinv); lor_count_launch();
+  } else {
+    k_diag_inv<float><<<grid_rows(m.ndof), kThreads, 0, s>>>(m, (const float*)vals, (float*)dinv); lor_count_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_spmv(const LorMesh& m, const void* vals, int dtype, const double* x, double* y, int* status,
+                            cudaStream_t s) {
+  if (dtype == LOR_F64)
+    return launch_stencil<double, double, ST_SPMV>(m, (const double*)vals, nullptr, x, nullptr, nullptr, 0.0, 0.0,
+                                                   nullptr, y, nullptr, nullptr, nullptr, status, s);
+  return launch_stencil<float, double, ST_SPMV>(m, (const float*)vals, nullptr, x, nullptr, nullptr, 0.0, 0.0, nullptr,
+                                                y, nullptr, nullptr, nullptr, status, s);
+}
+
+int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s) {
+  cudaError_t err;
+  if (c->pc_kind == LOR_PRECOND_NONE) {
+    err = cudaMemcpyAsync(z, r, sizeof(double) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
+  } else if (c->pc_dtype == LOR_F64) {
+    err = precond_apply_t<double>(c, c->vals64, c->dinv64, r, z, s);
+  } else {
+    err = precond_apply_t<float>(c, c->vals32, c->dinv32, r, z, s);
+  }
+  return err == cudaSuccess ? LOR_OK : fail(c, err, "precond_apply");
+}
+
+int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s) {
+  const int64_t n = c->m.ndof;
+  double* v = c->pcg_work;
+  double* w = c->pcg_work + n;
+  cudaError_t err;
+  if (v0) {
+    err = cudaMemcpyAsync(v, v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  } else {
+    k_fill<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0); lor_count_launch();
+    err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) return fail(c, err, "power iteration");
+  double* S = c->red + LOR_RED_BLOCKS;
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    err = dtype == LOR_F64
+              ? launch_stencil<double, double, ST_DINV_SPMV>(c->m, c->vals64, c->dinv64, v, nullptr, nullptr, 0.0, 0.0,
+                                                             nullptr, w, nullptr, nullptr, nullptr, c->d_status, s)
+              : launch_stencil<float, double, ST_DINV_SPMV>(c->m, c->vals32, c->dinv32, v, nullptr, nullptr, 0.0, 0.0,
+                                                            nullptr, w, nullptr, nullptr, nullptr, c->d_status, s);
+    if (err != cudaSuccess) return fail(c, err, "power iteration");
+    dot_to(c, w, w, S + 0, s);
+    dot_to(c, v, v, S + 1, s);
+    err = cudaMemcpyAsync(c->h_scalar, S, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = queue_status_read(c, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return fail(c, err, "power iteration");
+    if (int rc = timed_out(c, "power iteration")) return rc;
+    const double nw = sqrt(c->h_scalar[0]), nv = sqrt(c->h_scalar[1]);
+    if (!(nw > 0.0) || !(nv > 0.0)) {
+      c->err = "power iteration: zero vector";
+      return LOR_EINVAL;
+    }
+    lam = nw / nv;
+    // v = w / |w|
+    double* tmp = v;
+    v = w;
+    w = tmp;
+    k_scale<<<grid_rows(n), kThreads, 0, s>>>(v, n, 1.0 / nw); lor_count_launch();
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return fail(c, err, "power iteration");
+  }
+  *lambda = lam;
+  return LOR_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- fused PCG kernels
 __global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const double* __restrict__ a,
                                                       const double* __restrict__ b, double* __restrict__ partial,
                                                       unsigned* __restrict__ counter, double* __restrict__ out) {
@@ -381,36 +612,6 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double
   finish_sums(srr, srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz);
 }
 
-// Last Chebyshev step fused with r.z: z = z_in + (c1 d + c2 D^-1 (r - A z_in))
-// written as FP64, and the partial sums of r.z.  kLanes lanes per row; every
-// warp runs the same number of row rounds so that its shuffles stay uniform.
-template <typename VT>
-__global__ void __launch_bounds__(kThreads) k_pcg_cheb_last(int64_t n, const int64_t* __restrict__ rowptr,
-                                                            const int32_t* __restrict__ colidx,
-                                                            const VT* __restrict__ vals, const VT* __restrict__ dinv,
-                                                            const double* __restrict__ r,
-                                                            const VT* __restrict__ zin, const VT* __restrict__ d,
-                                                            VT c1, VT c2, double* __restrict__ z,
-                                                            double* __restrict__ partial,
-                                                            unsigned* __restrict__ counter, double* __restrict__ out) {
-  const int64_t rows_per_round = (int64_t)gridDim.x * blockDim.x / kLanes;
-  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kLanes;
-  const int group = (threadIdx.x & 31) / kLanes;
-  double srz = 0.0;
-  for (int64_t base = warp_first; base < n; base += rows_per_round) {
-    const int64_t i = base + group;
-    const bool valid = i < n;
-    const VT az = row_product_lanes<VT, VT>(rowptr, colidx, vals, zin, i, valid);
-    if (valid && (threadIdx.x & (kLanes - 1)) == 0) {
-      const double ri = r[i];
-      const VT zn = zin[i] + (c1 * d[i] + c2 * dinv[i] * ((VT)ri - az));
-      z[i] = (double)zn;
-      srz += ri * (double)zn;
-    }
-  }
-  finish_sums(srz, 0.0, 1, partial, counter, out, nullptr);
-}
-
 // p = z + beta p (beta = rz_new / rz_old; first: p = z) and the output of
 // the next apply initialised: q = p on essential DOFs, 0 elsewhere.
 __global__ void k_pcg_direction(LorMesh m, const double* __restrict__ S, int new_slot, int old_slot, int first,
@@ -441,7 +642,7 @@ int pcg_grid(K kernel) {
 
 template <typename VT>
 cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
-                             double* out_rz, int grid, cudaStream_t s) {
+                             double* out_rz, cudaStream_t s) {
   // Chebyshev steps 1 .. k-1 after k_pcg_update's step 0 (degree >= 2)
   const int64_t n = c->m.ndof;
   VT* zA = (VT*)c->pc_work;
@@ -457,11 +658,13 @@ cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const d
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
     if (j < k - 1) {
-      k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d,
-                                                            (VT)c1, (VT)c2, nullptr); lor_count_launch();
+      const cudaError_t err = cheb_step<VT>(c, vals, dinv, r, zin, zout, d, c1, c2, nullptr, s);
+      if (err != cudaSuccess) return err;
     } else {
-      k_pcg_cheb_last<VT><<<grid, kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, d, (VT)c1,
-                                                        (VT)c2, z, pcg_partials(c), c->red_count, out_rz); lor_count_launch();
+      const cudaError_t err = launch_stencil<VT, VT, ST_CHEB_DOT>(c->m, vals, dinv, zin, r, d, c1, c2, nullptr, z,
+                                                                  pcg_partials(c), c->red_count, out_rz, c->d_status,
+                                                                  s);
+      if (err != cudaSuccess) return err;
     }
     rho = rho_new;
     VT* t = zin;
@@ -500,7 +703,6 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
   const int mode = c->pc_kind == LOR_PRECOND_NONE ? 0 : c->pc_kind == LOR_PRECOND_JACOBI ? 1 : c->pc_degree == 1 ? 2 : 3;
   const int g_dot = pcg_grid(k_pcg_dot);
   const int g_upd = f64 ? pcg_grid(k_pcg_update<double>) : pcg_grid(k_pcg_update<float>);
-  const int g_last = f64 ? pcg_grid(k_pcg_cheb_last<double>) : pcg_grid(k_pcg_cheb_last<float>);
   auto dot = [&](const double* a, const double* bb, double* out) {
     k_pcg_dot<<<g_dot, kThreads, 0, s>>>(n, a, bb, pcg_partials(c), c->red_count, out); lor_count_launch();
   };
@@ -532,8 +734,10 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
       err = f64 ? pcg_update<double>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s)
                 : pcg_update<float>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s);
       if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = queue_status_read(c, s);
       if (err == cudaSuccess) err = cudaStreamSynchronize(s);
       if (err != cudaSuccess) return fail(c, err, "pcg");
+      if (int trc = timed_out(c, "pcg")) return trc;
       ++it;
       rel = sqrt(hs[0]) / nb;
       bool restarted = false;
@@ -559,8 +763,8 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
         restarted = true;
       }
       if (!restarted && mode == 3) {
-        err = f64 ? pcg_precond_rest<double>(c, c->vals64, c->dinv64, r, z, S + nxt, g_last, s)
-                  : pcg_precond_rest<float>(c, c->vals32, c->dinv32, r, z, S + nxt, g_last, s);
+        err = f64 ? pcg_precond_rest<double>(c, c->vals64, c->dinv64, r, z, S + nxt, s)
+                  : pcg_precond_rest<float>(c, c->vals32, c->dinv32, r, z, S + nxt, s);
         if (err != cudaSuccess) return fail(c, err, "pcg precond");
       }
       k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q); lor_count_launch();
@@ -647,8 +851,8 @@ cudaError_t precond_apply_noalloc_t(lor_ctx* c, const VT* vals, const VT* dinv, 
   for (int j = 1; j < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
-    k_cheb_step<VT><<<grid_row_lanes(n), kThreads, 0, s>>>(n, c->rowptr, c->colidx, vals, dinv, r, zin, zout, d, (VT)c1, (VT)c2,
-                                          j == k - 1 ? z : nullptr); lor_count_launch();
+    const cudaError_t err = cheb_step<VT>(c, vals, dinv, r, zin, zout, d, c1, c2, j == k - 1 ? z : nullptr, s);
+    if (err != cudaSuccess) return err;
     rho = rho_new;
     VT* t = zin;
     zin = zout;

@@ -324,6 +324,8 @@ int lor_check(lor_ctx* c, void* stream) {
   if (flags) {
     cudaMemsetAsync(c->d_status, 0, sizeof(int), S(stream));
     cudaStreamSynchronize(S(stream));
+    if (flags & LOR_FLAG_TIMEOUT)
+      return set_err(c, LOR_ETIMEOUT, "a bounded device wait expired (a bulk copy into shared memory never completed)");
     if (flags & LOR_FLAG_BAD_GEOM) return set_err(c, LOR_EGEOM, "a Jacobian determinant is <= 0");
     return set_err(c, LOR_EINVAL, "kappa must be finite and > 0 at every Gauss point");
   }
@@ -359,7 +361,8 @@ int lor_assemble(lor_ctx* c, void* d_values, int dtype, void* stream) {
   void* out = d_values;
   if (!out) {
     if (!c->have_pattern) return set_err(c, LOR_ESTATE, "lor_assemble: call lor_build_pattern first");
-    int rc = dtype == LOR_F64 ? alloc(c, &c->vals64, c->m.nnz, "values f64") : alloc(c, &c->vals32, c->m.nnz, "values f32");
+    int rc = dtype == LOR_F64 ? alloc(c, &c->vals64, c->m.nnz + LOR_VALS_PAD, "values f64")
+                                : alloc(c, &c->vals32, c->m.nnz + LOR_VALS_PAD, "values f32");
     if (rc) return rc;
     out = dtype == LOR_F64 ? (void*)c->vals64 : (void*)c->vals32;
   }
@@ -402,8 +405,8 @@ int lor_spmv(lor_ctx* c, int dtype, const double* d_x, double* d_y, void* stream
   if (!d_x || !d_y || d_x == d_y) return set_err(c, LOR_EINVAL, "lor_spmv: x, y must be distinct device arrays");
   const bool have = dtype == LOR_F64 ? c->have_vals64 : dtype == LOR_F32 ? c->have_vals32 : false;
   if (!have) return set_err(c, LOR_ESTATE, "lor_spmv: no assembled matrix of that dtype in the context");
-  cudaError_t e = lor_launch_spmv(c->m, c->rowptr, c->colidx, dtype == LOR_F64 ? (const void*)c->vals64 : (const void*)c->vals32,
-                                  dtype, d_x, d_y, S(stream));
+  cudaError_t e = lor_launch_spmv(c->m, dtype == LOR_F64 ? (const void*)c->vals64 : (const void*)c->vals32, dtype, d_x,
+                                  d_y, c->d_status, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_spmv");
 }
 
@@ -430,8 +433,7 @@ int lor_precond_setup(lor_ctx* c, int kind, int dtype, int degree, double lo_rat
     rc = alloc(c, (char**)&c->pc_work, 3 * n * (dtype == LOR_F64 ? 8 : 4), "smoother work");
   }
   if (rc) return rc;
-  cudaError_t e = lor_launch_diag_inv(c->m, c->rowptr, c->colidx,
-                                      dtype == LOR_F64 ? (const void*)c->vals64 : (const void*)c->vals32, dtype,
+  cudaError_t e = lor_launch_diag_inv(c->m, dtype == LOR_F64 ? (const void*)c->vals64 : (const void*)c->vals32, dtype,
                                       dtype == LOR_F64 ? (void*)c->dinv64 : (void*)c->dinv32, S(stream));
   if (e != cudaSuccess) return cuda_err(c, e, "lor_precond_setup");
   c->pc_kind = kind;

@@ -75,6 +75,11 @@ void lor_count_launch();
 // Device error flags (bit mask in ctx->d_status[0]).
 #define LOR_FLAG_BAD_KAPPA 1
 #define LOR_FLAG_BAD_GEOM 2
+#define LOR_FLAG_TIMEOUT 4  // a bounded wait on an mbarrier expired (a TMA copy never completed)
+
+// Elements of padding after the nnz CSR values of the context's value arrays
+// (a tile's bulk copy may end up to 15 bytes past the last value).
+#define LOR_VALS_PAD 4
 
 // Number of CTAs used by the reduction kernels (multiple of the 152 SMs).
 #define LOR_RED_BLOCKS 608
@@ -203,10 +208,13 @@ cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, cons
                                       const double* x, const double* gy, double* gx, double* gkappa,
                                       cudaStream_t s);
 // sparse / solver kernels (k_sparse.cu)
-cudaError_t lor_launch_diag_inv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
-                                int dtype, void* dinv, cudaStream_t s);
-cudaError_t lor_launch_spmv(const LorMesh& m, const int64_t* rowptr, const int32_t* colidx, const void* vals,
-                            int dtype, const double* x, double* y, cudaStream_t s);
+// The SpMV-type kernels read the CSR values only: the columns and row starts
+// of the 27-point LOR pattern are recomputed from the grid (the pattern
+// lor_launch_pattern writes).  Value arrays must be 16-byte aligned and padded
+// by LOR_VALS_PAD elements; a TMA wait that expires sets LOR_FLAG_TIMEOUT.
+cudaError_t lor_launch_diag_inv(const LorMesh& m, const void* vals, int dtype, void* dinv, cudaStream_t s);
+cudaError_t lor_launch_spmv(const LorMesh& m, const void* vals, int dtype, const double* x, double* y, int* status,
+                            cudaStream_t s);
 int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s);
 int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s);
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,

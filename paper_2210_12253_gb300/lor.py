@@ -12,7 +12,7 @@ import torch
 
 from .build import LIB
 
-LOR_OK, LOR_EINVAL, LOR_EGEOM, LOR_ENOMEM, LOR_ECUDA, LOR_ENOCONV, LOR_ESTATE = 0, 1, 2, 3, 4, 5, 7
+LOR_OK, LOR_EINVAL, LOR_EGEOM, LOR_ENOMEM, LOR_ECUDA, LOR_ENOCONV, LOR_ETIMEOUT, LOR_ESTATE = 0, 1, 2, 3, 4, 5, 6, 7
 LOR_F64, LOR_F32 = 0, 1
 LOR_PRECOND_NONE, LOR_PRECOND_JACOBI, LOR_PRECOND_CHEB = 0, 1, 2
 LOR_MAX_P = 10
