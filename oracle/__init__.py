@@ -44,22 +44,22 @@ def _declare(L):
         "orc_basis_1d": (i, [i, i, _dp, _dp]),
         "orc_geometry": (i, [i, i, i, _dp, i, _dp, _dp]),
         "orc_dof_coordinates": (i, [i, i, i, _dp, i, _dp]),
-        "orc_ho_apply": (i, [i, i, i, _dp, i, i, _dp, _dp, _dp, i]),
-        "orc_ho_apply_backward": (i, [i, i, i, _dp, i, i, _dp, _dp, _dp, vp, vp]),
+        "orc_ho_apply": (i, [i, i, i, _dp, i, i, _dp, vp, _dp, _dp, i]),
+        "orc_ho_apply_backward": (i, [i, i, i, _dp, i, i, _dp, vp, _dp, _dp, vp, vp]),
         "orc_load_vector": (i, [i, i, i, _dp, i, i, vp, _dp]),
-        "orc_dense_general": (i, [i64, i, i, _dp, _i64p, _dp, i64, _dp]),
+        "orc_dense_general": (i, [i64, i, i, _dp, _i64p, _dp, vp, i64, _dp]),
         "orc_lor_kappa_sub": (i, [i, i, i64, _dp, _dp]),
-        "orc_lor_assemble": (vp, [i, i, i, _dp, i, i, _dp, i, C.POINTER(i)]),
+        "orc_lor_assemble": (vp, [i, i, i, _dp, i, i, _dp, vp, i, C.POINTER(i)]),
         "orc_csr_nnz": (i64, [vp]),
         "orc_csr_n": (i64, [vp]),
         "orc_csr_copy": (None, [vp, _i64p, _i64p, _dp]),
         "orc_csr_free": (None, [vp]),
-        "orc_lor_rows": (i, [i, i, i, _dp, i, i, _dp, i, i64, _i64p, i, _i32p, _i64p, _dp]),
+        "orc_lor_rows": (i, [i, i, i, _dp, i, i, _dp, vp, i, i64, _i64p, i, _i32p, _i64p, _dp]),
         "orc_csr_spmv": (None, [i64, _i64p, _i64p, _dp, _dp, _dp]),
         "orc_csr_diagonal": (None, [i64, _i64p, _i64p, _dp, _dp]),
         "orc_power_lambda_max": (d, [i64, _i64p, _i64p, _dp, _dp, i]),
         "orc_chebyshev": (None, [i64, _i64p, _i64p, _dp, vp, i, d, d, _dp, _dp]),
-        "orc_pcg": (i, [i, i, i, _dp, i, i, _dp, _i64p, _i64p, _dp, i, i, d, d,
+        "orc_pcg": (i, [i, i, i, _dp, i, i, _dp, vp, _i64p, _i64p, _dp, i, i, d, d,
                         _dp, _dp, d, i, C.POINTER(i), C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
@@ -88,6 +88,16 @@ def _f64(a):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _opt(a, n=None):
+    """Optional coefficient array (None stays None): contiguous f64, flattened."""
+    if a is None:
+        return None
+    a = _f64(a).ravel()
+    if n is not None:
+        assert a.size == n
+    return a
 
 
 # ---------------------------------------------------------------- 1D rules
@@ -152,16 +162,20 @@ def dof_coordinates(mesh, p):
 
 
 # ---------------------------------------------------------------- HO operator
-def ho_apply(mesh, p, q, kappa, x, dirichlet=True):
+def ho_apply(mesh, p, q, kappa, x, dirichlet=True, beta=None):
+    """y = A_p x; beta (reaction coefficient at the Gauss points) adds the mass term."""
     y = np.zeros(mesh.ndof(p))
-    _check(lib().orc_ho_apply(*mesh.args(), p, q, _f64(kappa).ravel(), _f64(x), y, int(dirichlet)), "ho_apply")
+    b = _opt(beta, mesh.nel * q ** 3)
+    _check(lib().orc_ho_apply(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(b), _f64(x), y, int(dirichlet)),
+           "ho_apply")
     return y
 
 
-def ho_apply_backward(mesh, p, q, kappa, x, gy, want_gx=True, want_gkappa=True):
+def ho_apply_backward(mesh, p, q, kappa, x, gy, want_gx=True, want_gkappa=True, beta=None):
     gx = np.zeros(mesh.ndof(p)) if want_gx else None
     gk = np.zeros((mesh.nel, q ** 3)) if want_gkappa else None
-    _check(lib().orc_ho_apply_backward(*mesh.args(), p, q, _f64(kappa).ravel(), _f64(x), _f64(gy),
+    b = _opt(beta, mesh.nel * q ** 3)
+    _check(lib().orc_ho_apply_backward(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(b), _f64(x), _f64(gy),
                                        _ptr(gx), _ptr(gk)), "ho_apply_backward")
     return gx, gk
 
@@ -173,14 +187,15 @@ def load_vector(mesh, p, q, f=None):
     return b
 
 
-def dense_general(corners, dofs, kappa, p, q, N):
-    """Brute-force dense stiffness matrix on a general hex mesh."""
+def dense_general(corners, dofs, kappa, p, q, N, beta=None):
+    """Brute-force dense stiffness (+ beta-weighted mass) matrix on a general hex mesh."""
     corners = _f64(corners).reshape(-1, 8, 3)
     nel = corners.shape[0]
     dofs = np.ascontiguousarray(dofs, dtype=np.int64).reshape(nel, (p + 1) ** 3)
     kappa = _f64(kappa).reshape(nel, q ** 3)
+    b = _opt(beta, nel * q ** 3)
     A = np.zeros((N, N))
-    _check(lib().orc_dense_general(nel, p, q, corners, dofs, kappa, N, A), "dense_general")
+    _check(lib().orc_dense_general(nel, p, q, corners, dofs, kappa, _ptr(b), N, A), "dense_general")
     return A
 
 
@@ -193,10 +208,11 @@ def lor_kappa_sub(p, q, kappa):
     return ks
 
 
-def lor_assemble(mesh, p, q, kappa, dirichlet=True):
-    """Full LOR CSR (rowptr int64, colidx int64, values f64)."""
+def lor_assemble(mesh, p, q, kappa, dirichlet=True, beta=None):
+    """Full LOR CSR (rowptr int64, colidx int64, values f64); beta adds the LOR mass blocks."""
     st = C.c_int(0)
-    h = lib().orc_lor_assemble(*mesh.args(), p, q, _f64(kappa).ravel(), int(dirichlet), C.byref(st))
+    b = _opt(beta, mesh.nel * q ** 3)
+    h = lib().orc_lor_assemble(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(b), int(dirichlet), C.byref(st))
     if not h:
         raise OracleError(st.value, "lor_assemble")
     try:
@@ -209,7 +225,7 @@ def lor_assemble(mesh, p, q, kappa, dirichlet=True):
     return rowptr, colidx, values
 
 
-def lor_rows(mesh, p, q, kappa, rows, dirichlet=True, cap=64):
+def lor_rows(mesh, p, q, kappa, rows, dirichlet=True, cap=64, beta=None):
     """Selected rows of the LOR matrix, each computed from its own sub-hexes.
     Returns (counts int32[n], cols int64[n, cap], vals f64[n, cap])."""
     rows = np.ascontiguousarray(rows, dtype=np.int64)
@@ -217,7 +233,8 @@ def lor_rows(mesh, p, q, kappa, rows, dirichlet=True, cap=64):
     counts = np.zeros(n, np.int32)
     cols = np.zeros((n, cap), np.int64)
     vals = np.zeros((n, cap))
-    _check(lib().orc_lor_rows(*mesh.args(), p, q, _f64(kappa).ravel(), int(dirichlet), n, rows, cap,
+    b = _opt(beta, mesh.nel * q ** 3)
+    _check(lib().orc_lor_rows(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(b), int(dirichlet), n, rows, cap,
                               counts, cols, vals), "lor_rows")
     return counts, cols, vals
 
@@ -258,12 +275,13 @@ PRECOND_NONE, PRECOND_JACOBI, PRECOND_CHEB = 0, 1, 2
 
 
 def pcg(mesh, p, q, kappa, csr, b, rtol, maxit, precond=PRECOND_CHEB, cheb_k=3, lo=0.0, hi=1.0,
-        raise_on_noconv=True):
+        raise_on_noconv=True, beta=None):
     """Returns (x, iterations, final relative residual, status)."""
     rp, ci, v = _csr(*csr)
     x = np.zeros(mesh.ndof(p))
     it, rel = C.c_int(0), C.c_double(0.0)
-    rc = lib().orc_pcg(*mesh.args(), p, q, _f64(kappa).ravel(), rp, ci, v, int(precond), int(cheb_k),
+    bt = _opt(beta, mesh.nel * q ** 3)
+    rc = lib().orc_pcg(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(bt), rp, ci, v, int(precond), int(cheb_k),
                        float(lo), float(hi), _f64(b), x, float(rtol), int(maxit), C.byref(it), C.byref(rel))
     if rc not in (OK, ENOCONV) or (raise_on_noconv and rc != OK):
         raise OracleError(rc, "pcg")

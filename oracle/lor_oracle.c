@@ -304,6 +304,8 @@ static int is_essential(int64_t I, int64_t J, int64_t K, int64_t nx, int64_t ny,
 /* single rank), by sum factorisation with the 1D factors B_1D and D_1D.       */
 /* B = [B (x) B (x) D ; B (x) D (x) B ; D (x) B (x) B] in 3D (Step S2.1), with */
 /* D at each point = kappa * w detJ J^-1 J^-T (Step S1.1).                     */
+/* beta != NULL adds the reaction (mass) term of the definite Helmholtz       */
+/* problem of Section 4.1: B_m^T (beta w detJ) B_m with B_m = B (x) B (x) B.    */
 /* If dirichlet != 0: x is taken as zero on essential DOFs on the input side,  */
 /* no result is accumulated into essential rows, and y_ess = x_ess.            */
 /* ------------------------------------------------------------------------- */
@@ -404,6 +406,64 @@ static void element_reference_gradient_transpose(int n, int q, const double* B, 
   free(T0); free(T1); free(T2); free(U0); free(U1);
 }
 
+/* Values of the element field at every Gauss point, val[g] = ((B (x) B (x) B) u)_g:
+ * the basis operator of the mass matrix (Section 3, Step S2.1: B is the
+ * Kronecker product of the 1D evaluation matrix). */
+static void element_values(int n, int q, const double* B, const double* u, double* val) {
+  double* T1 = (double*)malloc(sizeof(double) * n * n * q);
+  double* T2 = (double*)malloc(sizeof(double) * n * q * q);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int g0 = 0; g0 < q; ++g0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += B[g0 * n + i] * u[(k * n + j) * n + i];
+        T1[(k * n + j) * q + g0] = s;
+      }
+  for (int k = 0; k < n; ++k)
+    for (int g1 = 0; g1 < q; ++g1)
+      for (int g0 = 0; g0 < q; ++g0) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += B[g1 * n + j] * T1[(k * n + j) * q + g0];
+        T2[(k * q + g1) * q + g0] = s;
+      }
+  for (int g2 = 0; g2 < q; ++g2)
+    for (int g1 = 0; g1 < q; ++g1)
+      for (int g0 = 0; g0 < q; ++g0) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += B[g2 * n + k] * T2[(k * q + g1) * q + g0];
+        val[(g2 * q + g1) * q + g0] = s;
+      }
+  free(T1); free(T2);
+}
+
+/* Transpose of element_values, accumulated: y[k][j][i] += ((B (x) B (x) B)^T v)_{ijk}. */
+static void element_values_transpose_add(int n, int q, const double* B, const double* v, double* y) {
+  double* T2 = (double*)malloc(sizeof(double) * n * q * q);
+  double* T1 = (double*)malloc(sizeof(double) * n * n * q);
+  for (int k = 0; k < n; ++k)
+    for (int g1 = 0; g1 < q; ++g1)
+      for (int g0 = 0; g0 < q; ++g0) {
+        double s = 0.0;
+        for (int g2 = 0; g2 < q; ++g2) s += B[g2 * n + k] * v[(g2 * q + g1) * q + g0];
+        T2[(k * q + g1) * q + g0] = s;
+      }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int g0 = 0; g0 < q; ++g0) {
+        double s = 0.0;
+        for (int g1 = 0; g1 < q; ++g1) s += B[g1 * n + j] * T2[(k * q + g1) * q + g0];
+        T1[(k * n + j) * q + g0] = s;
+      }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int g0 = 0; g0 < q; ++g0) s += B[g0 * n + i] * T1[(k * n + j) * q + g0];
+        y[(k * n + j) * n + i] += s;
+      }
+  free(T1); free(T2);
+}
+
 static void gather_element(int64_t nx, int64_t ny, int64_t nz, int p, int ex, int ey, int ez, const double* x, int dirichlet, double* xe) {
   int n = p + 1;
   for (int k = 0; k < n; ++k)
@@ -416,7 +476,8 @@ static void gather_element(int64_t nx, int64_t ny, int64_t nz, int p, int ex, in
       }
 }
 
-int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* x, double* y, int dirichlet) {
+int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
+                 const double* x, double* y, int dirichlet) {
   if (p < 1 || q < 1 || p + 1 > ORC_MAXN || q > ORC_MAXN) return ORC_EINVAL;
   int n = p + 1, nq3 = q * q * q;
   int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
@@ -425,11 +486,15 @@ int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const
   double* D = (double*)malloc(sizeof(double) * q * n);
   orc_basis_1d(p, q, B, D);
   double* G = (double*)malloc(sizeof(double) * nel * nq3 * 6);
-  int rc = orc_geometry(nex, ney, nez, V, q, NULL, G);
-  if (rc) { free(B); free(D); free(G); return rc; }
+  double* detJ = beta ? (double*)malloc(sizeof(double) * nel * nq3) : NULL;
+  int rc = orc_geometry(nex, ney, nez, V, q, detJ, G);
+  if (rc) { free(B); free(D); free(G); free(detJ); return rc; }
+  double xg[ORC_MAXN], wg[ORC_MAXN];
+  orc_gauss_legendre(q, xg, wg);
   double* xe = (double*)malloc(sizeof(double) * n * n * n);
   double* ye = (double*)malloc(sizeof(double) * n * n * n);
   double* gr = (double*)malloc(sizeof(double) * 3 * nq3);
+  double* val = (double*)malloc(sizeof(double) * nq3);
   for (int64_t i = 0; i < N; ++i) y[i] = 0.0;
   for (int ez = 0; ez < nez; ++ez)
     for (int ey = 0; ey < ney; ++ey)
@@ -446,6 +511,16 @@ int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const
           gr[3 * g + 2] = k * (Gq[2] * a + Gq[4] * b + Gq[5] * c);
         }
         element_reference_gradient_transpose(n, q, B, D, gr, ye);      /* B^T */
+        if (beta) {                                                    /* reaction: B^T (beta w detJ) B */
+          element_values(n, q, B, xe, val);
+          for (int g2 = 0; g2 < q; ++g2)
+            for (int g1 = 0; g1 < q; ++g1)
+              for (int g0 = 0; g0 < q; ++g0) {
+                int g = (g2 * q + g1) * q + g0;
+                val[g] *= beta[e * nq3 + g] * wg[g0] * wg[g1] * wg[g2] * detJ[e * nq3 + g];
+              }
+          element_values_transpose_add(n, q, B, val, ye);
+        }
         for (int k = 0; k < n; ++k)                                    /* G^T */
           for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
@@ -459,7 +534,7 @@ int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const
       for (int64_t J = 0; J < ny; ++J)
         for (int64_t I = 0; I < nx; ++I)
           if (is_essential(I, J, K, nx, ny, nz)) y[I + nx * (J + ny * K)] = x[I + nx * (J + ny * K)];
-  free(B); free(D); free(G); free(xe); free(ye); free(gr);
+  free(B); free(D); free(G); free(detJ); free(xe); free(ye); free(gr); free(val);
   return ORC_OK;
 }
 
@@ -469,10 +544,12 @@ int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const
  *   gkappa[e][g] = (grad_ref x)^T G_g (grad_ref gy) at Gauss point g, with
  *                  x and gy taken as zero on essential DOFs,
  * i.e. the derivative of gy^T A_p(kappa) x with respect to kappa[e][g].
- * Either output may be NULL. */
-int orc_ho_apply_backward(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* x, const double* gy, double* gx, double* gkappa) {
+ * Either output may be NULL; beta (may be NULL) is the reaction coefficient
+ * of the operator, which enters gx only. */
+int orc_ho_apply_backward(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
+                          const double* x, const double* gy, double* gx, double* gkappa) {
   if (gx) {
-    int rc = orc_ho_apply(nex, ney, nez, V, p, q, kappa, gy, gx, 1);
+    int rc = orc_ho_apply(nex, ney, nez, V, p, q, kappa, beta, gy, gx, 1);
     if (rc) return rc;
   }
   if (!gkappa) return ORC_OK;
@@ -562,8 +639,10 @@ int orc_load_vector(int nex, int ney, int nez, const double* V, int p, int q, co
 /* functions (Section 2.2, the bilinear form (grad u, grad v)).                */
 /* corners: [nel][8][3]; dofs: [nel][(p+1)^3] (local node i + n(j + n k));     */
 /* kappa: [nel][q^3]; A: N x N row-major, accumulated (caller zeroes it).      */
+/* beta (may be NULL): reaction coefficient, adds beta w detJ phi_i phi_j.     */
 /* ------------------------------------------------------------------------- */
-int orc_dense_general(int64_t nel, int p, int q, const double* corners, const int64_t* dofs, const double* kappa, int64_t N, double* A) {
+int orc_dense_general(int64_t nel, int p, int q, const double* corners, const int64_t* dofs, const double* kappa,
+                      const double* beta, int64_t N, double* A) {
   if (p < 1 || q < 1 || p + 1 > ORC_MAXN || q > ORC_MAXN) return ORC_EINVAL;
   int n = p + 1, n3 = n * n * n, nq3 = q * q * q;
   double gll[ORC_MAXN], xg[ORC_MAXN], wg[ORC_MAXN];
@@ -572,6 +651,7 @@ int orc_dense_general(int64_t nel, int p, int q, const double* corners, const in
   double L[ORC_MAXN][ORC_MAXN], dL[ORC_MAXN][ORC_MAXN];
   for (int g = 0; g < q; ++g) orc_lagrange(n, gll, xg[g], L[g], dL[g]);
   double* grad = (double*)malloc(sizeof(double) * 3 * n3);
+  double* phi = (double*)malloc(sizeof(double) * n3);
   int bad = 0;
   for (int64_t e = 0; e < nel; ++e) {
     double X[8][3];
@@ -585,11 +665,13 @@ int orc_dense_general(int64_t nel, int p, int q, const double* corners, const in
           double det = inverse3(J, Ji);
           if (!(det > 0.0)) bad = 1;
           double wk = wg[g0] * wg[g1] * wg[g2] * det * kappa[e * nq3 + g0 + q * (g1 + q * g2)];
+          double wb = beta ? wg[g0] * wg[g1] * wg[g2] * det * beta[e * nq3 + g0 + q * (g1 + q * g2)] : 0.0;
           for (int k = 0; k < n; ++k)
             for (int j = 0; j < n; ++j)
               for (int i = 0; i < n; ++i) {
                 double gr[3] = {dL[g0][i] * L[g1][j] * L[g2][k], L[g0][i] * dL[g1][j] * L[g2][k], L[g0][i] * L[g1][j] * dL[g2][k]};
                 int a = i + n * (j + n * k);
+                phi[a] = L[g0][i] * L[g1][j] * L[g2][k];
                 for (int d = 0; d < 3; ++d) /* physical gradient: J^-T gr */
                   grad[3 * a + d] = Ji[0][d] * gr[0] + Ji[1][d] * gr[1] + Ji[2][d] * gr[2];
               }
@@ -598,11 +680,13 @@ int orc_dense_general(int64_t nel, int p, int q, const double* corners, const in
             for (int b = 0; b < n3; ++b) {
               int64_t cb = dofs[e * n3 + b];
               A[ra * N + cb] += wk * (grad[3 * a] * grad[3 * b] + grad[3 * a + 1] * grad[3 * b + 1] + grad[3 * a + 2] * grad[3 * b + 2]);
+              if (beta) A[ra * N + cb] += wb * phi[a] * phi[b];
             }
           }
         }
   }
   free(grad);
+  free(phi);
   return bad ? ORC_EGEOM : ORC_OK;
 }
 
@@ -652,9 +736,12 @@ int orc_lor_kappa_sub(int p, int q, int64_t nel, const double* kappa, double* ks
 
 /* Reading R2: the 8 x 8 stiffness matrix of sub-hex (a,b,c) of an element
  * with corners X, kappa_s times 2x2x2 Gauss quadrature on the sub-hex's own
- * trilinear map through its 8 vertices T_e(GLL points).  Local vertex
+ * trilinear map through its 8 vertices T_e(GLL points); with a reaction
+ * term, plus beta_s times the trilinear mass matrix by the same quadrature
+ * (beta_s binned like kappa_s, reading R16).  Local vertex
  * r = r0 + 2 r1 + 4 r2 is the element node (a + r0, b + r1, c + r2). */
-static int lor_subhex_matrix(const double X[8][3], const double* gll, int a, int b, int c, double kappa_s, double K[8][8]) {
+static int lor_subhex_matrix(const double X[8][3], const double* gll, int a, int b, int c, double kappa_s, double beta_s,
+                             double K[8][8]) {
   double S[8][3];
   for (int r = 0; r < 8; ++r) {
     int r0 = r & 1, r1 = (r >> 1) & 1, r2 = (r >> 2) & 1;
@@ -673,7 +760,7 @@ static int lor_subhex_matrix(const double X[8][3], const double* gll, int a, int
         trilinear_map(S, xi, NULL, J);
         double det = inverse3(J, Ji);
         if (!(det > 0.0)) bad = 1;
-        double grad[8][3];
+        double grad[8][3], phi[8];
         for (int r = 0; r < 8; ++r) {
           int rk[3] = {r & 1, (r >> 1) & 1, (r >> 2) & 1};
           double l[3], dl[3];
@@ -683,11 +770,13 @@ static int lor_subhex_matrix(const double X[8][3], const double* gll, int a, int
           }
           double gr[3] = {dl[0] * l[1] * l[2], l[0] * dl[1] * l[2], l[0] * l[1] * dl[2]};
           for (int d = 0; d < 3; ++d) grad[r][d] = Ji[0][d] * gr[0] + Ji[1][d] * gr[1] + Ji[2][d] * gr[2];
+          phi[r] = l[0] * l[1] * l[2];
         }
-        double wk = kappa_s * det; /* 2-point Gauss weights are 1 */
+        double wk = kappa_s * det, wb = beta_s * det; /* 2-point Gauss weights are 1 */
         for (int r = 0; r < 8; ++r)
           for (int s = 0; s < 8; ++s)
-            K[r][s] += wk * (grad[r][0] * grad[s][0] + grad[r][1] * grad[s][1] + grad[r][2] * grad[s][2]);
+            K[r][s] += wk * (grad[r][0] * grad[s][0] + grad[r][1] * grad[s][1] + grad[r][2] * grad[s][2]) +
+                       wb * phi[r] * phi[s];
       }
   return bad;
 }
@@ -716,7 +805,8 @@ typedef struct {
  * (Step S1.2, A1-A2), formed as triplets, sorted by (row, col) and merged;
  * then (dirichlet != 0) essential rows/columns eliminated with the pattern
  * kept and the diagonal set to 1 (Step S1.2, A4; reading R4). */
-void* orc_lor_assemble(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, int dirichlet, int* status) {
+void* orc_lor_assemble(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
+                       int dirichlet, int* status) {
   *status = ORC_OK;
   int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
   int64_t N = nx * ny * nz, nel = (int64_t)nex * ney * nez;
@@ -724,10 +814,13 @@ void* orc_lor_assemble(int nex, int ney, int nez, const double* V, int p, int q,
   double gll[ORC_MAXN];
   if (orc_gauss_lobatto(p, gll)) { *status = ORC_EINVAL; return NULL; }
   double* ksub = (double*)malloc(sizeof(double) * nel * p3);
-  if (orc_lor_kappa_sub(p, q, nel, kappa, ksub)) { free(ksub); *status = ORC_EINVAL; return NULL; }
+  double* bsub = (double*)calloc((size_t)(nel * p3), sizeof(double));
+  if (orc_lor_kappa_sub(p, q, nel, kappa, ksub) || (beta && orc_lor_kappa_sub(p, q, nel, beta, bsub))) {
+    free(ksub); free(bsub); *status = ORC_EINVAL; return NULL;
+  }
   int64_t ntrip = nel * p3 * 64;
   orc_triplet* T = (orc_triplet*)malloc(sizeof(orc_triplet) * ntrip);
-  if (!T) { free(ksub); *status = ORC_ENOMEM; return NULL; }
+  if (!T) { free(ksub); free(bsub); *status = ORC_ENOMEM; return NULL; }
   int64_t t = 0;
   int bad = 0;
   for (int ez = 0; ez < nez; ++ez)
@@ -740,7 +833,7 @@ void* orc_lor_assemble(int nex, int ney, int nez, const double* V, int p, int q,
           for (int b = 0; b < p; ++b)
             for (int a = 0; a < p; ++a) {
               double K[8][8];
-              bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + a + p * (b + p * c)], K);
+              bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + a + p * (b + p * c)], bsub[e * p3 + a + p * (b + p * c)], K);
               int64_t dof[8];
               for (int r = 0; r < 8; ++r) {
                 int64_t I = (int64_t)ex * p + a + (r & 1), J = (int64_t)ey * p + b + ((r >> 1) & 1), Kk = (int64_t)ez * p + c + ((r >> 2) & 1);
@@ -756,6 +849,7 @@ void* orc_lor_assemble(int nex, int ney, int nez, const double* V, int p, int q,
             }
       }
   free(ksub);
+  free(bsub);
   qsort(T, (size_t)ntrip, sizeof(orc_triplet), triplet_cmp);
   orc_csr* A = (orc_csr*)calloc(1, sizeof(orc_csr));
   A->n = N;
@@ -812,13 +906,14 @@ void orc_csr_free(void* h) {
  * sub-hex s touching DOF r, add row r of K_s.  Entries are returned sorted
  * by column, at most cap per row: cols/vals are [nrows][cap], counts[nrows].
  * Same Dirichlet treatment as orc_lor_assemble. */
-int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, int dirichlet,
+int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta, int dirichlet,
                  int64_t nrows, const int64_t* rows, int cap, int32_t* counts, int64_t* cols, double* vals) {
   int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
   int nq3 = q * q * q, p3 = p * p * p;
   double gll[ORC_MAXN];
   orc_gauss_lobatto(p, gll);
   double* ks = (double*)malloc(sizeof(double) * p3);
+  double* bs = (double*)calloc((size_t)p3, sizeof(double));
   int bad = 0;
   for (int64_t t = 0; t < nrows; ++t) {
     int64_t r = rows[t];
@@ -834,9 +929,10 @@ int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const
           int a = (int)(sa % p), b = (int)(sb % p), c = (int)(sc % p);
           int64_t e = ex + (int64_t)nex * (ey + (int64_t)ney * ez);
           if (orc_lor_kappa_sub(p, q, 1, kappa + e * nq3, ks)) bad = 1;
+          if (beta && orc_lor_kappa_sub(p, q, 1, beta + e * nq3, bs)) bad = 1;
           double X[8][3], K[8][8];
           element_corners(V, nex, ney, ex, ey, ez, X);
-          bad |= lor_subhex_matrix(X, gll, a, b, c, ks[a + p * (b + p * c)], K);
+          bad |= lor_subhex_matrix(X, gll, a, b, c, ks[a + p * (b + p * c)], bs[a + p * (b + p * c)], K);
           int rloc = (int)(I - sa) + 2 * (int)(J - sb) + 4 * (int)(Kk - sc);
           for (int s = 0; s < 8; ++s) {
             int64_t cI = sa + (s & 1), cJ = sb + ((s >> 1) & 1), cK = sc + ((s >> 2) & 1);
@@ -845,7 +941,7 @@ int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const
             for (int m = 0; m < cnt; ++m)
               if (rc[m] == col) found = m;
             if (found < 0) {
-              if (cnt == cap) { free(ks); return ORC_EINVAL; }
+              if (cnt == cap) { free(ks); free(bs); return ORC_EINVAL; }
               rc[cnt] = col;
               rv[cnt] = 0.0;
               found = cnt++;
@@ -870,6 +966,7 @@ int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const
     counts[t] = cnt;
   }
   free(ks);
+  free(bs);
   return bad ? ORC_EGEOM : ORC_OK;
 }
 
@@ -960,7 +1057,7 @@ void orc_chebyshev(int64_t n, const int64_t* rowptr, const int64_t* colidx, cons
  * Stopping rule R7: ||r||/||b|| <= rtol on the recurrence residual, then
  * confirmed on the true residual b - A_p x (otherwise iteration continues
  * from the true residual).  Returns ORC_ENOCONV after maxit iterations. */
-int orc_pcg(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa,
+int orc_pcg(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
             const int64_t* rowptr, const int64_t* colidx, const double* values,
             int precond, int cheb_k, double lo, double hi,
             const double* b, double* x, double rtol, int maxit, int* iters, double* relres) {
@@ -988,13 +1085,13 @@ int orc_pcg(int nex, int ney, int nez, const double* V, int p, int q, const doub
     memcpy(pv, z, sizeof(double) * N);
     double rz = dot(N, r, z);
     while (it < maxit) {
-      orc_ho_apply(nex, ney, nez, V, p, q, kappa, pv, Ap, 1);
+      orc_ho_apply(nex, ney, nez, V, p, q, kappa, beta, pv, Ap, 1);
       double alpha = rz / dot(N, pv, Ap);
       for (int64_t i = 0; i < N; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * Ap[i]; }
       ++it;
       rel = sqrt(dot(N, r, r)) / nb;
       if (rel <= rtol) {
-        orc_ho_apply(nex, ney, nez, V, p, q, kappa, x, Ap, 1);
+        orc_ho_apply(nex, ney, nez, V, p, q, kappa, beta, x, Ap, 1);
         for (int64_t i = 0; i < N; ++i) r[i] = b[i] - Ap[i];
         rel = sqrt(dot(N, r, r)) / nb;
         if (rel <= rtol) { status = ORC_OK; break; }
