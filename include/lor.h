@@ -114,6 +114,20 @@ int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int
  * next lor_check (the call itself does not synchronise). */
 int lor_set_coefficient(lor_ctx* ctx, const double* d_kappa, void* stream);
 
+/* Reaction term of the definite Helmholtz (diffusion-reaction) operator
+ * -div(kappa grad u) + beta u that Section 4.1 solves: beta [nel][q^3]
+ * (device, f64, finite and > 0, same layout as kappa) at the Gauss points.
+ * The context keeps a copy and M_g = beta_g w_g detJ_g (FP64); from then on
+ * lor_apply, lor_apply_backward (gx), lor_assemble and lor_pcg_solve include
+ * the mass term: B_m^T M B_m with B_m = B(x)B(x)B (Step S2.1's Kronecker
+ * basis operator) in the high-order operator, and beta_s times the trilinear
+ * mass matrix of every sub-hex (2x2x2 Gauss, beta_s the Gauss-weight average
+ * of beta over the sub-hex like kappa_s) in the LOR matrix.  d_beta == NULL
+ * switches the term off.  Re-assemble (lor_assemble, lor_precond_setup) after
+ * changing it.  A bad beta is reported by the next lor_check.  Does not
+ * synchronise. */
+int lor_set_reaction(lor_ctx* ctx, const double* d_beta, void* stream);
+
 /* Synchronise the stream and report any error recorded by earlier device
  * work of this context (LOR_EINVAL for a bad coefficient, LOR_ETIMEOUT when
  * an SpMV-type kernel gave up waiting for its bulk copy of matrix values;
@@ -141,12 +155,13 @@ int lor_assemble(lor_ctx* ctx, void* d_values, int dtype, void* stream);
 /* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum
  * factorisation (B = [B(x)B(x)d; B(x)d(x)B; d(x)B(x)B] with the 1D
  * interpolation/derivative matrices, D from lor_set_coefficient), in FP64.
- * Dirichlet rows: y_ess = x_ess; x_ess is ignored in the free rows.
- * d_x, d_y: f64[N], must not alias. */
+ * Dirichlet rows: y_ess = x_ess; x_ess is ignored in the free rows.  With
+ * lor_set_reaction the mass term is included.  d_x, d_y: f64[N], must not
+ * alias. */
 int lor_apply(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
 
 /* Backward of y = A_p(kappa) x for the cotangent d_gy (FP64):
- *   d_gx     = A_p gy                                     (f64[N], may be NULL)
+ *   d_gx     = A_p gy (with the reaction term if set)     (f64[N], may be NULL)
  *   d_gkappa = d(gy^T A_p x)/d kappa = grad_ref(x)^T (D/kappa) grad_ref(gy)
  *              at every Gauss point, x and gy taken as 0 on essential DOFs
  *                                                          (f64[nel q^3], may be NULL).

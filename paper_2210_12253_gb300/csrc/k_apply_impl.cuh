@@ -1,0 +1,585 @@
+// k_apply_impl.cuh -- kernels and launch templates of the high-order apply
+// and its backward, instantiated without the reaction term in k_apply.cu and
+// with it in k_apply_mass.cu (two translation units compile in parallel).
+//
+// y = G^T B^T D B G x (Eq. (4) on one rank) by sum factorisation, and its
+// backward (gradients with respect to x and to kappa at the Gauss points).
+//
+//   B = [B(x)B(x)d ; B(x)d(x)B ; d(x)B(x)B]  (Step S2.1, 3D diffusion)
+//
+// with the 1D interpolation matrix B_1D and derivative matrix d_1D (q x n,
+// n = p+1 GLL nodes, q = p+2 Gauss points), D the symmetric 3x3 factor stored
+// by the setup (Step S1.1), G the gather through the structured element map
+// (Dirichlet DOFs masked) and G^T FP64 atomics into y.  All arithmetic FP64.
+//
+// GB300 design (FP64 issue is the bound: 2 DFMA/clk/SM):
+//  * even-odd folding: GLL nodes and Gauss points are symmetric about 0, so
+//    B_1D[q-1-g][n-1-i] = B_1D[g][i] and d_1D[q-1-g][n-1-i] = -d_1D[g][i];
+//    each 1D contraction works on the half-size symmetric/antisymmetric
+//    parts (u_i +- u_{n-1-i}), about 25-35% fewer FP64 operations;
+//  * one thread per 1D line of a stage, E elements per CTA so that the lines
+//    of a stage fill whole warps (idle lanes would waste FP64 issue slots);
+//  * the z stage, the D product and the transposed z stage run in registers
+//    on the same line (no shared-memory round trip for the q^3 values).
+//
+// With a reaction term (the definite Helmholtz operator of Section 4.1) the
+// mass part B_m^T (beta w detJ) B_m, B_m = B(x)B(x)B, shares every stage with
+// the diffusion part: B_m x is B_z applied to the BB line the z stage already
+// folds, and B_z^T of the scaled values joins d_z^T on the same output slot.
+#pragma once
+
+#include "lor_internal.cuh"
+
+namespace {
+
+template <int P>
+struct Sz {
+  static constexpr int N = P + 1, Q = P + 2, NH = N / 2, QH = Q / 2;
+  static constexpr bool NODD = (N & 1) != 0, QODD = (Q & 1) != 0;
+  static constexpr int NM = N / 2, QM = Q / 2;  // middle index when odd
+  static constexpr int A1 = 2 * N * N * Q;      // [c][k][j][g0], c in {B, d} of the x stage
+  static constexpr int A2 = 3 * N * Q * Q;      // [c][k][g1][g0]
+  static constexpr int PER_ELEM = A1 + A2;
+  // elements per CTA and CTA size: the z stage (the heaviest) gets about one
+  // line per thread, and high-degree CTAs stay small so that several share an
+  // SM (the FP64 pipe then stays busy while one CTA waits at a barrier)
+  static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 3 : P == 6 ? 2
+                         : P == 7 ? 3 : P <= 9 ? 2 : 1;
+  static constexpr int EB = E;
+  static constexpr int T = ((E * Q * Q + 31) / 32) * 32;
+  // folded tables in shared memory (doubles)
+  static constexpr int TB = Q * N;                  // B_1D, d_1D
+  static constexpr int TF = Q * (NH > 0 ? NH : 1);  // BE, BO, DE, DO: [g][i], g < Q, i < NH
+  static constexpr int TABLES = 2 * TB + 4 * TF;
+};
+
+// Folded tables: BE = (B[g][i] + B[g][n-1-i]) / 2, BO = (B[g][i] - B[g][n-1-i]) / 2
+// (same for d), for i < n/2.
+template <int P>
+struct Tab {
+  const double *B, *D, *BE, *BO, *DE, *DO;
+};
+
+template <int P>
+__device__ __forceinline__ Tab<P> load_tables(const LorTables& T, double* s) {
+  using Z = Sz<P>;
+  Tab<P> t;
+  double* B = s;
+  double* D = s + Z::TB;
+  double* BE = s + 2 * Z::TB;
+  double* BO = BE + Z::TF;
+  double* DE = BO + Z::TF;
+  double* DO = DE + Z::TF;
+  for (int x = threadIdx.x; x < Z::TB; x += blockDim.x) {
+    B[x] = T.B[x];
+    D[x] = T.Dm[x];
+  }
+  for (int x = threadIdx.x; x < Z::Q * Z::NH; x += blockDim.x) {
+    const int g = x / Z::NH, i = x % Z::NH;
+    const double b0 = T.B[g * Z::N + i], b1 = T.B[g * Z::N + Z::N - 1 - i];
+    const double d0 = T.Dm[g * Z::N + i], d1 = T.Dm[g * Z::N + Z::N - 1 - i];
+    BE[g * Z::NH + i] = 0.5 * (b0 + b1);
+    BO[g * Z::NH + i] = 0.5 * (b0 - b1);
+    DE[g * Z::NH + i] = 0.5 * (d0 + d1);
+    DO[g * Z::NH + i] = 0.5 * (d0 - d1);
+  }
+  t.B = B;
+  t.D = D;
+  t.BE = BE;
+  t.BO = BO;
+  t.DE = DE;
+  t.DO = DO;
+  return t;
+}
+
+// ---- 1D line operators (u has n entries, y has q entries, or the reverse) ----
+// y = B_1D u, from the folded input e_i = u_i + u_{n-1-i}, o_i = u_i - u_{n-1-i}, um = u_mid
+template <int P>
+__device__ __forceinline__ void fwd_B(const Tab<P>& t, const double* e, const double* o, double um, double* y) {
+  using Z = Sz<P>;
+#pragma unroll
+  for (int g = 0; g < Z::QH; ++g) {
+    double ev = Z::NODD ? t.B[g * Z::N + Z::NM] * um : 0.0, od = 0.0;
+#pragma unroll
+    for (int i = 0; i < Z::NH; ++i) {
+      ev += t.BE[g * Z::NH + i] * e[i];
+      od += t.BO[g * Z::NH + i] * o[i];
+    }
+    y[g] = ev + od;
+    y[Z::Q - 1 - g] = ev - od;
+  }
+  if (Z::QODD) {
+    double ev = 0.0;
+#pragma unroll
+    for (int i = 0; i < Z::NH; ++i) ev += t.BE[Z::QM * Z::NH + i] * e[i];
+    y[Z::QM] = ev;
+  }
+}
+// y = d_1D u
+template <int P>
+__device__ __forceinline__ void fwd_D(const Tab<P>& t, const double* e, const double* o, double um, double* y) {
+  using Z = Sz<P>;
+#pragma unroll
+  for (int g = 0; g < Z::QH; ++g) {
+    double s = Z::NODD ? t.D[g * Z::N + Z::NM] * um : 0.0, d = 0.0;
+#pragma unroll
+    for (int i = 0; i < Z::NH; ++i) {
+      s += t.DE[g * Z::NH + i] * e[i];
+      d += t.DO[g * Z::NH + i] * o[i];
+    }
+    y[g] = d + s;
+    y[Z::Q - 1 - g] = d - s;
+  }
+  if (Z::QODD) {
+    double d = 0.0;
+#pragma unroll
+    for (int i = 0; i < Z::NH; ++i) d += t.DO[Z::QM * Z::NH + i] * o[i];
+    y[Z::QM] = d;
+  }
+}
+template <int P>
+__device__ __forceinline__ void fold_n(const double* u, double* e, double* o, double& um) {
+  using Z = Sz<P>;
+#pragma unroll
+  for (int i = 0; i < Z::NH; ++i) {
+    e[i] = u[i] + u[Z::N - 1 - i];
+    o[i] = u[i] - u[Z::N - 1 - i];
+  }
+  um = Z::NODD ? u[Z::NM] : 0.0;
+}
+template <int P>
+__device__ __forceinline__ void fold_q(const double* v, double* e, double* o, double& vm) {
+  using Z = Sz<P>;
+#pragma unroll
+  for (int g = 0; g < Z::QH; ++g) {
+    e[g] = v[g] + v[Z::Q - 1 - g];
+    o[g] = v[g] - v[Z::Q - 1 - g];
+  }
+  vm = Z::QODD ? v[Z::QM] : 0.0;
+}
+// y = B_1D^T v1 + d_1D^T v2 (either part may be switched off); v1, v2 folded
+// as (e, o, middle) over the q Gauss points.
+template <int P, bool USE_B, bool USE_D>
+__device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const double* o1, double m1,
+                                    const double* e2, const double* o2, double m2, double* y) {
+  using Z = Sz<P>;
+  // B^T part: Ev_i = sum_g BE[g][i] e1_g (+ B[qm][i] m1), Od_i = sum_g BO[g][i] o1_g
+  // d^T part: S_i = sum_g DO[g][i] e2_g (+ d[qm][i] m2),  T_i = sum_g DE[g][i] o2_g
+  // y_i = (Ev + T) + (Od + S), y_{n-1-i} = (Ev + T) - (Od + S)
+#pragma unroll
+  for (int i = 0; i < Z::NH; ++i) {
+    double a1 = 0.0, a2 = 0.0;
+    if (Z::QODD) {
+      if (USE_B) a1 += t.B[Z::QM * Z::N + i] * m1;
+      if (USE_D) a2 += t.D[Z::QM * Z::N + i] * m2;
+    }
+#pragma unroll
+    for (int g = 0; g < Z::QH; ++g) {
+      if (USE_B) {
+        a1 += t.BE[g * Z::NH + i] * e1[g];
+        a2 += t.BO[g * Z::NH + i] * o1[g];
+      }
+      if (USE_D) {
+        a1 += t.DE[g * Z::NH + i] * o2[g];
+        a2 += t.DO[g * Z::NH + i] * e2[g];
+      }
+    }
+    y[i] = a1 + a2;
+    y[Z::N - 1 - i] = a1 - a2;
+  }
+  if (Z::NODD) {
+    double s = 0.0;
+#pragma unroll
+    for (int g = 0; g < Z::QH; ++g) {
+      if (USE_B) s += t.B[g * Z::N + Z::NM] * e1[g];
+      if (USE_D) s += t.D[g * Z::N + Z::NM] * o2[g];
+    }
+    y[Z::NM] = s;
+  }
+}
+
+// ---- stages over all lines of E elements (e_first .. e_first+E-1) ----
+// X: u (gathered from global, masked) -> A1[c][k][j][g0] = (B u, d u) along x.
+template <int P>
+__device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
+                                        const double* __restrict__ x, double* A) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  for (int w = threadIdx.x; w < E * N * N; w += blockDim.x) {
+    const int le = w / (N * N), jk = w % (N * N);
+    const int64_t e = e_first + le;
+    if (e >= m.nel) continue;
+    const int j = jk % N, k = jk / N;
+    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+    const int64_t J = ey * P + j, K = ez * P + k;
+    const bool row_ess = J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1;
+    const double* xr = x + (ex * P) + m.nx * (J + m.ny * K);
+    double u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int64_t I = ex * P + i;
+      u[i] = (row_ess || I == 0 || I == m.nx - 1) ? 0.0 : xr[i];
+    }
+    double e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], um;
+    fold_n<P>(u, e_, o_, um);
+    double yb[Q], yd[Q];
+    fwd_B<P>(t, e_, o_, um, yb);
+    fwd_D<P>(t, e_, o_, um, yd);
+    double* a = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
+#pragma unroll
+    for (int g = 0; g < Q; ++g) {
+      a[g] = yb[g];
+      a[N * N * Q + g] = yd[g];
+    }
+  }
+}
+
+// Y: A1 -> A2[c][k][g1][g0] with c = 0: B_y Bu (BB), 1: B_y du (BD), 2: d_y Bu (DB).
+template <int P>
+__device__ __forceinline__ void stage_y(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E, double* A) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  for (int w = threadIdx.x; w < E * N * Q; w += blockDim.x) {
+    const int le = w / (N * Q), r = w % (N * Q);
+    if (e_first + le >= m.nel) continue;
+    const int g0 = r % Q, k = r / Q;
+    const double* a1 = A + (size_t)le * Z::PER_ELEM;
+    double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+    double bu[N], du[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      bu[j] = a1[(k * N + j) * Q + g0];
+      du[j] = a1[N * N * Q + (k * N + j) * Q + g0];
+    }
+    double eb[Z::NH > 0 ? Z::NH : 1], ob[Z::NH > 0 ? Z::NH : 1], mb, ed[Z::NH > 0 ? Z::NH : 1],
+        od[Z::NH > 0 ? Z::NH : 1], md;
+    fold_n<P>(bu, eb, ob, mb);
+    fold_n<P>(du, ed, od, md);
+    double y[Q];
+    fwd_B<P>(t, eb, ob, mb, y);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) a2[(k * Q + g) * Q + g0] = y[g];
+    fwd_B<P>(t, ed, od, md, y);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) a2[N * Q * Q + (k * Q + g) * Q + g0] = y[g];
+    fwd_D<P>(t, eb, ob, mb, y);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) a2[2 * N * Q * Q + (k * Q + g) * Q + g0] = y[g];
+  }
+}
+
+// Reference gradient along one z line (g0, g1) from A2: g[c][g2]; with the
+// reaction term also the values u[g2] = B_z BB (the mass basis operator).
+template <int P, bool MASS>
+__device__ __forceinline__ void line_gradient(const Tab<P>& t, const double* a2, int g01, double (*g)[Sz<P>::Q],
+                                              double* u) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  double v[N], e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], vm;
+  // d/dxi0 = B_z BD
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = a2[N * Q * Q + k * Q * Q + g01];
+  fold_n<P>(v, e_, o_, vm);
+  fwd_B<P>(t, e_, o_, vm, g[0]);
+  // d/dxi1 = B_z DB
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = a2[2 * N * Q * Q + k * Q * Q + g01];
+  fold_n<P>(v, e_, o_, vm);
+  fwd_B<P>(t, e_, o_, vm, g[1]);
+  // d/dxi2 = d_z BB
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = a2[k * Q * Q + g01];
+  fold_n<P>(v, e_, o_, vm);
+  fwd_D<P>(t, e_, o_, vm, g[2]);
+  if constexpr (MASS) fwd_B<P>(t, e_, o_, vm, u);
+}
+
+// Z' on one line: v[c][g2] -> T0 = B_z^T v0, T1 = B_z^T v1, T2 = d_z^T v2
+// (+ B_z^T u with the reaction term) stored over A2[c][k][g1][g0] (the line's
+// own entries).
+template <int P, bool MASS>
+__device__ __forceinline__ void line_transpose_z(const Tab<P>& t, double (*v)[Sz<P>::Q], const double* u, double* a2,
+                                                 int g01) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  double e_[Z::QH], o_[Z::QH], m_, y[N];
+  fold_q<P>(v[0], e_, o_, m_);
+  bwd<P, true, false>(t, e_, o_, m_, e_, o_, m_, y);
+#pragma unroll
+  for (int k = 0; k < N; ++k) a2[k * Q * Q + g01] = y[k];
+  fold_q<P>(v[1], e_, o_, m_);
+  bwd<P, true, false>(t, e_, o_, m_, e_, o_, m_, y);
+#pragma unroll
+  for (int k = 0; k < N; ++k) a2[N * Q * Q + k * Q * Q + g01] = y[k];
+  if constexpr (MASS) {
+    double e2[Z::QH], o2[Z::QH], m2;
+    fold_q<P>(u, e_, o_, m_);
+    fold_q<P>(v[2], e2, o2, m2);
+    bwd<P, true, true>(t, e_, o_, m_, e2, o2, m2, y);
+  } else {
+    fold_q<P>(v[2], e_, o_, m_);
+    bwd<P, false, true>(t, e_, o_, m_, e_, o_, m_, y);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) a2[2 * N * Q * Q + k * Q * Q + g01] = y[k];
+}
+
+// u <- (beta w detJ) u at the q points of a z line (Mq[e][q^3])
+template <int P>
+__device__ __forceinline__ void line_apply_M(const double* __restrict__ Me, int g01, double* u) {
+  constexpr int Q = Sz<P>::Q, Q2 = Q * Q;
+#pragma unroll
+  for (int g2 = 0; g2 < Q; ++g2) u[g2] *= Me[g01 + Q2 * g2];
+}
+
+// v <- D v at the q points of a z line (D[e][6][q^3], pt = g01 + q^2 g2)
+template <int P>
+__device__ __forceinline__ void line_apply_D(const double* __restrict__ De, int g01, double (*v)[Sz<P>::Q]) {
+  using Z = Sz<P>;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q;
+#pragma unroll
+  for (int g2 = 0; g2 < Q; ++g2) {
+    const int pt = g01 + Q2 * g2;
+    const double a = v[0][g2], b = v[1][g2], c = v[2][g2];
+    const double d00 = De[pt], d01 = De[Q3 + pt], d02 = De[2 * Q3 + pt];
+    const double d11 = De[3 * Q3 + pt], d12 = De[4 * Q3 + pt], d22 = De[5 * Q3 + pt];
+    v[0][g2] = d00 * a + d01 * b + d02 * c;
+    v[1][g2] = d01 * a + d11 * b + d12 * c;
+    v[2][g2] = d02 * a + d12 * b + d22 * c;
+  }
+}
+
+// Y': A2 (T0, T1, T2) -> A1[c][k][j][g0]: U0 = B_y^T T0, U1 = d_y^T T1 + B_y^T T2.
+template <int P>
+__device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E, double* A) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  for (int w = threadIdx.x; w < E * N * Q; w += blockDim.x) {
+    const int le = w / (N * Q), r = w % (N * Q);
+    if (e_first + le >= m.nel) continue;
+    const int g0 = r % Q, k = r / Q;
+    double* a1 = A + (size_t)le * Z::PER_ELEM;
+    const double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+    double v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, y[N];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) v[g] = a2[(k * Q + g) * Q + g0];
+    fold_q<P>(v, e1, o1, m1);
+    bwd<P, true, false>(t, e1, o1, m1, e1, o1, m1, y);
+#pragma unroll
+    for (int j = 0; j < N; ++j) a1[(k * N + j) * Q + g0] = y[j];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) v[g] = a2[2 * N * Q * Q + (k * Q + g) * Q + g0];  // T2 (B^T)
+    fold_q<P>(v, e1, o1, m1);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) v[g] = a2[N * Q * Q + (k * Q + g) * Q + g0];  // T1 (d^T)
+    fold_q<P>(v, e2, o2, m2);
+    bwd<P, true, true>(t, e1, o1, m1, e2, o2, m2, y);
+#pragma unroll
+    for (int j = 0; j < N; ++j) a1[N * N * Q + (k * N + j) * Q + g0] = y[j];
+  }
+}
+
+// X': A1 (U0, U1) -> y_line = d_x^T U0 + B_x^T U1, scatter-added into y.
+template <int P>
+__device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
+                                          const double* A, double* __restrict__ y) {
+  using Z = Sz<P>;
+  constexpr int N = Z::N, Q = Z::Q;
+  for (int w = threadIdx.x; w < E * N * N; w += blockDim.x) {
+    const int le = w / (N * N), jk = w % (N * N);
+    const int64_t e = e_first + le;
+    if (e >= m.nel) continue;
+    const int j = jk % N, k = jk / N;
+    const double* a1 = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
+    double v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, yl[N];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) v[g] = a1[N * N * Q + g];  // U1 (B^T)
+    fold_q<P>(v, e1, o1, m1);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) v[g] = a1[g];  // U0 (d^T)
+    fold_q<P>(v, e2, o2, m2);
+    bwd<P, true, true>(t, e1, o1, m1, e2, o2, m2, yl);
+    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+    const int64_t J = ey * P + j, K = ez * P + k;
+    if (J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1) continue;
+    double* yr = y + (ex * P) + m.nx * (J + m.ny * K);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int64_t I = ex * P + i;
+      if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, yl[i]);
+    }
+  }
+}
+
+template <int P, bool MASS>
+__global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const double* __restrict__ Dq,
+                                                    const double* __restrict__ Mq, const double* __restrict__ x,
+                                                    double* __restrict__ y) {
+  using Z = Sz<P>;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E;
+  extern __shared__ double smem[];
+  const Tab<P> t = load_tables<P>(T, smem);
+  double* A = smem + Z::TABLES;
+  __syncthreads();
+  for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
+    stage_x<P>(m, t, e_first, E, x, A);
+    __syncthreads();
+    stage_y<P>(m, t, e_first, E, A);
+    __syncthreads();
+    for (int w = threadIdx.x; w < E * Q2; w += blockDim.x) {
+      const int le = w / Q2, g01 = w % Q2;
+      const int64_t e = e_first + le;
+      if (e >= m.nel) continue;
+      double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+      double v[3][Q], u[MASS ? Q : 1];
+      line_gradient<P, MASS>(t, a2, g01, v, u);
+      line_apply_D<P>(Dq + e * 6 * Q3, g01, v);
+      if constexpr (MASS) line_apply_M<P>(Mq + e * Q3, g01, u);
+      line_transpose_z<P, MASS>(t, v, u, a2, g01);
+    }
+    __syncthreads();
+    stage_y_t<P>(m, t, e_first, E, A);
+    __syncthreads();
+    stage_x_t<P>(m, t, e_first, E, A, y);
+    __syncthreads();
+  }
+}
+
+// Backward: holds both fields (gy in the first EB element slots, x in the
+// next EB); gkappa = grad(x)^T (D / kappa) grad(gy) on each z line, and
+// gx = A_p gy (with the reaction term if present) through the same
+// transposed stages as the apply.
+template <int P, bool MASS>
+__global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
+                                                             const double* __restrict__ Dq,
+                                                             const double* __restrict__ Mq,
+                                                             const double* __restrict__ kappa,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ gy,
+                                                             double* __restrict__ gx,
+                                                             double* __restrict__ gkappa) {
+  using Z = Sz<P>;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::EB;
+  extern __shared__ double smem[];
+  const Tab<P> t = load_tables<P>(T, smem);
+  double* A = smem + Z::TABLES;                    // gy: element slots 0..E-1
+  double* AX = A + (size_t)E * Z::PER_ELEM;        // x:  element slots E..2E-1
+  __syncthreads();
+  for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
+    stage_x<P>(m, t, e_first, E, gy, A);
+    if (gkappa) stage_x<P>(m, t, e_first, E, x, AX);
+    __syncthreads();
+    stage_y<P>(m, t, e_first, E, A);
+    if (gkappa) stage_y<P>(m, t, e_first, E, AX);
+    __syncthreads();
+    for (int w = threadIdx.x; w < E * Q2; w += blockDim.x) {
+      const int le = w / Q2, g01 = w % Q2;
+      const int64_t e = e_first + le;
+      if (e >= m.nel) continue;
+      const double* De = Dq + e * 6 * Q3;
+      double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+      double v[3][Q], u[MASS ? Q : 1];
+      line_gradient<P, MASS>(t, a2, g01, v, u);
+      if (gkappa) {
+        double gxl[3][Q];
+        line_gradient<P, false>(t, AX + (size_t)le * Z::PER_ELEM + Z::A1, g01, gxl, nullptr);
+#pragma unroll
+        for (int g2 = 0; g2 < Q; ++g2) {
+          const int pt = g01 + Q2 * g2;
+          const double a = v[0][g2], b = v[1][g2], c = v[2][g2];
+          const double d00 = De[pt], d01 = De[Q3 + pt], d02 = De[2 * Q3 + pt];
+          const double d11 = De[3 * Q3 + pt], d12 = De[4 * Q3 + pt], d22 = De[5 * Q3 + pt];
+          const double t0 = d00 * a + d01 * b + d02 * c;
+          const double t1 = d01 * a + d11 * b + d12 * c;
+          const double t2 = d02 * a + d12 * b + d22 * c;
+          gkappa[e * Q3 + pt] = (gxl[0][g2] * t0 + gxl[1][g2] * t1 + gxl[2][g2] * t2) / kappa[e * Q3 + pt];
+          v[0][g2] = t0;
+          v[1][g2] = t1;
+          v[2][g2] = t2;
+        }
+      } else {
+        line_apply_D<P>(De, g01, v);
+      }
+      if constexpr (MASS) line_apply_M<P>(Mq + e * Q3, g01, u);
+      if (gx) line_transpose_z<P, MASS>(t, v, u, a2, g01);
+    }
+    __syncthreads();
+    if (gx) {
+      stage_y_t<P>(m, t, e_first, E, A);
+      __syncthreads();
+      stage_x_t<P>(m, t, e_first, E, A, gx);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+cudaError_t configure(K kernel, size_t bytes, unsigned* mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!(*mask & (1u << dev))) {
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) return err;
+    // prefer the largest shared-memory carveout so that two CTAs fit per SM
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (err != cudaSuccess) return err;
+    *mask |= 1u << dev;
+  }
+  return cudaSuccess;
+}
+
+template <int P, bool MASS>
+cudaError_t apply_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
+                    double* y, cudaStream_t s) {
+  using Z = Sz<P>;
+  const size_t bytes = sizeof(double) * (Z::TABLES + (size_t)Z::E * Z::PER_ELEM);
+  static unsigned mask = 0;
+  cudaError_t err = configure(k_apply<P, MASS>, bytes, &mask);
+  if (err != cudaSuccess) return err;
+  const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
+  k_apply<P, MASS><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
+  return cudaGetLastError();
+}
+
+template <int P, bool MASS>
+cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* kappa,
+                       const double* x, const double* gy, double* gx, double* gk, cudaStream_t s) {
+  using Z = Sz<P>;
+  const size_t bytes = sizeof(double) * (Z::TABLES + 2 * (size_t)Z::EB * Z::PER_ELEM);
+  static unsigned mask = 0;
+  cudaError_t err = configure(k_apply_backward<P, MASS>, bytes, &mask);
+  if (err != cudaSuccess) return err;
+  const int64_t blocks = (m.nel + Z::EB - 1) / Z::EB;
+  k_apply_backward<P, MASS><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
+  lor_count_launch();
+  return cudaGetLastError();
+}
+
+template <bool MASS>
+cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
+                           double* y, cudaStream_t s) {
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: return apply_p<P, MASS>(m, T, Dq, Mq, x, y, s);
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool MASS>
+cudaError_t backward_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                              const double* kappa, const double* x, const double* gy, double* gx, double* gk,
+                              cudaStream_t s) {
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: return backward_p<P, MASS>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace

@@ -1,0 +1,316 @@
+// k_assemble_impl.cuh -- Step S1.2 / A1 + A4: batched LOR matrix assembly
+// (kernel template; instantiated without the reaction term in k_assemble.cu
+// and with it in k_assemble_mass.cu).
+//
+// One CTA per macro element (a high-order element split at the Gauss-Lobatto
+// points into p^3 sub-hexes, Section 2.1), one thread per sub-hex, as in the
+// paper's A1 (one block per macro element, one thread per sub-element).  Each
+// thread forms its sub-hex's 8x8 stiffness block by 2x2x2 Gauss quadrature on
+// the sub-hex's trilinear map with the sub-hex coefficient kappa_s (the
+// Gauss-weight average of kappa over the high-order Gauss points inside the
+// sub-hex), then adds the entries straight into the CSR values at positions
+// computed in closed form (no macro-element sparse block is stored), with
+// FP64/FP32 atomics for the entries shared between sub-hexes.  Rows and
+// columns of essential DOFs are skipped and their diagonal pre-set to 1 (A4),
+// so elimination costs no extra pass.
+//
+// Reaction term (definite Helmholtz, Section 4.1): the block gains beta_s
+// times the sub-hex's trilinear mass matrix by the same 2x2x2 Gauss rule; in
+// the modal basis that is 3^{-(|m|+|n|)/2} times the Walsh transform of
+// W(g) = beta_s detJ_sub(g) at m xor n, added before the Hadamard sandwich.
+//
+// Geometry: the sub-hex map is the element's trilinear map restricted to the
+// sub-box, so J_sub(tau) = J_e(xi(tau)) diag(r_a, r_b, r_c) with r the half
+// widths of the GLL intervals; only the element Jacobian columns (bilinear in
+// the two other coordinates) are evaluated, in FP64.
+#pragma once
+
+#include "lor_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Sub-hex stiffness block in the modal basis.
+//
+// On the sub-hex reference cube tau in [-1,1]^3 the trilinear nodal basis is
+// phi_i = prod_k l_{i_k}(tau_k), l_0 = (1 - t)/2, l_1 = (1 + t)/2.  In the
+// modal basis psi_m = prod_k psi_{m_k}(tau_k), psi_0 = 1, psi_1 = t, one has
+// phi = (1/8) H psi with H_im = prod_k s(i_k)^{m_k}, s(0) = -1, s(1) = +1.
+// At the 2x2x2 Gauss points tau_k = eps_k / sqrt(3), eps_k = +-1,
+//   d_a psi_m = [m_a = 1] prod_{k != a} (eps_k / sqrt(3))^{m_k},
+// so the modal stiffness
+//   Kt_mn = sum_g sum_ab G^ab(g) d_a psi_m(g) d_b psi_n(g)
+//         = sum_{a in m} sum_{b in n} 3^{-(|m|+|n|-2)/2} Ghat^ab(w(m,n,a,b)),
+// where Ghat^ab is the Walsh-Hadamard transform of G^ab over the 8 points,
+//   Ghat(w) = sum_g G(g) prod_k eps_k^{w_k},  w = (m without a) xor (n without b).
+// The nodal block is K = H Kt H^T / 64, applied axis by axis.  FP64 work per
+// sub-hex: 6 x 24 additions (transforms), 84 products (Kt), about 200
+// additions (H . H^T on the 36 symmetric entries), instead of 8 x 180
+// operations for the nodal formula at each Gauss point.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+__device__ __forceinline__ constexpr int pair_index(int a, int b) {  // (00,01,02,11,12,22)
+  return a <= b ? (a == 0 ? b : a == 1 ? 2 + b : 5) : (b == 0 ? a : b == 1 ? 2 + a : 5);
+}
+__device__ __forceinline__ constexpr int walsh_index(int m, int n, int a, int b) {
+  return (m & ~(1 << a)) ^ (n & ~(1 << b));
+}
+__device__ __forceinline__ constexpr double inv_sqrt3_pow(int p) {  // 3^(-p/2), p = 0..6
+  return p == 0 ? 1.0
+       : p == 1 ? 0.57735026918962576451
+       : p == 2 ? 0.33333333333333333333
+       : p == 3 ? 0.19245008972987525484
+       : p == 4 ? 0.11111111111111111111
+       : p == 5 ? 0.06415002990995841617
+                : 0.03703703703703703704;
+}
+__device__ __forceinline__ constexpr int sym(int i, int j) { return i <= j ? i * 8 + j : j * 8 + i; }
+
+template <typename VT>
+__device__ __forceinline__ void walsh8(VT* v) {  // v(w) = sum_g v(g) prod_k eps_k^{w_k}
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+      if (!((g >> k) & 1)) {
+        const VT lo = v[g], hi = v[g | (1 << k)];
+        v[g] = lo + hi;
+        v[g | (1 << k)] = hi - lo;
+      }
+}
+
+// K <- (H_k (x) H_k) K for axis k, on a symmetric 8x8 matrix stored at
+// K[sym(i,j)]; H_k maps (m_k = 0, m_k = 1) to (i_k = 0: a - b, i_k = 1: a + b).
+template <typename VT, int k>
+__device__ __forceinline__ void hadamard_axis(VT* K) {
+  VT out[64];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = i; j < 8; ++j) {
+      const int i0 = i & ~(1 << k), i1 = i | (1 << k), j0 = j & ~(1 << k), j1 = j | (1 << k);
+      const VT a = K[sym(i0, j0)], b = K[sym(i0, j1)], c = K[sym(i1, j0)], d = K[sym(i1, j1)];
+      const VT u = ((i >> k) & 1) ? a + c : a - c;
+      const VT v = ((i >> k) & 1) ? b + d : b - d;
+      out[sym(i, j)] = ((j >> k) & 1) ? u + v : u - v;
+    }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = i; j < 8; ++j) K[sym(i, j)] = out[sym(i, j)];
+}
+
+template <int P>
+constexpr int kElemsPerCta = P * P * P >= 64 ? 1 : 64 / (P * P * P);
+template <int P>
+constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
+                                            : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
+
+template <typename VT>
+__device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
+
+template <int P, typename VT, bool MASS>
+__global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTables T,
+                                                             const double* __restrict__ kappa,
+                                                             const double* __restrict__ beta,
+                                                             VT* __restrict__ vals) {
+  constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kElemsPerCta<P>;
+  constexpr int TAB = 3 * L * L * 3;  // three Jacobian-column tables per element
+  constexpr bool F32 = sizeof(VT) == sizeof(float);
+  __shared__ double Ehalf[EPB][36];
+  __shared__ double tab[EPB][TAB];
+  __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
+  __shared__ double sl0[L], sl1[L];
+  if (threadIdx.x < L) {
+    sl0[threadIdx.x] = T.sub_l0[threadIdx.x];
+    sl1[threadIdx.x] = T.sub_l1[threadIdx.x];
+  }
+  __syncthreads();
+  const int64_t e_first = (int64_t)blockIdx.x * EPB;
+  // Jacobian columns of each element at the sub-hex Gauss coordinates (FP64;
+  // the FP32 mode also keeps a rounded copy, converted once per element:
+  // conversions share the FP64 pipe on this GPU).
+  for (int le = 0; le < EPB; ++le) {
+    const int64_t e = e_first + le;
+    if (e < m.nel) lor_jacobian_columns(m, e, sl0, sl1, L, Ehalf[le], tab[le]);
+  }
+  if constexpr (F32) {
+    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
+    __syncthreads();
+  }
+  const int nwork = EPB * P3;
+  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+    const int le = w / P3, s = w % P3;
+    const int64_t e = e_first + le;
+    if (e >= m.nel) break;
+    const int a = s % P, b = (s / P) % P, c = s / (P * P);
+
+    // kappa_s (and beta_s): Gauss-weight averages over the high-order points in the sub-hex
+    double ks = 0.0, bs = 0.0;
+    for (int g2 = T.bin_first[c]; g2 < T.bin_first[c] + T.bin_count[c]; ++g2)
+      for (int g1 = T.bin_first[b]; g1 < T.bin_first[b] + T.bin_count[b]; ++g1) {
+        const double w12 = T.bin_w[g1] * T.bin_w[g2];
+        for (int g0 = T.bin_first[a]; g0 < T.bin_first[a] + T.bin_count[a]; ++g0) {
+          const double w = w12 * T.bin_w[g0];
+          const int64_t pt = e * Q3 + g0 + Q * (g1 + Q * g2);
+          ks += w * kappa[pt];
+          if constexpr (MASS) bs += w * beta[pt];
+        }
+      }
+
+    // G_sub^{ab}(g) = F_ab (A_a . A_b) / det_e with A the adjugate rows of the
+    // element Jacobian, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64 (the 1/64
+    // of the modal-to-nodal transform folded in).
+    VT G[6][8];
+    VT W[MASS ? 8 : 1];  // reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
+    const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
+    if constexpr (!F32) {
+      const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
+      const double k64 = ks * (1.0 / 64.0);
+      const double F00 = k64 * rb * rc * T.sub_rinv[a], F01 = k64 * rc, F02 = k64 * rb;
+      const double F11 = k64 * ra * rc * T.sub_rinv[b], F12 = k64 * ra, F22 = k64 * ra * rb * T.sub_rinv[c];
+      const double bR = MASS ? bs * (1.0 / 64.0) * ra * rb * rc : 0.0;
+      const double* t0 = tab[le];
+      const double* t1 = tab[le] + L * L * 3;
+      const double* t2 = tab[le] + 2 * L * L * 3;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
+        const double* c0 = t0 + 3 * (u1 + L * u2);
+        const double* c1 = t1 + 3 * (u0 + L * u2);
+        const double* c2 = t2 + 3 * (u0 + L * u1);
+        double A[3][3];
+        lor_cross(c1, c2, A[0]);
+        lor_cross(c2, c0, A[1]);
+        lor_cross(c0, c1, A[2]);
+        const double det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
+        const double r = lor_rcp(det);
+        if constexpr (MASS) W[g] = (VT)(bR * det);
+#pragma unroll
+        for (int ab = 0; ab < 6; ++ab) {
+          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
+          const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
+          G[ab][g] = (VT)((Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]));
+        }
+      }
+    } else {
+      // FP64: the first adjugate row and the determinant; FP32: the rest.
+      const float ra = (float)T.sub_r[a], rb = (float)T.sub_r[b], rc = (float)T.sub_r[c];
+      const float k64 = (float)ks * (1.0f / 64.0f);
+      const float F00 = k64 * rb * rc / ra, F01 = k64 * rc, F02 = k64 * rb;
+      const float F11 = k64 * ra * rc / rb, F12 = k64 * ra, F22 = k64 * ra * rb / rc;
+      const float bR = MASS ? (float)bs * (1.0f / 64.0f) * ra * rb * rc : 0.0f;
+      const double* t0 = tab[le];
+      const double* t1 = tab[le] + L * L * 3;
+      const double* t2 = tab[le] + 2 * L * L * 3;
+      const float* f0 = tabf[le];
+      const float* f1 = tabf[le] + L * L * 3;
+      const float* f2 = tabf[le] + 2 * L * L * 3;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
+        const int o0 = 3 * (u1 + L * u2), o1 = 3 * (u0 + L * u2), o2 = 3 * (u0 + L * u1);
+        double A0[3];
+        lor_cross(t1 + o1, t2 + o2, A0);
+        const double det = t0[o0] * A0[0] + t0[o0 + 1] * A0[1] + t0[o0 + 2] * A0[2];
+        const float detf = (float)det;
+        const float r = 1.0f / detf;
+        if constexpr (MASS) W[g] = (VT)(bR * detf);
+        const float* c0 = f0 + o0;
+        const float* c1 = f1 + o1;
+        const float* c2 = f2 + o2;
+        float A[3][3];
+        A[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
+        A[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
+        A[0][2] = c1[0] * c2[1] - c1[1] * c2[0];
+        A[1][0] = c2[1] * c0[2] - c2[2] * c0[1];
+        A[1][1] = c2[2] * c0[0] - c2[0] * c0[2];
+        A[1][2] = c2[0] * c0[1] - c2[1] * c0[0];
+        A[2][0] = c0[1] * c1[2] - c0[2] * c1[1];
+        A[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
+        A[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
+#pragma unroll
+        for (int ab = 0; ab < 6; ++ab) {
+          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
+          const float Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
+          G[ab][g] = (VT)((Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]));
+        }
+      }
+    }
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) walsh8<VT>(G[ab]);
+    if constexpr (MASS) walsh8<VT>(W);
+
+    // modal block (row/column 0 vanish: psi_0 has no gradient)
+    VT K[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) K[i] = (VT)0;
+#pragma unroll
+    for (int mm = 1; mm < 8; ++mm)
+#pragma unroll
+      for (int nn = mm; nn < 8; ++nn) {
+        VT acc = (VT)0;
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa)
+          if ((mm >> aa) & 1)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+              if ((nn >> bb) & 1)
+                acc += (VT)inv_sqrt3_pow(popc3(mm) + popc3(nn) - 2) * G[pair_index(aa, bb)][walsh_index(mm, nn, aa, bb)];
+        K[sym(mm, nn)] = acc;
+      }
+    if constexpr (MASS) {
+      // modal mass block: sum_g W(g) psi_m(g) psi_n(g) = 3^{-(|m|+|n|)/2} What(m xor n)
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm)
+#pragma unroll
+        for (int nn = mm; nn < 8; ++nn) K[sym(mm, nn)] += (VT)inv_sqrt3_pow(popc3(mm) + popc3(nn)) * W[mm ^ nn];
+    }
+    hadamard_axis<VT, 0>(K);
+    hadamard_axis<VT, 1>(K);
+    hadamard_axis<VT, 2>(K);
+
+    // Scatter into the CSR values (closed-form positions), skipping essential
+    // rows and columns (their diagonal was pre-set to 1).
+    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+    const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
+      if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
+      const int64_t base = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
+      const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
+        if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
+        const int di = (t & 1) - (r & 1), dj = ((t >> 1) & 1) - ((r >> 1) & 1), dk = (t >> 2) - (r >> 2);
+        atomic_add<VT>(vals + base + (dk * cy + dj) * cx + di, K[sym(r, t)]);
+      }
+    }
+  }
+}
+
+template <int P, typename VT, bool MASS>
+void launch_assemble_p(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
+                       cudaStream_t s) {
+  k_assemble<P, VT, MASS><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(
+      m, T, kappa, beta, vals);
+  lor_count_launch();
+}
+
+template <typename VT, bool MASS>
+cudaError_t assemble_dispatch(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
+                              cudaStream_t s) {
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: launch_assemble_p<P, VT, MASS>(m, T, kappa, beta, vals, s); break;
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace

@@ -58,6 +58,45 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   if (bad) atomicOr(status, bad);
 }
 
+// Reaction term (the definite Helmholtz operator of Section 4.1): at every
+// Gauss point M = beta w detJ, the diagonal factor between B_m = B(x)B(x)B
+// and its transpose; beta is copied and checked (finite, > 0) like kappa.
+template <int P>
+__global__ void __launch_bounds__(128) k_reaction_setup(LorMesh m, LorTables T, const double* __restrict__ bin,
+                                                        double* __restrict__ bcopy, double* __restrict__ Mq,
+                                                        int* __restrict__ status) {
+  constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q;
+  __shared__ double Ehalf[36];
+  __shared__ double col[3 * Q2 * 3];
+  __shared__ double sw[Q], s0[Q], s1[Q];
+  if (threadIdx.x < Q) {
+    sw[threadIdx.x] = T.gw[threadIdx.x];
+    s0[threadIdx.x] = T.gl0[threadIdx.x];
+    s1[threadIdx.x] = T.gl1[threadIdx.x];
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
+    lor_jacobian_columns(m, e, s0, s1, Q, Ehalf, col);
+    for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
+      const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
+      const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
+      const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
+      const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
+      double a0[3];
+      lor_cross(c1, c2, a0);
+      const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
+      const double b = bin[e * Q3 + pt];
+      if (!(b > 0.0) || !(b < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
+      if (!(det > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
+      Mq[e * Q3 + pt] = b * (sw[g0] * sw[g1] * sw[g2]) * det;
+      bcopy[e * Q3 + pt] = b;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, bad);
+}
+
 // Jacobian determinant check at the tensor grid t[0..L) of every element.
 __global__ void __launch_bounds__(128) k_geometry_check(LorMesh m, LorTables T, int L, int use_sub,
                                                         int* __restrict__ status) {
@@ -162,6 +201,20 @@ cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double*
   switch (m.p) {
 #define LOR_CASE(P) \
   case P: k_setup<P><<<g, 128, 0, s>>>(m, T, kappa_in, kappa_copy, Dq, d_status); lor_count_launch(); break;
+    LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
+    LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
+#undef LOR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_reaction_setup(const LorMesh& m, const LorTables& T, const double* beta_in, double* beta_copy,
+                                      double* Mq, int* d_status, cudaStream_t s) {
+  const int g = grid_for(m.nel);
+  switch (m.p) {
+#define LOR_CASE(P) \
+  case P: k_reaction_setup<P><<<g, 128, 0, s>>>(m, T, beta_in, beta_copy, Mq, d_status); lor_count_launch(); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

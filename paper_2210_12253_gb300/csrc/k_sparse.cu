@@ -727,7 +727,7 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
     dot(r, z, S + cur);
     k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
     while (it < maxit) {
-      err = lor_launch_apply_accumulate(c->m, c->T, c->Dq, p, q, s);
+      err = lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
       if (err != cudaSuccess) return fail(c, err, "pcg apply");
       dot(p, q, S + S_PQ);
       const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
@@ -743,7 +743,7 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
       bool restarted = false;
       if (rel <= rtol) {
         // confirm on the true residual b - A x
-        err = lor_launch_apply(c->m, c->T, c->Dq, x, q, s);
+        err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
         if (err == cudaSuccess) {
           k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
           dot(r, r, S + S_RR);

@@ -183,6 +183,8 @@ void free_all(lor_ctx* c) {
   cudaFree(c->verts);
   cudaFree(c->Dq);
   cudaFree(c->kappa);
+  cudaFree(c->beta);
+  cudaFree(c->Mq);
   cudaFree(c->rowptr);
   cudaFree(c->colidx);
   cudaFree(c->vals64);
@@ -316,6 +318,22 @@ int lor_set_coefficient(lor_ctx* c, const double* d_kappa, void* stream) {
   return LOR_OK;
 }
 
+int lor_set_reaction(lor_ctx* c, const double* d_beta, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_beta) {
+    c->have_beta = false;
+    return LOR_OK;
+  }
+  const int64_t nq = c->m.nel * (int64_t)c->T.q * c->T.q * c->T.q;
+  int rc = alloc(c, &c->beta, nq, "beta");
+  if (!rc) rc = alloc(c, &c->Mq, nq, "beta w detJ");
+  if (rc) return rc;
+  cudaError_t e = lor_launch_reaction_setup(c->m, c->T, d_beta, c->beta, c->Mq, c->d_status, S(stream));
+  if (e != cudaSuccess) return cuda_err(c, e, "lor_set_reaction");
+  c->have_beta = true;
+  return LOR_OK;
+}
+
 int lor_check(lor_ctx* c, void* stream) {
   if (!c) return LOR_EINVAL;
   int flags = 0;
@@ -327,7 +345,7 @@ int lor_check(lor_ctx* c, void* stream) {
     if (flags & LOR_FLAG_TIMEOUT)
       return set_err(c, LOR_ETIMEOUT, "a bounded device wait expired (a bulk copy into shared memory never completed)");
     if (flags & LOR_FLAG_BAD_GEOM) return set_err(c, LOR_EGEOM, "a Jacobian determinant is <= 0");
-    return set_err(c, LOR_EINVAL, "kappa must be finite and > 0 at every Gauss point");
+    return set_err(c, LOR_EINVAL, "kappa (and beta) must be finite and > 0 at every Gauss point");
   }
   return LOR_OK;
 }
@@ -366,7 +384,7 @@ int lor_assemble(lor_ctx* c, void* d_values, int dtype, void* stream) {
     if (rc) return rc;
     out = dtype == LOR_F64 ? (void*)c->vals64 : (void*)c->vals32;
   }
-  cudaError_t e = lor_launch_assemble(c->m, c->T, c->kappa, out, dtype, S(stream));
+  cudaError_t e = lor_launch_assemble(c->m, c->T, c->kappa, c->have_beta ? c->beta : nullptr, out, dtype, S(stream));
   if (e != cudaSuccess) return cuda_err(c, e, "lor_assemble");
   if (!d_values) {
     if (dtype == LOR_F64) c->have_vals64 = true;
@@ -379,7 +397,7 @@ int lor_apply(lor_ctx* c, const double* d_x, double* d_y, void* stream) {
   if (!c) return LOR_EINVAL;
   if (!d_x || !d_y || d_x == d_y) return set_err(c, LOR_EINVAL, "lor_apply: x, y must be distinct device arrays");
   if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_apply: call lor_set_coefficient first");
-  cudaError_t e = lor_launch_apply(c->m, c->T, c->Dq, d_x, d_y, S(stream));
+  cudaError_t e = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, d_x, d_y, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_apply");
 }
 
@@ -389,7 +407,8 @@ int lor_apply_backward(lor_ctx* c, const double* d_x, const double* d_gy, double
   if (!d_gy || (d_gkappa && !d_x) || (d_gx && d_gx == d_gy))
     return set_err(c, LOR_EINVAL, "lor_apply_backward: bad arguments");
   if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_apply_backward: call lor_set_coefficient first");
-  cudaError_t e = lor_launch_apply_backward(c->m, c->T, c->Dq, c->kappa, d_x, d_gy, d_gx, d_gkappa, S(stream));
+  cudaError_t e = lor_launch_apply_backward(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, c->kappa, d_x, d_gy, d_gx,
+                                            d_gkappa, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_apply_backward");
 }
 

@@ -50,12 +50,15 @@ struct lor_ctx {
   double* verts = nullptr;
   double* Dq = nullptr;        // [nel][6][q^3]: kappa w detJ J^-1 J^-T (00,01,02,11,12,22)
   double* kappa = nullptr;     // [nel][q^3]
+  double* beta = nullptr;      // [nel][q^3] reaction coefficient (copy), when set
+  double* Mq = nullptr;        // [nel][q^3] beta w detJ, when set
   int64_t* rowptr = nullptr;   // [N+1]
   int32_t* colidx = nullptr;   // [nnz]
   double* vals64 = nullptr;    // [nnz]
   float* vals32 = nullptr;     // [nnz]
   int* d_status = nullptr;     // device error flags
   bool have_coeff = false, have_pattern = false, have_vals64 = false, have_vals32 = false;
+  bool have_beta = false;      // the reaction term is on (lor_set_reaction)
   // preconditioner
   int pc_kind = LOR_PRECOND_NONE, pc_dtype = LOR_F64, pc_degree = 1;
   double pc_lo = 0, pc_hi = 0, pc_lmax = 0;
@@ -193,20 +196,25 @@ __device__ __forceinline__ double lor_rcp(double x) {
 cudaError_t lor_launch_geometry_check(const LorMesh& m, const LorTables& T, int* d_status, cudaStream_t s);
 cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double* kappa_in, double* kappa_copy,
                              double* Dq, int* d_status, cudaStream_t s);
+// Mq = beta w detJ at every Gauss point and a copy of beta (checked finite > 0).
+cudaError_t lor_launch_reaction_setup(const LorMesh& m, const LorTables& T, const double* beta_in, double* beta_copy,
+                                      double* Mq, int* d_status, cudaStream_t s);
 cudaError_t lor_launch_load_vector(const LorMesh& m, const LorTables& T, const double* f, double* b,
                                    cudaStream_t s);
 cudaError_t lor_launch_pattern(const LorMesh& m, int64_t* rowptr, int32_t* colidx, cudaStream_t s);
-cudaError_t lor_launch_assemble(const LorMesh& m, const LorTables& T, const double* kappa, void* values,
-                                int dtype, cudaStream_t s);
-cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double* Dq, const double* x, double* y,
-                             cudaStream_t s);
+// beta (may be NULL): the reaction coefficient; adds the LOR mass blocks.
+cudaError_t lor_launch_assemble(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta,
+                                void* values, int dtype, cudaStream_t s);
+// Mq (may be NULL): beta w detJ at the Gauss points, the reaction term.
+cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                             const double* x, double* y, cudaStream_t s);
 // The apply without its output initialisation: adds A_free x into y (y must
 // already hold x on essential DOFs and 0 elsewhere).
-cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* x,
-                                        double* y, cudaStream_t s);
-cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* kappa,
-                                      const double* x, const double* gy, double* gx, double* gkappa,
-                                      cudaStream_t s);
+cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                                        const double* x, double* y, cudaStream_t s);
+cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                                      const double* kappa, const double* x, const double* gy, double* gx,
+                                      double* gkappa, cudaStream_t s);
 // sparse / solver kernels (k_sparse.cu)
 // The SpMV-type kernels read the CSR values only: the columns and row starts
 // of the 27-point LOR pattern are recomputed from the grid (the pattern

@@ -21,7 +21,7 @@ EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
-    "lor_precond_apply_noalloc",
+    "lor_precond_apply_noalloc", "lor_set_reaction",
 ]
 
 
@@ -58,6 +58,8 @@ def load_library(path=LIB):
     L.lor_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.lor_set_coefficient.restype = i
     L.lor_set_coefficient.argtypes = [vp, vp, vp]
+    L.lor_set_reaction.restype = i
+    L.lor_set_reaction.argtypes = [vp, vp, vp]
     L.lor_check.restype = i
     L.lor_check.argtypes = [vp, vp]
     L.lor_build_pattern.restype = i
@@ -175,6 +177,16 @@ class LOR:
         _dev(kappa, torch.float64, self.nqpt, "kappa")
         self._call("lor_set_coefficient", _ptr(kappa))
         self._kappa_key = (kappa.data_ptr(), kappa._version)
+        if check:
+            self.check()
+
+    def set_reaction(self, beta, check=False):
+        """Reaction term beta u of the definite Helmholtz operator (beta at
+        the Gauss points, like kappa); None switches it off.  Re-assemble the
+        LOR matrix (and the preconditioner) afterwards."""
+        if beta is not None:
+            _dev(beta, torch.float64, self.nqpt, "beta")
+        self._call("lor_set_reaction", _ptr(beta))
         if check:
             self.check()
 
