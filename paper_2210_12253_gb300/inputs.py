@@ -136,3 +136,10 @@ def power_start_vector(n, seed=12345):
     """Seeded start vector for the power iteration that estimates the largest
     eigenvalue of D^-1 A (a random input of the method, passed to both sides)."""
     return np.random.default_rng(seed).standard_normal(n)
+
+
+def reaction_coefficient(nel, q, seed=777):
+    """Seeded reaction coefficient beta = exp(N(0,1)) per (element, Gauss
+    point) for the definite Helmholtz (diffusion-reaction) workloads; drawn
+    from its own generator so the diffusion workloads' draws are unchanged."""
+    return np.exp(np.random.default_rng(seed).standard_normal((nel, q ** 3)))

@@ -63,6 +63,18 @@ def backward_flops_per_element(p):
     return 6 * sumfact_fma(p) + 36 * (p + 2) ** 3
 
 
+def reaction_extra_apply_flops_per_element(p):
+    """The reaction term's share of the apply: B_z on the q^2 BB lines and its
+    transpose (q^3 n FMAs each) and the scaling by beta w detJ (q^3)."""
+    q, n = p + 2, p + 1
+    return 4 * q ** 3 * n + q ** 3
+
+
+def reaction_extra_assemble_flops_per_subhex():
+    """W(g) (8), its Walsh transform (24), 36 modal mass terms (72)."""
+    return 8 + 24 + 72
+
+
 def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
     """(flops, bytes) of one launch of `kind` on the given sizes."""
     q = p + 2
@@ -76,6 +88,18 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
         return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
     if kind == "backward":
         return backward_flops_per_element(p) * nel, 24 * ndof + 64 * nq
+    if kind == "reaction_setup":
+        # det (3 cross-product terms, 5) and beta w detJ (3); beta in, beta copy and M out
+        return 8 * nq, 24 * nq
+    if kind == "assemble_helmholtz":
+        f, b = kernel_work("assemble", p, ndof, nel, nnz, vbytes)
+        return f + reaction_extra_assemble_flops_per_subhex() * nsub, b + 8 * nq
+    if kind == "apply_helmholtz":
+        f, b = kernel_work("apply", p, ndof, nel, nnz, vbytes)
+        return f + reaction_extra_apply_flops_per_element(p) * nel, b + 8 * nq
+    if kind == "backward_helmholtz":
+        f, b = kernel_work("backward", p, ndof, nel, nnz, vbytes)
+        return f + reaction_extra_apply_flops_per_element(p) * nel, b + 8 * nq
     if kind == "precond":
         # degree-1 SpMV passes over the matrix (values + int32 columns + row
         # pointers) and ~6 vector streams per step
