@@ -11,7 +11,9 @@ ranks.  The PCG time to 1e-8 (FP64 vs mixed precision) is measured on the
 32^3-element, p = 6 workload (7,189,057 DOFs) and reported under "pcg"; the
 adjoint gradient dJ/dtheta (forward solve, adjoint solve, gradient kernel) on
 the 24^3-element, p = 5 workload under "gradient"; the same step with the
-reaction term of the definite Helmholtz problem under "helmholtz".
+reaction term of the definite Helmholtz problem under "helmholtz"; the
+macro-element vs unstructured LOR assembly at ~4M DOFs per degree under
+"assembly_comparator".
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
@@ -296,6 +298,9 @@ def run_gpu(args, rank, world, local_rank):
     helm = None
     if not args.no_helmholtz:
         helm = run_helmholtz(args, dev)
+    comparator = None
+    if not args.no_comparator:
+        comparator = run_comparator(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -312,7 +317,7 @@ def run_gpu(args, rank, world, local_rank):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps},
            "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad,
-           "helmholtz": helm}
+           "helmholtz": helm, "assembly_comparator": comparator}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     op.close()
@@ -493,6 +498,66 @@ def run_helmholtz(args, dev):
             "fp64_peak_tflops": FP64_PEAK_TFLOPS, "kernels": kernels}
 
 
+def run_comparator(args, dev):
+    """Macro-element vs unstructured LOR assembly (Section 4.2's comparison)
+    at about 4M DOFs for p = 1, 2, 3, 4, 6, 8 (jittered mesh, lognormal
+    kappa, seed 4, FP64 values).  macro = lor_assemble; unstructured =
+    lor_assemble_unstructured on the LOR mesh given as E-vectors (built once
+    by lor_lor_mesh, whose time is reported separately: the paper notes that
+    building the LOR mesh and its restriction dominates the unstructured
+    path).  Median of 5 event-timed launches after one warm-up, L2 flushed
+    before each."""
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import make_problem
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    rows = []
+    for p in (1, 2, 3, 4, 6, 8):
+        ne = max(1, round(4e6 ** (1 / 3) / p))
+        prob = make_problem("cmp_p%d" % p, ne, ne, ne, p, seed=4, kappa="lognormal", rhs=None)
+        op = LOR(p, ne, ne, ne, torch.tensor(prob.vertices, device=dev))
+        op.set_coefficient(torch.tensor(prob.kappa.reshape(-1), device=dev))
+        rp, ci = op.build_pattern()
+        op.build_pattern_internal()
+        vals = torch.empty(op.nnz, dtype=torch.float64, device=dev)
+        ms_macro = timed(lambda: op.assemble(torch.float64, out=vals))
+        mesh_box = {}
+
+        def build_mesh():
+            mesh_box["m"] = op.lor_mesh()
+
+        ms_mesh = timed(build_mesh, reps=3)
+        corners, dofs, ks, _, ess = mesh_box["m"]
+        ms_uns = timed(lambda: op.assemble_unstructured(corners, dofs, ks, rp, ci, op.ndof, ess=ess, out=vals))
+        op.check()
+        rows.append({"p": p, "elements": op.nel, "ndof": op.ndof, "nnz": op.nnz, "macro_ms": ms_macro,
+                     "unstructured_ms": ms_uns, "lor_mesh_ms": ms_mesh,
+                     "macro_gdofs": op.ndof / (ms_macro * 1e-3) / 1e9,
+                     "unstructured_gdofs": op.ndof / (ms_uns * 1e-3) / 1e9,
+                     "ratio": ms_uns / ms_macro, "ratio_with_mesh": (ms_uns + ms_mesh) / ms_macro})
+        del corners, dofs, ks, ess, mesh_box, vals, rp, ci
+        op.close()
+        torch.cuda.empty_cache()
+    return {"workload": "~4M DOFs per degree, +-10% jitter, kappa lognormal(0,1), seed 4, FP64 values",
+            "rows": rows}
+
+
 def run_sweep(args, dev):
     """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
     JSON object per degree (setup, FP64 and FP32 assembly, apply, backward,
@@ -633,6 +698,8 @@ def main(argv=None):
     ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the 24^3 p=5 adjoint-gradient timing")
+    ap.add_argument("--no-comparator", action="store_true",
+                    help="skip the macro-element vs unstructured LOR assembly comparison")
     ap.add_argument("--no-helmholtz", action="store_true",
                     help="skip the definite Helmholtz (reaction term) step on the 16^3 p=4 workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -152,6 +152,38 @@ int lor_build_pattern(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, void* 
  * lor_build_pattern and lor_set_coefficient. */
 int lor_assemble(lor_ctx* ctx, void* d_values, int dtype, void* stream);
 
+/* The LOR mesh as a general hex mesh (E-vectors), the input of the
+ * unstructured assembly below: for every sub-hex s = a + p(b + p c) of every
+ * element e (index e p^3 + s), its 8 vertices T_e(GLL tensor points)
+ * d_corners [nsub][8][3] f64 (local vertex r = r0 + 2 r1 + 4 r2), their global
+ * DOF ids d_dofs [nsub][8] int64, kappa_s d_kappa_sub [nsub] f64 (the same
+ * Gauss-weight binning the macro-element assembly uses) and, if d_beta_sub is
+ * not NULL, beta_s [nsub] (requires lor_set_reaction).  d_ess (uint8[N], may
+ * be NULL) receives 1 on essential (boundary) DOFs.  nsub = nel p^3.  All
+ * arrays are caller-owned device memory.  Requires lor_set_coefficient. */
+int lor_lor_mesh(lor_ctx* ctx, double* d_corners, int64_t* d_dofs, double* d_kappa_sub, double* d_beta_sub,
+                 uint8_t* d_ess, void* stream);
+
+/* Unstructured Q1 assembly, the comparator of the macro-element algorithm
+ * in Section 4.2 (one thread per degree of freedom of a sub-element, global
+ * CSR positions found by search): for any conforming hex mesh given as
+ * E-vectors (d_corners, d_dofs as above, one coefficient per element in
+ * d_kappa_sub, optional reaction coefficient d_beta_sub), adds each element's
+ * 8x8 block
+ *   K_rc = sum over the 2x2x2 Gauss points of kappa_s grad phi_r . grad phi_c
+ *          detJ (+ beta_s phi_r phi_c detJ)
+ * into d_values (f64 or f32 per dtype, nnz entries, zeroed first) of the CSR
+ * pattern d_rowptr int64[n+1] / d_colidx int32[nnz] (columns ascending per
+ * row), the position of each coupling found by binary search in its row.
+ * Rows and columns with d_ess[i] != 0 (may be NULL) are eliminated, their
+ * diagonal set to 1.  The context only carries the error state.  A coupling
+ * missing from the pattern or a detJ <= 0 is reported by the next
+ * lor_check.  Does not synchronise. */
+int lor_assemble_unstructured(lor_ctx* ctx, int64_t nsub, const double* d_corners, const int64_t* d_dofs,
+                              const double* d_kappa_sub, const double* d_beta_sub, int64_t n, int64_t nnz,
+                              const int64_t* d_rowptr, const int32_t* d_colidx, const uint8_t* d_ess, void* d_values,
+                              int dtype, void* stream);
+
 /* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum
  * factorisation (B = [B(x)B(x)d; B(x)d(x)B; d(x)B(x)B] with the 1D
  * interpolation/derivative matrices, D from lor_set_coefficient), in FP64.

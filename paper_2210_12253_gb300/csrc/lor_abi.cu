@@ -334,6 +334,31 @@ int lor_set_reaction(lor_ctx* c, const double* d_beta, void* stream) {
   return LOR_OK;
 }
 
+int lor_lor_mesh(lor_ctx* c, double* d_corners, int64_t* d_dofs, double* d_kappa_sub, double* d_beta_sub,
+                 uint8_t* d_ess, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_corners || !d_dofs || !d_kappa_sub) return set_err(c, LOR_EINVAL, "lor_lor_mesh: NULL output array");
+  if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_lor_mesh: call lor_set_coefficient first");
+  if (d_beta_sub && !c->have_beta) return set_err(c, LOR_ESTATE, "lor_lor_mesh: beta_sub asked without lor_set_reaction");
+  cudaError_t e = lor_launch_lor_mesh(c->m, c->T, c->kappa, d_beta_sub ? c->beta : nullptr, d_corners, d_dofs,
+                                      d_kappa_sub, d_beta_sub, d_ess, S(stream));
+  return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_lor_mesh");
+}
+
+int lor_assemble_unstructured(lor_ctx* c, int64_t nsub, const double* d_corners, const int64_t* d_dofs,
+                              const double* d_kappa_sub, const double* d_beta_sub, int64_t n, int64_t nnz,
+                              const int64_t* d_rowptr, const int32_t* d_colidx, const uint8_t* d_ess, void* d_values,
+                              int dtype, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (dtype != LOR_F64 && dtype != LOR_F32) return set_err(c, LOR_EINVAL, "lor_assemble_unstructured: bad dtype");
+  if (nsub < 0 || n < 0 || nnz < 0 || (nsub > 0 && (!d_corners || !d_dofs || !d_kappa_sub)) || !d_rowptr ||
+      !d_colidx || (nnz > 0 && !d_values))
+    return set_err(c, LOR_EINVAL, "lor_assemble_unstructured: bad arguments");
+  cudaError_t e = lor_launch_assemble_unstructured(nsub, d_corners, d_dofs, d_kappa_sub, d_beta_sub, n, nnz, d_rowptr,
+                                                   d_colidx, d_ess, d_values, dtype, c->d_status, S(stream));
+  return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_assemble_unstructured");
+}
+
 int lor_check(lor_ctx* c, void* stream) {
   if (!c) return LOR_EINVAL;
   int flags = 0;
@@ -345,6 +370,8 @@ int lor_check(lor_ctx* c, void* stream) {
     if (flags & LOR_FLAG_TIMEOUT)
       return set_err(c, LOR_ETIMEOUT, "a bounded device wait expired (a bulk copy into shared memory never completed)");
     if (flags & LOR_FLAG_BAD_GEOM) return set_err(c, LOR_EGEOM, "a Jacobian determinant is <= 0");
+    if (flags & LOR_FLAG_BAD_PATTERN)
+      return set_err(c, LOR_EINVAL, "lor_assemble_unstructured: a coupling is missing from the given CSR pattern");
     return set_err(c, LOR_EINVAL, "kappa (and beta) must be finite and > 0 at every Gauss point");
   }
   return LOR_OK;

@@ -79,6 +79,7 @@ void lor_count_launch();
 #define LOR_FLAG_BAD_KAPPA 1
 #define LOR_FLAG_BAD_GEOM 2
 #define LOR_FLAG_TIMEOUT 4  // a bounded wait on an mbarrier expired (a TMA copy never completed)
+#define LOR_FLAG_BAD_PATTERN 8  // the unstructured assembly met a coupling missing from the given CSR pattern
 
 // Elements of padding after the nnz CSR values of the context's value arrays
 // (a tile's bulk copy may end up to 15 bytes past the last value).
@@ -215,6 +216,14 @@ cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, co
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                       const double* kappa, const double* x, const double* gy, double* gx,
                                       double* gkappa, cudaStream_t s);
+// unstructured assembly (k_unstructured.cu)
+cudaError_t lor_launch_lor_mesh(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta,
+                                double* corners, int64_t* dofs, double* ksub, double* bsub, uint8_t* ess,
+                                cudaStream_t s);
+cudaError_t lor_launch_assemble_unstructured(int64_t nsub, const double* corners, const int64_t* dofs,
+                                             const double* ksub, const double* bsub, int64_t n, int64_t nnz,
+                                             const int64_t* rowptr, const int32_t* colidx, const uint8_t* ess,
+                                             void* vals, int dtype, int* status, cudaStream_t s);
 // sparse / solver kernels (k_sparse.cu)
 // The SpMV-type kernels read the CSR values only: the columns and row starts
 // of the 27-point LOR pattern are recomputed from the grid (the pattern

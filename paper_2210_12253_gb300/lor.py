@@ -21,7 +21,7 @@ EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
-    "lor_precond_apply_noalloc", "lor_set_reaction",
+    "lor_precond_apply_noalloc", "lor_set_reaction", "lor_lor_mesh", "lor_assemble_unstructured",
 ]
 
 
@@ -60,6 +60,10 @@ def load_library(path=LIB):
     L.lor_set_coefficient.argtypes = [vp, vp, vp]
     L.lor_set_reaction.restype = i
     L.lor_set_reaction.argtypes = [vp, vp, vp]
+    L.lor_lor_mesh.restype = i
+    L.lor_lor_mesh.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.lor_assemble_unstructured.restype = i
+    L.lor_assemble_unstructured.argtypes = [vp, i64, vp, vp, vp, vp, i64, i64, vp, vp, vp, vp, i, vp]
     L.lor_check.restype = i
     L.lor_check.argtypes = [vp, vp]
     L.lor_build_pattern.restype = i
@@ -219,6 +223,43 @@ class LOR:
         """Assemble into the context's own matrix (used by the preconditioner)."""
         code, _ = _dtype_code(dtype)
         self._call("lor_assemble", None, code)
+
+    def lor_mesh(self, with_beta=False):
+        """The LOR mesh as a general hex mesh: (corners [nsub, 8, 3] f64,
+        dofs [nsub, 8] int64, kappa_s [nsub], beta_s [nsub] or None,
+        essential mask uint8[N])."""
+        nsub = self.nel * self.p ** 3
+        corners = self._new(nsub * 24).reshape(nsub, 8, 3)
+        dofs = torch.empty((nsub, 8), dtype=torch.int64, device=self.device)
+        ks = self._new(nsub)
+        bs = self._new(nsub) if with_beta else None
+        ess = torch.empty(self.ndof, dtype=torch.uint8, device=self.device)
+        self._call("lor_lor_mesh", _ptr(corners), _ptr(dofs), _ptr(ks), _ptr(bs), _ptr(ess))
+        return corners, dofs, ks, bs, ess
+
+    def assemble_unstructured(self, corners, dofs, kappa_sub, rowptr, colidx, n, beta_sub=None, ess=None,
+                              dtype=torch.float64, out=None):
+        """Unstructured Q1 assembly of a general hex mesh (E-vectors) into the
+        CSR pattern (rowptr int64[n+1], colidx int32[nnz]); the comparator of
+        the macro-element assembly."""
+        code, tdt = _dtype_code(dtype)
+        nsub = int(kappa_sub.numel())
+        nnz = int(colidx.numel())
+        _dev(corners, torch.float64, nsub * 24, "corners")
+        _dev(dofs, torch.int64, nsub * 8, "dofs")
+        _dev(kappa_sub, torch.float64, nsub, "kappa_sub")
+        if beta_sub is not None:
+            _dev(beta_sub, torch.float64, nsub, "beta_sub")
+        _dev(rowptr, torch.int64, n + 1, "rowptr")
+        _dev(colidx, torch.int32, nnz, "colidx")
+        if ess is not None:
+            _dev(ess, torch.uint8, n, "ess")
+        if out is None:
+            out = self._new(nnz, tdt)
+        _dev(out, tdt, nnz, "values")
+        self._call("lor_assemble_unstructured", nsub, _ptr(corners), _ptr(dofs), _ptr(kappa_sub), _ptr(beta_sub),
+                   n, nnz, _ptr(rowptr), _ptr(colidx), _ptr(ess), _ptr(out), code)
+        return out
 
     def apply(self, x, out=None):
         """Step S2.1: y = A_p x (FP64, Dirichlet rows return x)."""
