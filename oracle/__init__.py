@@ -55,6 +55,8 @@ def _declare(L):
         "orc_csr_copy": (None, [vp, _i64p, _i64p, _dp]),
         "orc_csr_free": (None, [vp]),
         "orc_lor_rows": (i, [i, i, i, _dp, i, i, _dp, vp, i, i64, _i64p, i, _i32p, _i64p, _dp]),
+        "orc_lor_edge_count": (i64, [i, i, i, i]),
+        "orc_discrete_gradient": (i, [i, i, i, i, _i64p, _i64p, _dp]),
         "orc_csr_spmv": (None, [i64, _i64p, _i64p, _dp, _dp, _dp]),
         "orc_csr_diagonal": (None, [i64, _i64p, _i64p, _dp, _dp]),
         "orc_power_lambda_max": (d, [i64, _i64p, _i64p, _dp, _dp, i]),
@@ -237,6 +239,15 @@ def lor_rows(mesh, p, q, kappa, rows, dirichlet=True, cap=64, beta=None):
     _check(lib().orc_lor_rows(*mesh.args(), p, q, _f64(kappa).ravel(), _ptr(b), int(dirichlet), n, rows, cap,
                               counts, cols, vals), "lor_rows")
     return counts, cols, vals
+
+
+# ---------------------------------------------------------------- H(curl) topology
+def discrete_gradient(nex, ney, nez, p):
+    """LOR vertex-to-edge discrete gradient as CSR (rowptr, colidx int64, values)."""
+    ne = lib().orc_lor_edge_count(nex, ney, nez, p)
+    rowptr, colidx, values = np.zeros(ne + 1, np.int64), np.zeros(2 * ne, np.int64), np.zeros(2 * ne)
+    _check(lib().orc_discrete_gradient(nex, ney, nez, p, rowptr, colidx, values), "discrete_gradient")
+    return rowptr, colidx, values
 
 
 # ---------------------------------------------------------------- sparse / solver

@@ -971,6 +971,46 @@ int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const
 }
 
 /* ------------------------------------------------------------------------- */
+/* Discrete gradient of the LOR mesh (Section 3, the matrix Algorithm 1 builds */
+/* for the H(curl) solver): it maps the H1 LOR space (values at the LOR       */
+/* vertices, i.e. the global GLL grid points) to the lowest-order H(curl)     */
+/* space on the LOR edges.  Row i (an edge) holds -1 at the edge's tail vertex */
+/* and +1 at its head vertex.  Reading R17 (the paper leaves the numbering to  */
+/* the element restriction): the x-directed edges first, then the y- and      */
+/* z-directed ones, each set lexicographic by its tail vertex (I fastest); an */
+/* edge runs from its tail (I,J,K) to the next vertex along its axis, so the  */
+/* tail has the lower global index and each row's columns are ascending.      */
+/* ------------------------------------------------------------------------- */
+int64_t orc_lor_edge_count(int nex, int ney, int nez, int p) {
+  int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
+  return (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1);
+}
+
+/* rowptr[nedge+1], colidx[2 nedge], values[2 nedge] */
+int orc_discrete_gradient(int nex, int ney, int nez, int p, int64_t* rowptr, int64_t* colidx, double* values) {
+  int64_t n[3] = {(int64_t)nex * p + 1, (int64_t)ney * p + 1, (int64_t)nez * p + 1};
+  int64_t stride[3] = {1, n[0], n[0] * n[1]};
+  int64_t e = 0;
+  for (int d = 0; d < 3; ++d) {
+    int64_t m[3] = {n[0], n[1], n[2]};
+    m[d] -= 1; /* tails: all vertices but the last along the edge's axis */
+    for (int64_t K = 0; K < m[2]; ++K)
+      for (int64_t J = 0; J < m[1]; ++J)
+        for (int64_t I = 0; I < m[0]; ++I) {
+          int64_t tail = I + n[0] * (J + n[1] * K);
+          rowptr[e] = 2 * e;
+          colidx[2 * e] = tail;
+          colidx[2 * e + 1] = tail + stride[d];
+          values[2 * e] = -1.0;
+          values[2 * e + 1] = 1.0;
+          ++e;
+        }
+  }
+  rowptr[e] = 2 * e;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Sparse kernels and preconditioners on a CSR matrix (Step S2.2: the solve    */
 /* phase reduces to spmv and vector updates).                                  */
 /* ------------------------------------------------------------------------- */
