@@ -13,7 +13,8 @@ adjoint gradient dJ/dtheta (forward solve, adjoint solve, gradient kernel) on
 the 24^3-element, p = 5 workload under "gradient"; the same step with the
 reaction term of the definite Helmholtz problem under "helmholtz"; the
 macro-element vs unstructured LOR assembly at ~4M DOFs per degree under
-"assembly_comparator".
+"assembly_comparator"; the discrete gradient and vertex coordinates of the
+32^3 p = 6 LOR mesh under "hcurl_topology".
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
@@ -301,6 +302,9 @@ def run_gpu(args, rank, world, local_rank):
     comparator = None
     if not args.no_comparator:
         comparator = run_comparator(args, dev)
+    hcurl = None
+    if not args.no_hcurl:
+        hcurl = run_hcurl(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -317,7 +321,7 @@ def run_gpu(args, rank, world, local_rank):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps},
            "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad,
-           "helmholtz": helm, "assembly_comparator": comparator}
+           "helmholtz": helm, "assembly_comparator": comparator, "hcurl_topology": hcurl}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     op.close()
@@ -558,6 +562,55 @@ def run_comparator(args, dev):
             "rows": rows}
 
 
+def run_hcurl(args, dev):
+    """The LOR mesh's H(curl) topology on the 32^3, p = 6 mesh (7.19M vertices,
+    21.5M edges): the discrete gradient (Algorithm 1) and the deduplicated
+    vertex coordinates; median of 5 event-timed launches after one warm-up,
+    L2 flushed before each.  Both are HBM-bound writes: 32 bytes per edge
+    (row pointer 8, two int32 columns 8, two f64 values 16) and 24 bytes per
+    vertex."""
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import workload
+    from paper_2210_12253_gb300.perfmodel import hbm_peak_gbs
+
+    prob = workload(PCG_WORKLOAD)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ne = op.edge_count()
+    rp = torch.empty(ne + 1, dtype=torch.int64, device=dev)
+    ci = torch.empty(2 * ne, dtype=torch.int32, device=dev)
+    vals = torch.empty(2 * ne, dtype=torch.float64, device=dev)
+    xyz = torch.empty(3 * op.ndof, dtype=torch.float64, device=dev)
+    from paper_2210_12253_gb300.lor import _ptr
+
+    def timed(fn):
+        fn()
+        out = []
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    ms_g = timed(lambda: op._call("lor_discrete_gradient", _ptr(rp), _ptr(ci), _ptr(vals), None))
+    ms_x = timed(lambda: op._call("lor_vertex_coordinates", _ptr(xyz)))
+    peak, src = hbm_peak_gbs()
+    bg, bx = 32 * ne + 8, 24 * op.ndof
+    op.close()
+    return {"workload": PCG_WORKLOAD + " mesh (topology only)", "edges": ne, "vertices": op.ndof,
+            "discrete_gradient": {"ms": ms_g, "gbs": bg / (ms_g * 1e-3) / 1e9,
+                                  "frac_hbm": bg / (ms_g * 1e-3) / 1e9 / peak, "bytes": bg},
+            "vertex_coordinates": {"ms": ms_x, "gbs": bx / (ms_x * 1e-3) / 1e9,
+                                   "frac_hbm": bx / (ms_x * 1e-3) / 1e9 / peak, "bytes": bx},
+            "hbm_peak_gbs": peak, "peak_source": src}
+
+
 def run_sweep(args, dev):
     """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
     JSON object per degree (setup, FP64 and FP32 assembly, apply, backward,
@@ -698,6 +751,7 @@ def main(argv=None):
     ap.add_argument("--no-pcg", action="store_true", help="skip the 32^3 p=6 PCG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the 24^3 p=5 adjoint-gradient timing")
+    ap.add_argument("--no-hcurl", action="store_true", help="skip the discrete-gradient / vertex-coordinate timing")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip the macro-element vs unstructured LOR assembly comparison")
     ap.add_argument("--no-helmholtz", action="store_true",

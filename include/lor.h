@@ -184,6 +184,25 @@ int lor_assemble_unstructured(lor_ctx* ctx, int64_t nsub, const double* d_corner
                               const int64_t* d_rowptr, const int32_t* d_colidx, const uint8_t* d_ess, void* d_values,
                               int dtype, void* stream);
 
+/* Discrete gradient of the LOR mesh (Section 3, Algorithm 1), for the
+ * H(curl) auxiliary-space solver: the incidence matrix from the LOR vertices
+ * (the N global GLL grid points) to the LOR edges, as CSR with two entries per
+ * row: -1 at the edge's tail vertex, +1 at its head.  Edge order: all
+ * x-directed edges, then y-, then z-directed, each set lexicographic by its
+ * tail vertex (I fastest); an edge runs from its tail to the next vertex along
+ * its axis (so columns ascend).  *nedge (host, may be NULL) receives the
+ * number of edges; with all three arrays NULL only the count is returned.
+ * d_rowptr int64[nedge+1], d_colidx int32[2 nedge] (8-byte aligned),
+ * d_values f64[2 nedge] (16-byte aligned).  The matrix depends on the
+ * topology and p only. */
+int lor_discrete_gradient(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
+                          void* stream);
+
+/* Coordinates of the LOR vertices without duplicates (the vector AMS takes
+ * besides the discrete gradient): d_xyz f64[N][3], vertex I + nx(J + ny K) at
+ * T_e(GLL point) of the lowest-index element containing it. */
+int lor_vertex_coordinates(lor_ctx* ctx, double* d_xyz, void* stream);
+
 /* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum
  * factorisation (B = [B(x)B(x)d; B(x)d(x)B; d(x)B(x)B] with the 1D
  * interpolation/derivative matrices, D from lor_set_coefficient), in FP64.

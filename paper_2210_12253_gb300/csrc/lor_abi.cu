@@ -359,6 +359,27 @@ int lor_assemble_unstructured(lor_ctx* c, int64_t nsub, const double* d_corners,
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_assemble_unstructured");
 }
 
+int lor_discrete_gradient(lor_ctx* c, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
+                          void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (nedge) *nedge = lor_edge_count(c->m);
+  if (!d_rowptr && !d_colidx && !d_values) return LOR_OK;
+  if (!d_rowptr || !d_colidx || !d_values)
+    return set_err(c, LOR_EINVAL, "lor_discrete_gradient: give all three output arrays or none");
+  if (((uintptr_t)d_colidx & 7) || ((uintptr_t)d_values & 15))
+    return set_err(c, LOR_EINVAL, "lor_discrete_gradient: colidx must be 8-byte and values 16-byte aligned");
+  if (c->m.ndof > INT32_MAX) return set_err(c, LOR_EINVAL, "lor_discrete_gradient: more vertices than int32 columns");
+  cudaError_t e = lor_launch_discrete_gradient(c->m, d_rowptr, d_colidx, d_values, S(stream));
+  return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_discrete_gradient");
+}
+
+int lor_vertex_coordinates(lor_ctx* c, double* d_xyz, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_xyz) return set_err(c, LOR_EINVAL, "lor_vertex_coordinates: xyz is NULL");
+  cudaError_t e = lor_launch_vertex_coordinates(c->m, c->T, d_xyz, S(stream));
+  return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_vertex_coordinates");
+}
+
 int lor_check(lor_ctx* c, void* stream) {
   if (!c) return LOR_EINVAL;
   int flags = 0;

@@ -224,6 +224,11 @@ cudaError_t lor_launch_assemble_unstructured(int64_t nsub, const double* corners
                                              const double* ksub, const double* bsub, int64_t n, int64_t nnz,
                                              const int64_t* rowptr, const int32_t* colidx, const uint8_t* ess,
                                              void* vals, int dtype, int* status, cudaStream_t s);
+// H(curl) topology of the LOR mesh (k_hcurl.cu)
+int64_t lor_edge_count(const LorMesh& m);
+cudaError_t lor_launch_discrete_gradient(const LorMesh& m, int64_t* rowptr, int32_t* colidx, double* values,
+                                         cudaStream_t s);
+cudaError_t lor_launch_vertex_coordinates(const LorMesh& m, const LorTables& T, double* xyz, cudaStream_t s);
 // sparse / solver kernels (k_sparse.cu)
 // The SpMV-type kernels read the CSR values only: the columns and row starts
 // of the 27-point LOR pattern are recomputed from the grid (the pattern

@@ -22,6 +22,7 @@ EXPORTED = [
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
     "lor_precond_apply_noalloc", "lor_set_reaction", "lor_lor_mesh", "lor_assemble_unstructured",
+    "lor_discrete_gradient", "lor_vertex_coordinates",
 ]
 
 
@@ -60,6 +61,10 @@ def load_library(path=LIB):
     L.lor_set_coefficient.argtypes = [vp, vp, vp]
     L.lor_set_reaction.restype = i
     L.lor_set_reaction.argtypes = [vp, vp, vp]
+    L.lor_discrete_gradient.restype = i
+    L.lor_discrete_gradient.argtypes = [vp, vp, vp, vp, C.POINTER(i64), vp]
+    L.lor_vertex_coordinates.restype = i
+    L.lor_vertex_coordinates.argtypes = [vp, vp, vp]
     L.lor_lor_mesh.restype = i
     L.lor_lor_mesh.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.lor_assemble_unstructured.restype = i
@@ -223,6 +228,27 @@ class LOR:
         """Assemble into the context's own matrix (used by the preconditioner)."""
         code, _ = _dtype_code(dtype)
         self._call("lor_assemble", None, code)
+
+    def edge_count(self):
+        ne = C.c_int64(0)
+        self._call("lor_discrete_gradient", None, None, None, C.byref(ne))
+        return ne.value
+
+    def discrete_gradient(self):
+        """LOR vertex-to-edge discrete gradient (Algorithm 1): (rowptr int64,
+        colidx int32, values f64) CSR with two entries per edge."""
+        ne = self.edge_count()
+        rowptr = torch.empty(ne + 1, dtype=torch.int64, device=self.device)
+        colidx = torch.empty(2 * ne, dtype=torch.int32, device=self.device)
+        values = self._new(2 * ne)
+        self._call("lor_discrete_gradient", _ptr(rowptr), _ptr(colidx), _ptr(values), None)
+        return rowptr, colidx, values
+
+    def vertex_coordinates(self):
+        """Deduplicated LOR vertex coordinates [N, 3]."""
+        xyz = self._new(3 * self.ndof).reshape(self.ndof, 3)
+        self._call("lor_vertex_coordinates", _ptr(xyz))
+        return xyz
 
     def lor_mesh(self, with_beta=False):
         """The LOR mesh as a general hex mesh: (corners [nsub, 8, 3] f64,
