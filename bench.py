@@ -613,9 +613,11 @@ def run_hcurl(args, dev):
 
 def run_sweep(args, dev):
     """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
-    JSON object per degree (setup, FP64 and FP32 assembly, apply, backward,
-    one FP32 Chebyshev-Jacobi degree-3 application), CUDA-event timed, median
-    of `--sweep-reps` after one warm-up, L2 flushed before each launch."""
+    JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
+    (the kappa-gradient kernel), one FP32 Chebyshev-Jacobi degree-3
+    application), CUDA-event timed, median of `--sweep-reps` after one
+    warm-up, L2 flushed before each launch; then the time per PCG iteration
+    (30 iterations) in mixed precision and in FP64."""
     import numpy as np
     import torch
 
@@ -630,7 +632,7 @@ def run_sweep(args, dev):
         prob = workload("c5_p%d" % p)
         op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
         kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
-        del prob.kappa
+        prob.kappa = None
         x = torch.tensor(np.random.default_rng(5).standard_normal(op.ndof), device=dev)
         y, z, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
         gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
@@ -665,8 +667,22 @@ def run_sweep(args, dev):
             res[name] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
                          "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        # PCG per iteration (30 iterations from x0 = 0, fixed count), mixed
+        # precision and FP64, with the same lambda_max
+        b = torch.tensor(prob.rhs, device=dev)
+        for tag, dt in (("pcg_mixed", torch.float32), ("pcg_f64", torch.float64)):
+            op.precond_setup("cheb", dt, degree=3, lambda_max=lam)
+            op.pcg_solve(b, 1e-30, 3, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, its, _ = op.pcg_solve(b, 1e-30, 30, raise_on_noconv=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_it = e0.elapsed_time(e1) / its
+            res[tag] = {"ms_per_iteration": ms_it, "gdofs_iterations": op.ndof / (ms_it * 1e-3) / 1e9}
         op.close()
-        del op, kappa, x, y, z, gx, gk
+        del op, kappa, x, y, z, gx, gk, b
         torch.cuda.empty_cache()
         print(json.dumps(res), flush=True)
         out.append(res)

@@ -101,8 +101,9 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
         f, b = kernel_work("backward", p, ndof, nel, nnz, vbytes)
         return f + reaction_extra_apply_flops_per_element(p) * nel, b + 8 * nq
     if kind == "precond":
-        # degree-1 SpMV passes over the matrix (values + int32 columns + row
-        # pointers) and ~6 vector streams per step
-        spmv = nnz * (vbytes + 4) + 8 * (ndof + 1)
+        # degree-1 SpMV passes over the matrix values (the pattern-implicit
+        # SpMV reads no column indices or row pointers: they are the closed
+        # form of the 27-point pattern) and ~6 vector streams per step
+        spmv = nnz * vbytes
         return 2 * nnz * (degree - 1), (degree - 1) * (spmv + 6 * vbytes * ndof) + 3 * 8 * ndof
     raise KeyError(kind)
