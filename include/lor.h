@@ -94,6 +94,25 @@ const char* lor_last_error(const lor_ctx* ctx);
  * the context (NULL on failure). */
 int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, void* stream);
 
+/* Create a context on a general conforming hex mesh given in the
+ * element-restriction form of Step S1.1 (the maps G of Eq. (4)): nel
+ * trilinear elements with corners d_corners [nel][8][3] f64 (corner
+ * c0 + 2 c1 + 4 c2 at reference vertex (2 c0 - 1, 2 c1 - 1, 2 c2 - 1)), the
+ * element-to-DOF map d_elem_dofs [nel][(p+1)^3] int64 (local GLL node
+ * i + n(j + n k), n = p+1, to a global DOF in [0, ndof); nodes shared by
+ * elements share their DOF) and the essential-DOF mask d_ess uint8[ndof]
+ * (NULL: none).  kappa, beta, x, y and every per-point array use the element
+ * order and the same local node / Gauss point order as on the structured
+ * mesh.  The LOR pattern is built here from the map (the sub-hexes' 8-DOF
+ * couplings, sorted and de-duplicated per row; vertex valence up to 64) and
+ * the LOR assembly finds CSR positions by binary search; lor_spmv and the
+ * smoother read the explicit pattern.  lor_lor_mesh, lor_discrete_gradient
+ * and lor_vertex_coordinates are for structured meshes only (LOR_ESTATE).
+ * LOR_EINVAL for a map entry out of range, LOR_EGEOM for detJ <= 0.  All
+ * input arrays are device memory, copied.  Synchronises the stream. */
+int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const double* d_corners,
+                       const int64_t* d_elem_dofs, const uint8_t* d_ess, void* stream);
+
 /* Free the context and every device buffer it owns.  Synchronises the device
  * work of the context first.  NULL is accepted. */
 int lor_destroy(lor_ctx* ctx);

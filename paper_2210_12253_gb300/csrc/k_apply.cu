@@ -9,14 +9,19 @@ cudaError_t lor_apply_mass_dispatch(const LorMesh& m, const LorTables& T, const 
 cudaError_t lor_backward_mass_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                        const double* kappa, const double* x, const double* gy, double* gx,
                                        double* gk, cudaStream_t s);
+// general meshes (k_apply_general.cu)
+cudaError_t lor_apply_general_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                                       const double* x, double* y, cudaStream_t s);
+cudaError_t lor_backward_general_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                                          const double* kappa, const double* x, const double* gy, double* gx,
+                                          double* gk, cudaStream_t s);
 
 namespace {
 
 // y <- x on essential DOFs, 0 elsewhere (the apply then adds the free rows).
 __global__ void k_init_output(LorMesh m, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m.ndof; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t I = r % m.nx, J = (r / m.nx) % m.ny, K = r / (m.nx * m.ny);
-    y[r] = lor_is_essential(I, J, K, m.nx, m.ny, m.nz) ? x[r] : 0.0;
+    y[r] = lor_dof_essential(m, r) ? x[r] : 0.0;
   }
 }
 
@@ -37,8 +42,9 @@ cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double*
 
 cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                         const double* x, double* y, cudaStream_t s) {
+  if (m.edofs) return lor_apply_general_dispatch(m, T, Dq, Mq, x, y, s);
   if (Mq) return lor_apply_mass_dispatch(m, T, Dq, Mq, x, y, s);
-  return apply_dispatch<false>(m, T, Dq, nullptr, x, y, s);
+  return apply_dispatch<false, false>(m, T, Dq, nullptr, x, y, s);
 }
 
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
@@ -49,6 +55,7 @@ cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, cons
     if (err != cudaSuccess) return err;
   }
   if (!gx && !gkappa) return cudaSuccess;
+  if (m.edofs) return lor_backward_general_dispatch(m, T, Dq, Mq, kappa, x, gy, gx, gkappa, s);
   if (Mq) return lor_backward_mass_dispatch(m, T, Dq, Mq, kappa, x, gy, gx, gkappa, s);
-  return backward_dispatch<false>(m, T, Dq, nullptr, kappa, x, gy, gx, gkappa, s);
+  return backward_dispatch<false, false>(m, T, Dq, nullptr, kappa, x, gy, gx, gkappa, s);
 }

@@ -200,7 +200,8 @@ __device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const dou
 
 // ---- stages over all lines of E elements (e_first .. e_first+E-1) ----
 // X: u (gathered from global, masked) -> A1[c][k][j][g0] = (B u, d u) along x.
-template <int P>
+// GEN: through the general element-to-DOF map and essential mask.
+template <int P, bool GEN>
 __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
                                         const double* __restrict__ x, double* A) {
   using Z = Sz<P>;
@@ -210,15 +211,24 @@ __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64
     const int64_t e = e_first + le;
     if (e >= m.nel) continue;
     const int j = jk % N, k = jk / N;
-    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
-    const int64_t J = ey * P + j, K = ez * P + k;
-    const bool row_ess = J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1;
-    const double* xr = x + (ex * P) + m.nx * (J + m.ny * K);
     double u[N];
+    if constexpr (GEN) {
+      const int64_t* dm = m.edofs + e * (N * N * N) + jk * N;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int64_t I = ex * P + i;
-      u[i] = (row_ess || I == 0 || I == m.nx - 1) ? 0.0 : xr[i];
+      for (int i = 0; i < N; ++i) {
+        const int64_t d = dm[i];
+        u[i] = m.ess[d] ? 0.0 : x[d];
+      }
+    } else {
+      const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+      const int64_t J = ey * P + j, K = ez * P + k;
+      const bool row_ess = J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1;
+      const double* xr = x + (ex * P) + m.nx * (J + m.ny * K);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int64_t I = ex * P + i;
+        u[i] = (row_ess || I == 0 || I == m.nx - 1) ? 0.0 : xr[i];
+      }
     }
     double e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], um;
     fold_n<P>(u, e_, o_, um);
@@ -380,7 +390,7 @@ __device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P>& t, int
 }
 
 // X': A1 (U0, U1) -> y_line = d_x^T U0 + B_x^T U1, scatter-added into y.
-template <int P>
+template <int P, bool GEN>
 __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
                                           const double* A, double* __restrict__ y) {
   using Z = Sz<P>;
@@ -399,19 +409,28 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int
     for (int g = 0; g < Q; ++g) v[g] = a1[g];  // U0 (d^T)
     fold_q<P>(v, e2, o2, m2);
     bwd<P, true, true>(t, e1, o1, m1, e2, o2, m2, yl);
-    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
-    const int64_t J = ey * P + j, K = ez * P + k;
-    if (J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1) continue;
-    double* yr = y + (ex * P) + m.nx * (J + m.ny * K);
+    if constexpr (GEN) {
+      const int64_t* dm = m.edofs + e * (N * N * N) + jk * N;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int64_t I = ex * P + i;
-      if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, yl[i]);
+      for (int i = 0; i < N; ++i) {
+        const int64_t d = dm[i];
+        if (!m.ess[d]) atomicAdd(y + d, yl[i]);
+      }
+    } else {
+      const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+      const int64_t J = ey * P + j, K = ez * P + k;
+      if (J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1) continue;
+      double* yr = y + (ex * P) + m.nx * (J + m.ny * K);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int64_t I = ex * P + i;
+        if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, yl[i]);
+      }
     }
   }
 }
 
-template <int P, bool MASS>
+template <int P, bool MASS, bool GEN>
 __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const double* __restrict__ Dq,
                                                     const double* __restrict__ Mq, const double* __restrict__ x,
                                                     double* __restrict__ y) {
@@ -422,7 +441,7 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
   double* A = smem + Z::TABLES;
   __syncthreads();
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
-    stage_x<P>(m, t, e_first, E, x, A);
+    stage_x<P, GEN>(m, t, e_first, E, x, A);
     __syncthreads();
     stage_y<P>(m, t, e_first, E, A);
     __syncthreads();
@@ -440,7 +459,7 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
     __syncthreads();
     stage_y_t<P>(m, t, e_first, E, A);
     __syncthreads();
-    stage_x_t<P>(m, t, e_first, E, A, y);
+    stage_x_t<P, GEN>(m, t, e_first, E, A, y);
     __syncthreads();
   }
 }
@@ -449,7 +468,7 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
 // next EB); gkappa = grad(x)^T (D / kappa) grad(gy) on each z line, and
 // gx = A_p gy (with the reaction term if present) through the same
 // transposed stages as the apply.
-template <int P, bool MASS>
+template <int P, bool MASS, bool GEN>
 __global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
                                                              const double* __restrict__ Dq,
                                                              const double* __restrict__ Mq,
@@ -466,8 +485,8 @@ __global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(Lor
   double* AX = A + (size_t)E * Z::PER_ELEM;        // x:  element slots E..2E-1
   __syncthreads();
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
-    stage_x<P>(m, t, e_first, E, gy, A);
-    if (gkappa) stage_x<P>(m, t, e_first, E, x, AX);
+    stage_x<P, GEN>(m, t, e_first, E, gy, A);
+    if (gkappa) stage_x<P, GEN>(m, t, e_first, E, x, AX);
     __syncthreads();
     stage_y<P>(m, t, e_first, E, A);
     if (gkappa) stage_y<P>(m, t, e_first, E, AX);
@@ -507,7 +526,7 @@ __global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(Lor
     if (gx) {
       stage_y_t<P>(m, t, e_first, E, A);
       __syncthreads();
-      stage_x_t<P>(m, t, e_first, E, A, gx);
+      stage_x_t<P, GEN>(m, t, e_first, E, A, gx);
     }
     __syncthreads();
   }
@@ -528,39 +547,39 @@ cudaError_t configure(K kernel, size_t bytes, unsigned* mask) {
   return cudaSuccess;
 }
 
-template <int P, bool MASS>
+template <int P, bool MASS, bool GEN>
 cudaError_t apply_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
                     double* y, cudaStream_t s) {
   using Z = Sz<P>;
   const size_t bytes = sizeof(double) * (Z::TABLES + (size_t)Z::E * Z::PER_ELEM);
   static unsigned mask = 0;
-  cudaError_t err = configure(k_apply<P, MASS>, bytes, &mask);
+  cudaError_t err = configure(k_apply<P, MASS, GEN>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply<P, MASS><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
+  k_apply<P, MASS, GEN><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
-template <int P, bool MASS>
+template <int P, bool MASS, bool GEN>
 cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* kappa,
                        const double* x, const double* gy, double* gx, double* gk, cudaStream_t s) {
   using Z = Sz<P>;
   const size_t bytes = sizeof(double) * (Z::TABLES + 2 * (size_t)Z::EB * Z::PER_ELEM);
   static unsigned mask = 0;
-  cudaError_t err = configure(k_apply_backward<P, MASS>, bytes, &mask);
+  cudaError_t err = configure(k_apply_backward<P, MASS, GEN>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::EB - 1) / Z::EB;
-  k_apply_backward<P, MASS><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
+  k_apply_backward<P, MASS, GEN><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
   lor_count_launch();
   return cudaGetLastError();
 }
 
-template <bool MASS>
+template <bool MASS, bool GEN>
 cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
                            double* y, cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: return apply_p<P, MASS>(m, T, Dq, Mq, x, y, s);
+  case P: return apply_p<P, MASS, GEN>(m, T, Dq, Mq, x, y, s);
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE
@@ -568,13 +587,13 @@ cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const double* D
   }
 }
 
-template <bool MASS>
+template <bool MASS, bool GEN>
 cudaError_t backward_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                               const double* kappa, const double* x, const double* gy, double* gx, double* gk,
                               cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: return backward_p<P, MASS>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
+  case P: return backward_p<P, MASS, GEN>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

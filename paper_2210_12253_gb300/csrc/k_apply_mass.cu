@@ -6,11 +6,11 @@
 
 cudaError_t lor_apply_mass_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                     const double* x, double* y, cudaStream_t s) {
-  return apply_dispatch<true>(m, T, Dq, Mq, x, y, s);
+  return apply_dispatch<true, false>(m, T, Dq, Mq, x, y, s);
 }
 
 cudaError_t lor_backward_mass_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                        const double* kappa, const double* x, const double* gy, double* gx,
                                        double* gk, cudaStream_t s) {
-  return backward_dispatch<true>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
+  return backward_dispatch<true, false>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
 }

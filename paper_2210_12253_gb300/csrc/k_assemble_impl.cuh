@@ -109,7 +109,7 @@ constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P 
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
 
-template <int P, typename VT, bool MASS>
+template <int P, typename VT, bool MASS, bool GEN>
 __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTables T,
                                                              const double* __restrict__ kappa,
                                                              const double* __restrict__ beta,
@@ -270,41 +270,61 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
     hadamard_axis<VT, 1>(K);
     hadamard_axis<VT, 2>(K);
 
-    // Scatter into the CSR values (closed-form positions), skipping essential
+    // Scatter into the CSR values (closed-form positions on the structured
+    // grid, binary search in the row on a general mesh), skipping essential
     // rows and columns (their diagonal was pre-set to 1).
-    const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
-    const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
+    if constexpr (GEN) {
+      constexpr int N = P + 1;
+      const int64_t* dm = m.edofs + e * (N * N * N);
+      int64_t dv[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
-      if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
-      const int64_t base = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
-      const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
+      for (int r = 0; r < 8; ++r) dv[r] = dm[(a + (r & 1)) + N * ((b + ((r >> 1) & 1)) + N * (c + (r >> 2)))];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
-        if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
-        const int di = (t & 1) - (r & 1), dj = ((t >> 1) & 1) - ((r >> 1) & 1), dk = (t >> 2) - (r >> 2);
-        atomic_add<VT>(vals + base + (dk * cy + dj) * cx + di, K[sym(r, t)]);
+      for (int r = 0; r < 8; ++r) {
+        if (m.ess[dv[r]]) continue;
+        const int64_t rb = m.rowptr[dv[r]], re = m.rowptr[dv[r] + 1];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (m.ess[dv[t]]) continue;
+          const int64_t pos = lor_find_col(m.colidx, rb, re, dv[t]);
+          if (pos >= 0) atomic_add<VT>(vals + pos, K[sym(r, t)]);
+        }
+      }
+    } else {
+      const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+      const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
+        if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
+        const int64_t base = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
+        const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
+          if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
+          const int di = (t & 1) - (r & 1), dj = ((t >> 1) & 1) - ((r >> 1) & 1), dk = (t >> 2) - (r >> 2);
+          atomic_add<VT>(vals + base + (dk * cy + dj) * cx + di, K[sym(r, t)]);
+        }
       }
     }
   }
 }
 
-template <int P, typename VT, bool MASS>
+template <int P, typename VT, bool MASS, bool GEN>
 void launch_assemble_p(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
                        cudaStream_t s) {
-  k_assemble<P, VT, MASS><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(
+  k_assemble<P, VT, MASS, GEN><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(
       m, T, kappa, beta, vals);
   lor_count_launch();
 }
 
-template <typename VT, bool MASS>
+template <typename VT, bool MASS, bool GEN>
 cudaError_t assemble_dispatch(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
                               cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: launch_assemble_p<P, VT, MASS>(m, T, kappa, beta, vals, s); break;
+  case P: launch_assemble_p<P, VT, MASS, GEN>(m, T, kappa, beta, vals, s); break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

@@ -4,10 +4,10 @@
 
 cudaError_t lor_assemble_mass_dispatch(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta,
                                        double* vals, cudaStream_t s) {
-  return assemble_dispatch<double, true>(m, T, kappa, beta, vals, s);
+  return assemble_dispatch<double, true, false>(m, T, kappa, beta, vals, s);
 }
 
 cudaError_t lor_assemble_mass_dispatch(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta,
                                        float* vals, cudaStream_t s) {
-  return assemble_dispatch<float, true>(m, T, kappa, beta, vals, s);
+  return assemble_dispatch<float, true, false>(m, T, kappa, beta, vals, s);
 }

@@ -181,6 +181,11 @@ __global__ void __launch_bounds__(128) k_load_vector(LorMesh m, LorTables T, con
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       double s = 0.0;
       for (int g0 = 0; g0 < Q; ++g0) s += sB[g0 * N + i] * t2[g0 + Q * (j + N * k)];
+      if (m.edofs) {
+        const int64_t d = m.edofs[e * (int64_t)N * N * N + idx];
+        if (!m.ess[d]) atomicAdd(b + d, s);
+        continue;
+      }
       const int64_t I = ex * P + i, J = ey * P + j, K = ez * P + k;
       if (!lor_is_essential(I, J, K, m.nx, m.ny, m.nz)) atomicAdd(b + I + m.nx * (J + m.ny * K), s);
     }

@@ -361,6 +361,57 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
   if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
 }
 
+// ---- the same modes on an explicit CSR pattern (general meshes, whose LOR
+// pattern has no closed form): kLanes lanes per row read consecutive entries
+// of the row and combine by shuffles; every warp runs the same number of row
+// rounds (the grid loops), so the shuffles stay uniform and the reducing mode
+// can finish in the last CTA.
+constexpr int kLanes = 4;
+
+template <typename VT, typename XT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restrict__ vals, const VT* __restrict__ dinv,
+                                                  const XT* __restrict__ x, const double* __restrict__ r,
+                                                  VT* __restrict__ d, VT c1, VT c2, VT* __restrict__ zout,
+                                                  double* __restrict__ y, double* __restrict__ partial,
+                                                  unsigned* __restrict__ counter, double* __restrict__ out) {
+  const int64_t n = m.ndof;
+  const int64_t rows_per_round = (int64_t)gridDim.x * blockDim.x / kLanes;
+  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kLanes;
+  const int group = (threadIdx.x & 31) / kLanes, lane = threadIdx.x & (kLanes - 1);
+  double acc = 0.0;
+  for (int64_t base = warp_first; base < n; base += rows_per_round) {
+    const int64_t i = base + group;
+    const bool valid = i < n;
+    VT s = 0;
+    if (valid) {
+      const int64_t b = m.rowptr[i], e = m.rowptr[i + 1];
+      for (int64_t j = b + lane; j < e; j += kLanes) s += vals[j] * (VT)x[m.colidx[j]];
+    }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (!valid || lane != 0) continue;
+    if constexpr (MODE == ST_SPMV) {
+      y[i] = (double)s;
+    } else if constexpr (MODE == ST_DINV_SPMV) {
+      y[i] = (double)(dinv[i] * s);
+    } else {
+      const double ri = r[i];
+      const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
+      const VT zn = (VT)x[i] + dn;
+      if constexpr (MODE == ST_CHEB_DOT) {
+        y[i] = (double)zn;
+        acc += ri * (double)zn;
+      } else if (y) {
+        y[i] = (double)zn;
+      } else {
+        d[i] = dn;
+        zout[i] = zn;
+      }
+    }
+  }
+  if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
+}
+
 // Persistent grid: every SM filled to the kernel's occupancy (at most one CTA
 // per tile; the reducing mode at most LOR_PCG_MAX_BLOCKS CTAs).  The shared
 // memory limit is raised once per device.
@@ -393,6 +444,15 @@ template <typename VT, typename XT, int MODE>
 cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, const XT* x, const double* r, VT* d,
                            double c1, double c2, VT* zout, double* y, double* partial, unsigned* counter,
                            double* out, int* status, cudaStream_t s) {
+  if (m.rowptr) {  // general mesh: explicit CSR pattern
+    const int64_t want = (m.ndof * kLanes + kThreads - 1) / kThreads;
+    const int64_t cap = MODE == ST_CHEB_DOT ? LOR_PCG_MAX_BLOCKS : 152 * 8;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    k_csr<VT, XT, MODE><<<grid, kThreads, 0, s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y, partial, counter,
+                                                  out);
+    lor_count_launch();
+    return cudaGetLastError();
+  }
   int grid = 0;
   cudaError_t err = stencil_grid<VT, XT, MODE>(m, &grid);
   if (err != cudaSuccess) return err;
@@ -405,6 +465,11 @@ cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, con
 template <typename VT>
 __global__ void k_diag_inv(LorMesh m, const VT* __restrict__ vals, VT* __restrict__ dinv) {
   LOR_GRID_STRIDE(i, m.ndof) {
+    if (m.rowptr) {
+      const int64_t pos = lor_find_col(m.colidx, m.rowptr[i], m.rowptr[i + 1], i);
+      dinv[i] = (VT)1 / vals[pos];
+      continue;
+    }
     int64_t I, J, K;
     grid_index(m, i, I, J, K);
     dinv[i] = (VT)1 / vals[lor_entry_pos(I, J, K, 0, 0, 0, m.nx, m.ny, m.nz)];
@@ -620,8 +685,7 @@ __global__ void k_pcg_direction(LorMesh m, const double* __restrict__ S, int new
   LOR_GRID_STRIDE(i, m.ndof) {
     const double pi = first ? z[i] : z[i] + beta * p[i];
     p[i] = pi;
-    const int64_t I = i % m.nx, J = (i / m.nx) % m.ny, K = i / (m.nx * m.ny);
-    q[i] = lor_is_essential(I, J, K, m.nx, m.ny, m.nz) ? pi : 0.0;
+    q[i] = lor_dof_essential(m, i) ? pi : 0.0;
   }
 }
 

@@ -83,18 +83,6 @@ __global__ void k_zero_u8(uint8_t* __restrict__ v, int64_t n) {
     v[i] = 0;
 }
 
-// Position of column col in row [b, e) of a sorted CSR row (-1 if absent).
-__device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ colidx, int64_t b, int64_t e, int64_t col) {
-  while (b < e) {
-    const int64_t mid = (b + e) >> 1;
-    const int64_t v = colidx[mid];
-    if (v == col) return mid;
-    if (v < col) b = mid + 1;
-    else e = mid;
-  }
-  return -1;
-}
-
 // One 8-thread group per sub-hex: thread g first evaluates the geometry at
 // Gauss point g (tau = eps / sqrt 3), then thread r forms row r of the block
 //   K_rc = sum_g kappa_s grad phi_r^T (adj(J) adj(J)^T / detJ) grad phi_c
@@ -192,7 +180,7 @@ __global__ void __launch_bounds__(kUThreads) k_assemble_unstructured(
         for (int c = 0; c < 8; ++c) {
           const int64_t C = dofs[s * 8 + c];
           if (ess && ess[C]) continue;
-          const int64_t pos = find_col(colidx, b, e, C);
+          const int64_t pos = lor_find_col(colidx, b, e, C);
           if (pos < 0) {
             bad |= 2;
             continue;
@@ -213,7 +201,7 @@ __global__ void k_unstructured_diag(int64_t n, const int64_t* __restrict__ rowpt
                                     const uint8_t* __restrict__ ess, VT* __restrict__ vals, int* __restrict__ status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (!ess[i]) continue;
-    const int64_t pos = find_col(colidx, rowptr[i], rowptr[i + 1], i);
+    const int64_t pos = lor_find_col(colidx, rowptr[i], rowptr[i + 1], i);
     if (pos < 0) atomicOr(status, LOR_FLAG_BAD_PATTERN);
     else vals[pos] = (VT)1;
   }

@@ -196,6 +196,9 @@ void free_all(lor_ctx* c) {
   cudaFree(c->pcg_work);
   cudaFree(c->red);
   cudaFree(c->red_count);
+  cudaFree(c->ecorners);
+  cudaFree(c->edofs);
+  cudaFree(c->ess);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
 }
 
@@ -282,6 +285,82 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
   return LOR_OK;
 }
 
+int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const double* d_corners,
+                       const int64_t* d_elem_dofs, const uint8_t* d_ess, void* stream) {
+  if (!out) return set_err(nullptr, LOR_EINVAL, "lor_create_general: out is NULL");
+  *out = nullptr;
+  if (!d_corners || !d_elem_dofs) return set_err(nullptr, LOR_EINVAL, "lor_create_general: corners or map is NULL");
+  if (p < 1 || p > LOR_MAX_P)
+    return set_err(nullptr, LOR_EINVAL, "lor_create_general: p must be in [1, " + std::to_string(LOR_MAX_P) + "]");
+  if (nel < 1 || ndof < 1) return set_err(nullptr, LOR_EINVAL, "lor_create_general: empty mesh");
+  if (ndof >= (int64_t(1) << 31))
+    return set_err(nullptr, LOR_EINVAL, "lor_create_general: more than 2^31-1 DOFs (int32 column indices)");
+  lor_ctx* c = new (std::nothrow) lor_ctx();
+  if (!c) return set_err(nullptr, LOR_ENOMEM, "lor_create_general: host allocation failed");
+  c->cfg.p = p;
+  c->cfg.nex = c->cfg.ney = c->cfg.nez = 0;
+  c->general = true;
+  cudaGetDevice(&c->device);
+  build_tables(p, &c->T);
+  LorMesh& m = c->m;
+  // the structured extents are unused on a general mesh; 1 keeps any index
+  // arithmetic that is evaluated but not used free of divisions by zero
+  m.nex = m.ney = m.nez = 1;
+  m.p = p;
+  m.nx = m.ny = m.nz = 1;
+  m.ndof = ndof;
+  m.nel = nel;
+  m.verts = nullptr;
+  const int64_t n3 = (int64_t)(p + 1) * (p + 1) * (p + 1);
+  int rc = LOR_OK;
+  if (!rc) rc = alloc(c, &c->ecorners, 24 * nel, "element corners");
+  if (!rc) rc = alloc(c, &c->edofs, n3 * nel, "element-to-DOF map");
+  if (!rc) rc = alloc(c, &c->ess, ndof, "essential mask");
+  if (!rc) rc = alloc(c, &c->d_status, 4, "status");
+  if (!rc) rc = alloc(c, &c->red, LOR_RED_BLOCKS + 16 + 2 * LOR_PCG_MAX_BLOCKS, "reduction");
+  if (!rc) rc = alloc(c, &c->red_count, 8, "reduction counters");
+  if (!rc) rc = alloc(c, &c->pcg_work, 4 * ndof, "pcg work");
+  if (!rc && cudaMallocHost((void**)&c->h_scalar, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->h_scalar = nullptr;
+    rc = set_err(c, LOR_ENOMEM, "pinned host allocation failed");
+  }
+  cudaError_t e = cudaSuccess;
+  if (!rc) {
+    m.ecorners = c->ecorners;
+    m.edofs = c->edofs;
+    m.ess = c->ess;
+    e = cudaMemcpyAsync(c->ecorners, d_corners, sizeof(double) * 24 * nel, cudaMemcpyDeviceToDevice, S(stream));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->edofs, d_elem_dofs, sizeof(int64_t) * n3 * nel, cudaMemcpyDeviceToDevice, S(stream));
+    if (e == cudaSuccess)
+      e = d_ess ? cudaMemcpyAsync(c->ess, d_ess, ndof, cudaMemcpyDeviceToDevice, S(stream))
+                : cudaMemsetAsync(c->ess, 0, ndof, S(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), S(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->red_count, 0, 8 * sizeof(unsigned), S(stream));
+    if (e == cudaSuccess) e = lor_launch_geometry_check(m, c->T, c->d_status, S(stream));
+    if (e == cudaSuccess) e = lor_general_pattern(m, &c->rowptr, &c->colidx, &m.nnz, c->d_status, S(stream));
+    if (e != cudaSuccess) rc = cuda_err(c, e, "lor_create_general");
+  }
+  int flags = 0;
+  if (!rc) rc = read_status(c, S(stream), &flags);
+  if (!rc && (flags & LOR_FLAG_BAD_MAP))
+    rc = set_err(c, LOR_EINVAL, "lor_create_general: element-to-DOF map entry out of [0, ndof) or vertex valence > 64");
+  if (!rc && (flags & LOR_FLAG_BAD_GEOM))
+    rc = set_err(c, LOR_EGEOM, "lor_create_general: a Jacobian determinant is <= 0");
+  if (rc) {
+    g_create_error = c->err;
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  m.rowptr = c->rowptr;
+  m.colidx = c->colidx;
+  c->have_pattern = true;
+  *out = c;
+  return LOR_OK;
+}
+
 int lor_launch_count(int64_t* count) {
   if (!count) return LOR_EINVAL;
   *count = g_launches.load(std::memory_order_relaxed);
@@ -337,6 +416,7 @@ int lor_set_reaction(lor_ctx* c, const double* d_beta, void* stream) {
 int lor_lor_mesh(lor_ctx* c, double* d_corners, int64_t* d_dofs, double* d_kappa_sub, double* d_beta_sub,
                  uint8_t* d_ess, void* stream) {
   if (!c) return LOR_EINVAL;
+  if (c->general) return set_err(c, LOR_ESTATE, "lor_lor_mesh: structured (lor_create) meshes only");
   if (!d_corners || !d_dofs || !d_kappa_sub) return set_err(c, LOR_EINVAL, "lor_lor_mesh: NULL output array");
   if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_lor_mesh: call lor_set_coefficient first");
   if (d_beta_sub && !c->have_beta) return set_err(c, LOR_ESTATE, "lor_lor_mesh: beta_sub asked without lor_set_reaction");
@@ -362,6 +442,7 @@ int lor_assemble_unstructured(lor_ctx* c, int64_t nsub, const double* d_corners,
 int lor_discrete_gradient(lor_ctx* c, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
                           void* stream) {
   if (!c) return LOR_EINVAL;
+  if (c->general) return set_err(c, LOR_ESTATE, "lor_discrete_gradient: structured (lor_create) meshes only");
   if (nedge) *nedge = lor_edge_count(c->m);
   if (!d_rowptr && !d_colidx && !d_values) return LOR_OK;
   if (!d_rowptr || !d_colidx || !d_values)
@@ -375,6 +456,7 @@ int lor_discrete_gradient(lor_ctx* c, int64_t* d_rowptr, int32_t* d_colidx, doub
 
 int lor_vertex_coordinates(lor_ctx* c, double* d_xyz, void* stream) {
   if (!c) return LOR_EINVAL;
+  if (c->general) return set_err(c, LOR_ESTATE, "lor_vertex_coordinates: structured (lor_create) meshes only");
   if (!d_xyz) return set_err(c, LOR_EINVAL, "lor_vertex_coordinates: xyz is NULL");
   cudaError_t e = lor_launch_vertex_coordinates(c->m, c->T, d_xyz, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_vertex_coordinates");

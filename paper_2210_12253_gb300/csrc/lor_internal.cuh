@@ -38,6 +38,15 @@ struct LorMesh {
   int64_t nx, ny, nz;   // DOFs per axis
   int64_t ndof, nel, nnz;
   const double* verts;  // device [(nex+1)(ney+1)(nez+1)][3]
+  // General conforming hex mesh (the element-restriction form; NULL on the
+  // structured unit-cube grid): element corners [nel][8][3] (corner
+  // c0 + 2 c1 + 4 c2), element-to-DOF map [nel][(p+1)^3] (node i + n(j + n k)),
+  // essential-DOF mask [ndof], and the LOR CSR pattern built from the map.
+  const double* ecorners = nullptr;
+  const int64_t* edofs = nullptr;
+  const uint8_t* ess = nullptr;
+  const int64_t* rowptr = nullptr;
+  const int32_t* colidx = nullptr;
 };
 
 struct lor_ctx {
@@ -59,6 +68,10 @@ struct lor_ctx {
   int* d_status = nullptr;     // device error flags
   bool have_coeff = false, have_pattern = false, have_vals64 = false, have_vals32 = false;
   bool have_beta = false;      // the reaction term is on (lor_set_reaction)
+  bool general = false;        // created by lor_create_general (element-restriction mesh)
+  double* ecorners = nullptr;  // general: [nel][8][3]
+  int64_t* edofs = nullptr;    // general: [nel][(p+1)^3]
+  uint8_t* ess = nullptr;      // general: [ndof]
   // preconditioner
   int pc_kind = LOR_PRECOND_NONE, pc_dtype = LOR_F64, pc_degree = 1;
   double pc_lo = 0, pc_hi = 0, pc_lmax = 0;
@@ -80,6 +93,7 @@ void lor_count_launch();
 #define LOR_FLAG_BAD_GEOM 2
 #define LOR_FLAG_TIMEOUT 4  // a bounded wait on an mbarrier expired (a TMA copy never completed)
 #define LOR_FLAG_BAD_PATTERN 8  // the unstructured assembly met a coupling missing from the given CSR pattern
+#define LOR_FLAG_BAD_MAP 16  // a general mesh's element-to-DOF map is out of range (or a vertex valence above 64)
 
 // Elements of padding after the nnz CSR values of the context's value arrays
 // (a tile's bulk copy may end up to 15 bytes past the last value).
@@ -121,11 +135,39 @@ __host__ __device__ __forceinline__ bool lor_is_essential(int64_t I, int64_t J, 
   return I == 0 || J == 0 || K == 0 || I == nx - 1 || J == ny - 1 || K == nz - 1;
 }
 
+// Essential (Dirichlet) DOF: the mask of a general mesh, else the boundary of
+// the structured grid.
+__host__ __device__ __forceinline__ bool lor_dof_essential(const LorMesh& m, int64_t r) {
+  if (m.ess) return m.ess[r] != 0;
+  const int64_t I = r % m.nx, J = (r / m.nx) % m.ny, K = r / (m.nx * m.ny);
+  return lor_is_essential(I, J, K, m.nx, m.ny, m.nz);
+}
+
+// Position of column col in the sorted CSR row segment [b, e) (-1 if absent).
+__device__ __forceinline__ int64_t lor_find_col(const int32_t* __restrict__ colidx, int64_t b, int64_t e,
+                                                int64_t col) {
+  while (b < e) {
+    const int64_t mid = (b + e) >> 1;
+    const int64_t v = colidx[mid];
+    if (v == col) return mid;
+    if (v < col) b = mid + 1;
+    else e = mid;
+  }
+  return -1;
+}
+
 // -------------------------------------------------------------------------
 // Device helpers shared by the geometry and assembly kernels.
 // -------------------------------------------------------------------------
 // Corner c = c0 + 2 c1 + 4 c2 of element e.
 __device__ __forceinline__ void lor_element_corner(const LorMesh& m, int64_t e, int c, double X[3]) {
+  if (m.ecorners) {
+    const double* v = m.ecorners + (e * 8 + c) * 3;
+    X[0] = v[0];
+    X[1] = v[1];
+    X[2] = v[2];
+    return;
+  }
   const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
   const int64_t a = ex + (c & 1), b = ey + ((c >> 1) & 1), cc = ez + ((c >> 2) & 1);
   const double* v = m.verts + 3 * (a + (int64_t)(m.nex + 1) * (b + (int64_t)(m.ney + 1) * cc));
@@ -224,6 +266,10 @@ cudaError_t lor_launch_assemble_unstructured(int64_t nsub, const double* corners
                                              const double* ksub, const double* bsub, int64_t n, int64_t nnz,
                                              const int64_t* rowptr, const int32_t* colidx, const uint8_t* ess,
                                              void* vals, int dtype, int* status, cudaStream_t s);
+// general meshes (k_general.cu): LOR pattern from the element-to-DOF map
+// (allocates *rowptr and *colidx, sets *nnz; synchronises), map validation
+cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr, int32_t** colidx, int64_t* nnz, int* d_status,
+                                cudaStream_t s);
 // H(curl) topology of the LOR mesh (k_hcurl.cu)
 int64_t lor_edge_count(const LorMesh& m);
 cudaError_t lor_launch_discrete_gradient(const LorMesh& m, int64_t* rowptr, int32_t* colidx, double* values,

@@ -22,7 +22,7 @@ EXPORTED = [
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
     "lor_precond_apply_noalloc", "lor_set_reaction", "lor_lor_mesh", "lor_assemble_unstructured",
-    "lor_discrete_gradient", "lor_vertex_coordinates",
+    "lor_discrete_gradient", "lor_vertex_coordinates", "lor_create_general",
 ]
 
 
@@ -53,6 +53,8 @@ def load_library(path=LIB):
     L.lor_last_error.argtypes = [vp]
     L.lor_create.restype = i
     L.lor_create.argtypes = [C.POINTER(vp), C.POINTER(lor_config), vp, vp]
+    L.lor_create_general.restype = i
+    L.lor_create_general.argtypes = [C.POINTER(vp), i, i64, i64, vp, vp, vp, vp]
     L.lor_destroy.restype = i
     L.lor_destroy.argtypes = [vp]
     L.lor_sizes.restype = i
@@ -150,11 +152,40 @@ class LOR:
         if rc != LOR_OK:
             raise LORError(rc, self._lib.lor_last_error(None).decode())
         self._h = h
+        self._sizes()
+
+    def _sizes(self):
         n, z, e, q = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         self._call("lor_sizes", C.byref(n), C.byref(z), C.byref(e), C.byref(q), stream=False)
         self.ndof, self.nnz, self.nel, self.nqpt = n.value, z.value, e.value, q.value
         self.q = self.p + 2
         self._kappa_key = None
+
+    @classmethod
+    def general(cls, p, corners, elem_dofs, ndof, ess=None):
+        """A context on a general conforming hex mesh in element-restriction
+        form: corners [nel, 8, 3] f64, elem_dofs [nel, (p+1)^3] int64 (local
+        node i + n(j + n k) -> global DOF), ess uint8[ndof] or None."""
+        self = cls.__new__(cls)
+        self._lib = load_library()
+        self._h = None
+        self.p = int(p)
+        nel = int(corners.numel() // 24)
+        self.nex = self.ney = self.nez = None
+        _dev(corners, torch.float64, 24 * nel, "corners")
+        _dev(elem_dofs, torch.int64, nel * (self.p + 1) ** 3, "elem_dofs")
+        if ess is not None:
+            _dev(ess, torch.uint8, int(ndof), "ess")
+        self.device = corners.device
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.lor_create_general(C.byref(h), self.p, nel, int(ndof), _ptr(corners), _ptr(elem_dofs),
+                                              _ptr(ess), _stream())
+        if rc != LOR_OK:
+            raise LORError(rc, self._lib.lor_last_error(None).decode())
+        self._h = h
+        self._sizes()
+        return self
 
     # ------------------------------------------------------------------ plumbing
     def _call(self, name, *args, stream=True):
