@@ -14,7 +14,8 @@ the 24^3-element, p = 5 workload under "gradient"; the same step with the
 reaction term of the definite Helmholtz problem under "helmholtz"; the
 macro-element vs unstructured LOR assembly at ~4M DOFs per degree under
 "assembly_comparator"; the discrete gradient and vertex coordinates of the
-32^3 p = 6 LOR mesh under "hcurl_topology".
+32^3 p = 6 LOR mesh under "hcurl_topology"; the step's kernels on the same
+workload handed over as a general mesh under "general_mesh".
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
@@ -305,6 +306,9 @@ def run_gpu(args, rank, world, local_rank):
     hcurl = None
     if not args.no_hcurl:
         hcurl = run_hcurl(args, dev)
+    general = None
+    if not args.no_general:
+        general = run_general(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -321,7 +325,8 @@ def run_gpu(args, rank, world, local_rank):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps},
            "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad,
-           "helmholtz": helm, "assembly_comparator": comparator, "hcurl_topology": hcurl}
+           "helmholtz": helm, "assembly_comparator": comparator, "hcurl_topology": hcurl,
+           "general_mesh": general}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     op.close()
@@ -611,6 +616,76 @@ def run_hcurl(args, dev):
             "hbm_peak_gbs": peak, "peak_source": src}
 
 
+def run_general(args, dev):
+    """The 16^3 p=4 step workload handed over as a general mesh (corners,
+    element-to-DOF map, essential mask; natural numbering, no rotation):
+    pattern build (count/scan/fill/sort on the GPU), setup, FP64 assembly
+    (CSR positions by search), apply, backward and the FP64 Chebyshev step
+    on the explicit pattern, each next to the structured path's time.  Median
+    of 5 event-timed launches after one warm-up, L2 flushed before each."""
+    import numpy as np
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import boundary_mask, power_start_vector, workload
+
+    prob = workload(STEP_WORKLOAD)
+    p, n = prob.p, prob.p + 1
+    nex, ney, nez = prob.nex, prob.ney, prob.nez
+    V = prob.vertices.reshape(nez + 1, ney + 1, nex + 1, 3)
+    ez, ey, ex = np.meshgrid(np.arange(nez), np.arange(ney), np.arange(nex), indexing="ij")
+    corners = np.stack([V[ez + (c >> 2), ey + ((c >> 1) & 1), ex + (c & 1)] for c in range(8)], axis=3)
+    corners = corners.reshape(-1, 8, 3)
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    nx, ny = nex * p + 1, ney * p + 1
+    edofs = ((ex.reshape(-1, 1) * p + i.reshape(1, -1)) +
+             nx * ((ey.reshape(-1, 1) * p + j.reshape(1, -1)) + ny * (ez.reshape(-1, 1) * p + k.reshape(1, -1))))
+    ess = boundary_mask(nex, ney, nez, p).astype(np.uint8)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=5):
+        fn()
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    t_c, t_d, t_e = (torch.tensor(a, device=dev) for a in (corners, edofs, ess))
+    t0 = time.perf_counter()
+    g = LOR.general(p, t_c, t_d, int(ess.size), t_e)
+    create_s = time.perf_counter() - t0
+    s = LOR(p, nex, ney, nez, torch.tensor(prob.vertices, device=dev))
+    kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
+    x = torch.tensor(np.random.default_rng(5).standard_normal(g.ndof), device=dev)
+    r = torch.tensor(prob.rhs, device=dev)
+    out = {"workload": STEP_WORKLOAD + " as a general mesh (natural numbering)", "create_s": create_s,
+           "nnz": g.nnz}
+    for name, op in (("general", g), ("structured", s)):
+        y, z, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
+        op.set_coefficient(kappa, check=True)
+        op.build_pattern_internal()
+        op.assemble_internal(torch.float64)
+        lam = op.precond_setup("cheb", torch.float64, degree=3, power_iters=20,
+                               v0=torch.tensor(power_start_vector(op.ndof), device=dev))
+        out[name] = {
+            "setup_ms": timed(lambda: op.set_coefficient(kappa)),
+            "assemble_ms": timed(lambda: op.assemble_internal(torch.float64)),
+            "apply_ms": timed(lambda: op.apply(x, out=y)),
+            "backward_ms": timed(lambda: op.apply_backward(x, x, gx_out=gx, gk_out=gk)),
+            "precond_ms": timed(lambda: op.precond_apply(r, out=z)),
+            "lambda_max": lam}
+    g.close()
+    s.close()
+    return out
+
+
 def run_sweep(args, dev):
     """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
     JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
@@ -768,6 +843,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the 24^3 p=5 adjoint-gradient timing")
     ap.add_argument("--no-hcurl", action="store_true", help="skip the discrete-gradient / vertex-coordinate timing")
+    ap.add_argument("--no-general", action="store_true", help="skip the general-mesh (element-restriction) timing")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip the macro-element vs unstructured LOR assembly comparison")
     ap.add_argument("--no-helmholtz", action="store_true",
