@@ -13,8 +13,14 @@
  * high-order operator A_p = P^T G^T B^T D B G P matrix-free (Eq. (4),
  * Step S2.1) and the LOR-based preconditioner B_h (Step S2.2).  This library
  * implements that pipeline on one GPU for structured meshes of the unit cube
- * (nex x ney x nez trilinear hexes with arbitrary interior vertex positions),
- * with B_h a Chebyshev-Jacobi smoother on the assembled LOR matrix.
+ * (nex x ney x nez trilinear hexes with arbitrary interior vertex positions,
+ * lor_create) and for general conforming hex meshes given by element corners
+ * and an element-to-DOF map (lor_create_general), with B_h a Chebyshev-Jacobi
+ * smoother on the assembled LOR matrix.  Optional parts: the reaction term
+ * of the definite Helmholtz problem of Section 4.1 (lor_set_reaction), the
+ * gradients of the operator with respect to x and kappa, the unstructured
+ * LOR assembly the paper compares against (lor_assemble_unstructured), and
+ * the discrete gradient of the LOR mesh (Algorithm 1).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
