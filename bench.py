@@ -703,8 +703,10 @@ def run_sweep(args, dev):
     hbm_peak, _ = hbm_peak_gbs()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     out = []
-    for p in args.sweep_p:
-        prob = workload("c5_p%d" % p)
+    names = args.sweep_workloads or ["c5_p%d" % p for p in args.sweep_p]
+    for name in names:
+        prob = workload(name)
+        p = prob.p
         op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
         kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
         prob.kappa = None
@@ -855,6 +857,8 @@ def main(argv=None):
     ap.add_argument("--sweep", action="store_true", help="per-kernel throughput versus p at ~20M DOFs")
     ap.add_argument("--sweep-p", type=int, nargs="*", default=list(range(2, 11)))
     ap.add_argument("--sweep-reps", type=int, default=5)
+    ap.add_argument("--sweep-workloads", nargs="*", default=None,
+                    help="run the sweep's kernel set on these named workloads instead (e.g. c4_24x24x24_p5)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
