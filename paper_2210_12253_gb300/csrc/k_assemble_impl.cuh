@@ -66,10 +66,15 @@ __device__ __forceinline__ constexpr double inv_sqrt3_pow(int p) {  // 3^(-p/2),
 }
 __device__ __forceinline__ constexpr int sym(int i, int j) { return i <= j ? i * 8 + j : j * 8 + i; }
 
-template <typename VT>
-__device__ __forceinline__ void walsh8(VT* v) {  // v(w) = sum_g v(g) prod_k eps_k^{w_k}
+// v(w) = sum_g v(g) prod_k eps_k^{w_k}; the three butterfly stages commute,
+// stage FIRST runs first.  For a diagonal metric entry G^{aa} only the
+// outputs with bit a clear are used later, so with FIRST = a the whole
+// bit-a-set half is dead after the first stage and the compiler drops it.
+template <typename VT, int FIRST>
+__device__ __forceinline__ void walsh8(VT* v) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+  for (int s = 0; s < 3; ++s) {
+    const int k = s == 0 ? FIRST : (s == 1 ? (FIRST == 0 ? 1 : 0) : (FIRST == 2 ? 1 : 2));
 #pragma unroll
     for (int g = 0; g < 8; ++g)
       if (!((g >> k) & 1)) {
@@ -77,23 +82,41 @@ __device__ __forceinline__ void walsh8(VT* v) {  // v(w) = sum_g v(g) prod_k eps
         v[g] = lo + hi;
         v[g | (1 << k)] = hi - lo;
       }
+  }
 }
 
 // K <- (H_k (x) H_k) K for axis k, on a symmetric 8x8 matrix stored at
 // K[sym(i,j)]; H_k maps (m_k = 0, m_k = 1) to (i_k = 0: a - b, i_k = 1: a + b).
+// Work per 2x2 block of the axis (rows i0, i1 = i0 | bit, columns j0, j1):
+// off-diagonal blocks 8 additions for 4 outputs; a diagonal block (i0 = j0,
+// symmetric input a, b, b, d) needs only a - 2b + d, a - d and a + 2b + d.
 template <typename VT, int k>
 __device__ __forceinline__ void hadamard_axis(VT* K) {
+  constexpr int bit = 1 << k;
   VT out[64];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i0 = 0; i0 < 8; ++i0) {
+    if (i0 & bit) continue;
 #pragma unroll
-    for (int j = i; j < 8; ++j) {
-      const int i0 = i & ~(1 << k), i1 = i | (1 << k), j0 = j & ~(1 << k), j1 = j | (1 << k);
-      const VT a = K[sym(i0, j0)], b = K[sym(i0, j1)], c = K[sym(i1, j0)], d = K[sym(i1, j1)];
-      const VT u = ((i >> k) & 1) ? a + c : a - c;
-      const VT v = ((i >> k) & 1) ? b + d : b - d;
-      out[sym(i, j)] = ((j >> k) & 1) ? u + v : u - v;
+    for (int j0 = i0; j0 < 8; ++j0) {
+      if (j0 & bit) continue;
+      const int i1 = i0 | bit, j1 = j0 | bit;
+      if (i0 == j0) {
+        const VT a = K[sym(i0, i0)], b = K[sym(i0, i1)], d = K[sym(i1, i1)];
+        const VT t = a + d;
+        out[sym(i0, i0)] = t - (VT)2 * b;
+        out[sym(i1, i1)] = t + (VT)2 * b;
+        out[sym(i0, i1)] = a - d;
+      } else {
+        const VT a = K[sym(i0, j0)], b = K[sym(i0, j1)], c = K[sym(i1, j0)], d = K[sym(i1, j1)];
+        const VT u0 = a - c, u1 = a + c, v0 = b - d, v1 = b + d;
+        out[sym(i0, j0)] = u0 - v0;
+        out[sym(i0, j1)] = u0 + v0;
+        out[sym(i1, j0)] = u1 - v1;
+        out[sym(i1, j1)] = u1 + v1;
+      }
     }
+  }
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -237,9 +260,14 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
         }
       }
     }
-#pragma unroll
-    for (int ab = 0; ab < 6; ++ab) walsh8<VT>(G[ab]);
-    if constexpr (MASS) walsh8<VT>(W);
+    // pair order (00, 01, 02, 11, 12, 22): diagonal entries start with their own axis
+    walsh8<VT, 0>(G[0]);
+    walsh8<VT, 0>(G[1]);
+    walsh8<VT, 0>(G[2]);
+    walsh8<VT, 1>(G[3]);
+    walsh8<VT, 0>(G[4]);
+    walsh8<VT, 2>(G[5]);
+    if constexpr (MASS) walsh8<VT, 0>(W);
 
     // modal block (row/column 0 vanish: psi_0 has no gradient)
     VT K[64];

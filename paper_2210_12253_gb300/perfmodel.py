@@ -42,13 +42,16 @@ def setup_flops_per_point():
 
 
 def assemble_flops_per_subhex():
-    """One sub-hex block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form:
-    per Gauss point adjugate (27), det (5), 1/det (1), the six scaled metric
-    entries (42) = 75 x 8; six 8-point Walsh transforms (144); the 84-term
-    modal block (168); the modal-to-nodal transform on the 36 symmetric
-    entries, 3 additions per entry and axis (324); kappa_s and scales (20).
-    (The direct nodal formula costs 3,936 flops per sub-hex.)"""
-    return 8 * 75 + 144 + 168 + 324 + 20
+    """One sub-hex block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form, as
+    the kernel evaluates it: per Gauss point adjugate (27), det (5), 1/det
+    (1), the six scaled metric entries (42) = 75 x 8; six 8-point Walsh
+    transforms, 24 additions each less the 12 whose outputs the diagonal
+    entries never use (108); the 84-term modal block (168); the
+    modal-to-nodal transform per axis, 8 additions for each of the 6
+    off-diagonal 2x2 blocks and 6 flops for each of the 4 diagonal ones
+    (3 x 72 = 216); kappa_s and scales (20).  (The direct nodal formula costs
+    3,936 flops per sub-hex.)"""
+    return 8 * 75 + 108 + 168 + 216 + 20
 
 
 def apply_flops_per_element(p):
