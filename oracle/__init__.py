@@ -14,6 +14,7 @@ tests check only that it stays bounded as p grows: "parity unpinned" beyond
 that property).
 """
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -23,9 +24,11 @@ _lib = None
 
 
 def lib():
+    """The oracle library; LOR_ORACLE_LIB names another build of the same
+    source (the mutation tests load deliberately broken copies this way)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build_oracle())
+        _lib = C.CDLL(os.environ.get("LOR_ORACLE_LIB") or build_oracle())
         _declare(_lib)
     return _lib
 

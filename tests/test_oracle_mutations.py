@@ -1,0 +1,65 @@
+"""Mutation tests of the oracle's pins: each case plants one plausible
+mistake in a copy of oracle/lor_oracle.c (a dropped term, a wrong weight,
+sign or index, a swapped operand), builds it, and runs the CPU pin suite
+against that build; at least one pin must fail.  The planted copies live in
+a temporary directory and are loaded through LOR_ORACLE_LIB; the oracle
+itself is untouched."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "lor_oracle.c")
+PINS = ["tests/test_oracle_basis.py", "tests/test_oracle_ho.py", "tests/test_oracle_lor.py",
+        "tests/test_oracle_solver.py", "tests/test_oracle_helmholtz.py", "tests/test_oracle_hcurl.py"]
+
+# (name, original text, planted text)
+MUTATIONS = [
+    ("x-derivative uses the interpolation matrix",
+     "sd += D[g0 * n + i] * u[(k * n + j) * n + i];", "sd += B[g0 * n + i] * u[(k * n + j) * n + i];"),
+    ("z-stage derivative uses the interpolation matrix",
+     "s2 += D[g2 * n + k] * BBu[(k * q + g1) * q + g0];", "s2 += B[g2 * n + k] * BBu[(k * q + g1) * q + g0];"),
+    ("quadrature weight dropped from the metric factor",
+     "M[a][b] = w * det * s;", "M[a][b] = det * s;"),
+    ("transposed inverse Jacobian",
+     "Ai[1][0] = c01 / det;", "Ai[1][0] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;"),
+    ("Dirichlet rows of the apply set to zero",
+     "y[I + nx * (J + ny * K)] = x[I + nx * (J + ny * K)];", "y[I + nx * (J + ny * K)] = 0.0;"),
+    ("kappa_s as an unweighted average",
+     "den[s] += w;", "den[s] += 1.0;"),
+    ("sub-hex Gauss points at +-1/3",
+     "const double g1 = 1.0 / sqrt(3.0);", "const double g1 = 1.0 / 3.0;"),
+    ("reaction term without detJ",
+     "* wg[g0] * wg[g1] * wg[g2] * detJ[e * nq3 + g];", "* wg[g0] * wg[g1] * wg[g2];"),
+    ("LOR mass block uses phi_r twice",
+     "wb * phi[r] * phi[s];", "wb * phi[r] * phi[r];"),
+    ("Chebyshev step coefficient halved",
+     "(2.0 * rho_new / delta) * res[i] / dg[i];", "(rho_new / delta) * res[i] / dg[i];"),
+    ("PCG beta inverted",
+     "double beta = rz_new / rz;", "double beta = rz / rz_new;"),
+    ("Gauss-Lobatto Newton stopped after one step",
+     "for (int it = 0; it < 100; ++it) {\n      double P, Pm1;\n      legendre_pair(p, t, &P, &Pm1);\n      double d1",
+     "for (int it = 0; it < 1; ++it) {\n      double P, Pm1;\n      legendre_pair(p, t, &P, &Pm1);\n      double d1"),
+    ("discrete gradient orientation lost",
+     "values[2 * e] = -1.0;", "values[2 * e] = 1.0;"),
+    ("power iteration without the diagonal scaling",
+     "for (int64_t i = 0; i < n; ++i) w[i] /= d[i];", ""),
+]
+
+
+@pytest.mark.parametrize("name,orig,planted", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, orig, planted, tmp_path):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, "mutation site not found (oracle source changed?): " + name
+    bad = tmp_path / "lor_oracle_mutant.c"
+    bad.write_text(src.replace(orig, planted))
+    lib = tmp_path / "liblor_oracle_mutant.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(lib), str(bad),
+                    "-lm"], check=True)
+    env = dict(os.environ, LOR_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"] + PINS,
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "no pin caught: " + name + "\n" + r.stdout[-2000:]
