@@ -8,7 +8,7 @@
   the full apply, and PCG to 1e-8 in FP64 and mixed precision whose true
   residual is re-checked with the oracle's operator.
 * 24^3 elements, p = 5 (1,771,561 DOFs; the gradient workload): dJ/dtheta by
-  the adjoint against fourth-order central differences on 8 random
+  the adjoint against fourth-order central differences on 16 random
   directions, and the
   gradient kernel against the oracle's on the same fields.
 """
@@ -144,7 +144,7 @@ def test_gradient_workload_24x24x24_p5():
     gref = -np.exp(prob.theta).ravel() * gk_ref.ravel()
     assert np.abs(g - gref).max() <= 1e-8 * np.abs(gref).max()
     # fourth-order central differences (steps h and 2h, Richardson-combined)
-    # on 8 random directions.  h = 1e-3 |theta| keeps the difference quotient
+    # on 16 random directions.  h = 1e-3 |theta| keeps the difference quotient
     # far above the solver's forward error (relative residual 1e-12 times the
     # condition number) while the O(h^4) truncation error stays below 1e-7.
     # The error is measured against |g|, the typical size of g.v for
@@ -156,7 +156,7 @@ def test_gradient_workload_24x24x24_p5():
     def J_at(d):
         return 0.5 * float(((solve(op, torch.exp(th + t(d)), b, **opts) - ustar) ** 2).sum())
 
-    for _ in range(8):
+    for _ in range(16):
         v = rng.standard_normal(th.numel())
         h = 1e-3 * np.linalg.norm(prob.theta) / np.linalg.norm(v)
         d1 = J_at(h * v) - J_at(-h * v)
