@@ -112,8 +112,9 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
  * mesh.  The LOR pattern is built here from the map (the sub-hexes' 8-DOF
  * couplings, sorted and de-duplicated per row; vertex valence up to 64) and
  * the LOR assembly finds CSR positions by binary search; lor_spmv and the
- * smoother read the explicit pattern.  lor_lor_mesh, lor_discrete_gradient
- * and lor_vertex_coordinates are for structured meshes only (LOR_ESTATE).
+ * smoother read the explicit pattern.  lor_lor_mesh is for structured meshes
+ * only (LOR_ESTATE); lor_discrete_gradient numbers the LOR edges of a general
+ * mesh itself (see there).
  * LOR_EINVAL for a map entry out of range, LOR_EGEOM for detJ <= 0.  All
  * input arrays are device memory, copied.  Synchronises the stream. */
 int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const double* d_corners,
@@ -219,13 +220,16 @@ int lor_assemble_unstructured(lor_ctx* ctx, int64_t nsub, const double* d_corner
  * number of edges; with all three arrays NULL only the count is returned.
  * d_rowptr int64[nedge+1], d_colidx int32[2 nedge] (8-byte aligned),
  * d_values f64[2 nedge] (16-byte aligned).  The matrix depends on the
- * topology and p only. */
+ * topology and p only.  On a general mesh (lor_create_general) the edges are
+ * the sub-hex edges through the element-to-DOF map, each oriented from its
+ * lower to its higher global DOF and numbered by (tail, head) ascending; the
+ * first call enumerates them (synchronises) and keeps them in the context. */
 int lor_discrete_gradient(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
                           void* stream);
 
 /* Coordinates of the LOR vertices without duplicates (the vector AMS takes
- * besides the discrete gradient): d_xyz f64[N][3], vertex I + nx(J + ny K) at
- * T_e(GLL point) of the lowest-index element containing it. */
+ * besides the discrete gradient): d_xyz f64[N][3], DOF d (structured: vertex
+ * I + nx(J + ny K)) at T_e(GLL node) of the lowest-index element holding it. */
 int lor_vertex_coordinates(lor_ctx* ctx, double* d_xyz, void* stream);
 
 /* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum

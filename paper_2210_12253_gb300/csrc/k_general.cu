@@ -188,6 +188,97 @@ __global__ void k_row_write(int64_t n, const int64_t* __restrict__ off, const in
   }
 }
 
+// ---------------------------------------------------------------- edges (discrete gradient)
+// The 12 edges of the unit cube as pairs of local vertices r = r0 + 2 r1 + 4 r2.
+__constant__ int kEdgeA[12] = {0, 2, 4, 6, 0, 1, 4, 5, 0, 1, 2, 3};
+__constant__ int kEdgeB[12] = {1, 3, 5, 7, 2, 3, 6, 7, 4, 5, 6, 7};
+
+__device__ __forceinline__ void subhex_edge(const LorMesh& m, int64_t w, int64_t& tail, int64_t& head) {
+  const int64_t P3 = (int64_t)m.p * m.p * m.p;
+  const int64_t e = w / (P3 * 12);
+  const int s = (int)((w / 12) % P3), k = (int)(w % 12);
+  const int64_t a = subhex_dof(m, e, s, kEdgeA[k]), b = subhex_dof(m, e, s, kEdgeB[k]);
+  tail = a < b ? a : b;
+  head = a < b ? b : a;
+}
+
+__global__ void k_edge_count(LorMesh m, int64_t* __restrict__ cnt) {
+  GRID_STRIDE(w, m.nel * (int64_t)m.p * m.p * m.p * 12) {
+    int64_t t, h;
+    subhex_edge(m, w, t, h);
+    atomicAdd((unsigned long long*)(cnt + t), 1ull);
+  }
+}
+
+__global__ void k_edge_fill(LorMesh m, const int64_t* __restrict__ off, int64_t* __restrict__ cur,
+                            int32_t* __restrict__ list) {
+  GRID_STRIDE(w, m.nel * (int64_t)m.p * m.p * m.p * 12) {
+    int64_t t, h;
+    subhex_edge(m, w, t, h);
+    list[off[t] + (int64_t)atomicAdd((unsigned long long*)(cur + t), 1ull)] = (int32_t)h;
+  }
+}
+
+__global__ void k_edge_write(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ list,
+                             const int64_t* __restrict__ estart, int32_t* __restrict__ tail, int32_t* __restrict__ head) {
+  GRID_STRIDE(i, n) {
+    int64_t o = estart[i];
+    if (estart[i + 1] == o) continue;
+    for (int64_t j = off[i]; j < off[i + 1]; ++j)
+      if (j == off[i] || list[j] != list[j - 1]) {
+        tail[o] = (int32_t)i;
+        head[o] = list[j];
+        ++o;
+      }
+  }
+}
+
+__global__ void k_edges_to_csr(int64_t nedge, const int32_t* __restrict__ tail, const int32_t* __restrict__ head,
+                               int64_t* __restrict__ rowptr, int32_t* __restrict__ colidx,
+                               double* __restrict__ values) {
+  GRID_STRIDE(i, nedge + 1) {
+    rowptr[i] = 2 * i;
+    if (i == nedge) break;
+    reinterpret_cast<int2*>(colidx)[i] = make_int2(tail[i], head[i]);
+    reinterpret_cast<double2*>(values)[i] = make_double2(-1.0, 1.0);
+  }
+}
+
+// ---------------------------------------------------------------- vertex coordinates
+__global__ void k_owner_min(LorMesh m, unsigned long long* __restrict__ owner) {
+  const int64_t n3 = (int64_t)(m.p + 1) * (m.p + 1) * (m.p + 1);
+  GRID_STRIDE(w, m.nel * n3) atomicMin(owner + m.edofs[w], (unsigned long long)(w / n3));
+}
+
+// Each DOF written once, by the lowest-index element that holds it: x =
+// T_e(GLL node), the trilinear map through the element's corners.
+__global__ void k_general_vertices(LorMesh m, LorTables T, const unsigned long long* __restrict__ owner,
+                                   double* __restrict__ xyz) {
+  const int n = m.p + 1;
+  const int64_t n3 = (int64_t)n * n * n;
+  GRID_STRIDE(w, m.nel * n3) {
+    const int64_t e = w / n3, d = m.edofs[w];
+    if (owner[d] != (unsigned long long)e) continue;
+    const int loc = (int)(w % n3), i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const double l0[2] = {0.5 * (1.0 - T.gll[i]), 0.5 * (1.0 + T.gll[i])};
+    const double l1[2] = {0.5 * (1.0 - T.gll[j]), 0.5 * (1.0 + T.gll[j])};
+    const double l2[2] = {0.5 * (1.0 - T.gll[k]), 0.5 * (1.0 + T.gll[k])};
+    double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      double X[3];
+      lor_element_corner(m, e, c, X);
+      const double wc = l0[c & 1] * l1[(c >> 1) & 1] * l2[c >> 2];
+      x[0] += wc * X[0];
+      x[1] += wc * X[1];
+      x[2] += wc * X[2];
+    }
+    xyz[3 * d] = x[0];
+    xyz[3 * d + 1] = x[1];
+    xyz[3 * d + 2] = x[2];
+  }
+}
+
 }  // namespace
 
 cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out,
@@ -240,4 +331,77 @@ cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr_out, int32_t*
   *colidx_out = colidx;
   *nnz_out = nnz;
   return cudaSuccess;
+}
+
+cudaError_t lor_general_edges(const LorMesh& m, int32_t** tail_out, int32_t** head_out, int64_t* nedge_out,
+                              int* d_status, cudaStream_t s) {
+  const int64_t n = m.ndof;
+  const int64_t nb = (n + kChunk - 1) / kChunk + 1;
+  const int64_t nw = m.nel * (int64_t)m.p * m.p * m.p * 12;
+  int64_t *off = nullptr, *cur = nullptr, *scratch = nullptr, *estart = nullptr;
+  int32_t *list = nullptr, *tail = nullptr, *head = nullptr;
+  int64_t nedge = 0;
+  cudaError_t err = cudaMalloc(&off, sizeof(int64_t) * (n + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&cur, sizeof(int64_t) * (n + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&estart, sizeof(int64_t) * (n + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&scratch, sizeof(int64_t) * nb);
+  if (err == cudaSuccess) err = cudaMalloc(&list, sizeof(int32_t) * (nw > 0 ? nw : 1));
+  if (err == cudaSuccess) err = cudaMemsetAsync(off, 0, sizeof(int64_t) * (n + 1), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(cur, 0, sizeof(int64_t) * (n + 1), s);
+  if (err == cudaSuccess) {
+    k_edge_count<<<grid_for(nw), kT, 0, s>>>(m, off); lor_count_launch();
+    err = exclusive_scan(off, n, scratch, s);
+  }
+  if (err == cudaSuccess) {
+    k_edge_fill<<<grid_for(nw), kT, 0, s>>>(m, off, cur, list); lor_count_launch();
+    k_row_sort_count<<<grid_for(n), kT, 0, s>>>(n, off, list, cur, d_status); lor_count_launch();
+    err = cudaMemcpyAsync(estart, cur, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
+  }
+  if (err == cudaSuccess) err = exclusive_scan(estart, n, scratch, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&nedge, estart + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = cudaMalloc(&tail, sizeof(int32_t) * (nedge > 0 ? nedge : 1));
+  if (err == cudaSuccess) err = cudaMalloc(&head, sizeof(int32_t) * (nedge > 0 ? nedge : 1));
+  if (err == cudaSuccess) {
+    k_edge_write<<<grid_for(n), kT, 0, s>>>(n, off, list, estart, tail, head); lor_count_launch();
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(off);
+  cudaFree(cur);
+  cudaFree(estart);
+  cudaFree(scratch);
+  cudaFree(list);
+  if (err != cudaSuccess) {
+    cudaFree(tail);
+    cudaFree(head);
+    return err;
+  }
+  *tail_out = tail;
+  *head_out = head;
+  *nedge_out = nedge;
+  return cudaSuccess;
+}
+
+cudaError_t lor_launch_general_gradient(int64_t nedge, const int32_t* tail, const int32_t* head, int64_t* rowptr,
+                                        int32_t* colidx, double* values, cudaStream_t s) {
+  k_edges_to_csr<<<grid_for(nedge + 1), kT, 0, s>>>(nedge, tail, head, rowptr, colidx, values); lor_count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_general_vertices(const LorMesh& m, const LorTables& T, double* xyz, cudaStream_t s) {
+  unsigned long long* owner = nullptr;
+  const int64_t nw = m.nel * (int64_t)(m.p + 1) * (m.p + 1) * (m.p + 1);
+  cudaError_t err = cudaMallocAsync(&owner, sizeof(unsigned long long) * m.ndof, s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * m.ndof, s);
+  if (err == cudaSuccess) {
+    k_owner_min<<<grid_for(nw), kT, 0, s>>>(m, owner); lor_count_launch();
+    k_general_vertices<<<grid_for(nw), kT, 0, s>>>(m, T, owner, xyz); lor_count_launch();
+    err = cudaGetLastError();
+  }
+  if (owner) {
+    const cudaError_t e2 = cudaFreeAsync(owner, s);
+    if (err == cudaSuccess) err = e2;
+  }
+  return err;
 }

@@ -199,6 +199,8 @@ void free_all(lor_ctx* c) {
   cudaFree(c->ecorners);
   cudaFree(c->edofs);
   cudaFree(c->ess);
+  cudaFree(c->etail);
+  cudaFree(c->ehead);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
 }
 
@@ -442,23 +444,29 @@ int lor_assemble_unstructured(lor_ctx* c, int64_t nsub, const double* d_corners,
 int lor_discrete_gradient(lor_ctx* c, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
                           void* stream) {
   if (!c) return LOR_EINVAL;
-  if (c->general) return set_err(c, LOR_ESTATE, "lor_discrete_gradient: structured (lor_create) meshes only");
-  if (nedge) *nedge = lor_edge_count(c->m);
+  if (c->general && c->nedge < 0) {  // enumerate the LOR edges once
+    cudaError_t e = lor_general_edges(c->m, &c->etail, &c->ehead, &c->nedge, c->d_status, S(stream));
+    if (e != cudaSuccess) return cuda_err(c, e, "lor_discrete_gradient: edges");
+  }
+  const int64_t ne = c->general ? c->nedge : lor_edge_count(c->m);
+  if (nedge) *nedge = ne;
   if (!d_rowptr && !d_colidx && !d_values) return LOR_OK;
   if (!d_rowptr || !d_colidx || !d_values)
     return set_err(c, LOR_EINVAL, "lor_discrete_gradient: give all three output arrays or none");
   if (((uintptr_t)d_colidx & 7) || ((uintptr_t)d_values & 15))
     return set_err(c, LOR_EINVAL, "lor_discrete_gradient: colidx must be 8-byte and values 16-byte aligned");
   if (c->m.ndof > INT32_MAX) return set_err(c, LOR_EINVAL, "lor_discrete_gradient: more vertices than int32 columns");
-  cudaError_t e = lor_launch_discrete_gradient(c->m, d_rowptr, d_colidx, d_values, S(stream));
+  cudaError_t e = c->general
+                      ? lor_launch_general_gradient(ne, c->etail, c->ehead, d_rowptr, d_colidx, d_values, S(stream))
+                      : lor_launch_discrete_gradient(c->m, d_rowptr, d_colidx, d_values, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_discrete_gradient");
 }
 
 int lor_vertex_coordinates(lor_ctx* c, double* d_xyz, void* stream) {
   if (!c) return LOR_EINVAL;
-  if (c->general) return set_err(c, LOR_ESTATE, "lor_vertex_coordinates: structured (lor_create) meshes only");
   if (!d_xyz) return set_err(c, LOR_EINVAL, "lor_vertex_coordinates: xyz is NULL");
-  cudaError_t e = lor_launch_vertex_coordinates(c->m, c->T, d_xyz, S(stream));
+  cudaError_t e = c->general ? lor_launch_general_vertices(c->m, c->T, d_xyz, S(stream))
+                             : lor_launch_vertex_coordinates(c->m, c->T, d_xyz, S(stream));
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_vertex_coordinates");
 }
 

@@ -72,6 +72,9 @@ struct lor_ctx {
   double* ecorners = nullptr;  // general: [nel][8][3]
   int64_t* edofs = nullptr;    // general: [nel][(p+1)^3]
   uint8_t* ess = nullptr;      // general: [ndof]
+  int32_t* etail = nullptr;    // general: LOR edges (built on the first discrete-gradient call)
+  int32_t* ehead = nullptr;
+  int64_t nedge = -1;
   // preconditioner
   int pc_kind = LOR_PRECOND_NONE, pc_dtype = LOR_F64, pc_degree = 1;
   double pc_lo = 0, pc_hi = 0, pc_lmax = 0;
@@ -270,6 +273,14 @@ cudaError_t lor_launch_assemble_unstructured(int64_t nsub, const double* corners
 // (allocates *rowptr and *colidx, sets *nnz; synchronises), map validation
 cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr, int32_t** colidx, int64_t* nnz, int* d_status,
                                 cudaStream_t s);
+// the LOR edges of a general mesh (tail < head, ordered by tail then head;
+// allocates *tail and *head, synchronises), the discrete gradient from them,
+// and the vertex coordinates through the map
+cudaError_t lor_general_edges(const LorMesh& m, int32_t** tail, int32_t** head, int64_t* nedge, int* d_status,
+                              cudaStream_t s);
+cudaError_t lor_launch_general_gradient(int64_t nedge, const int32_t* tail, const int32_t* head, int64_t* rowptr,
+                                        int32_t* colidx, double* values, cudaStream_t s);
+cudaError_t lor_launch_general_vertices(const LorMesh& m, const LorTables& T, double* xyz, cudaStream_t s);
 // H(curl) topology of the LOR mesh (k_hcurl.cu)
 int64_t lor_edge_count(const LorMesh& m);
 cudaError_t lor_launch_discrete_gradient(const LorMesh& m, int64_t* rowptr, int32_t* colidx, double* values,

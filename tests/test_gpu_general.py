@@ -242,6 +242,28 @@ def test_general_mesh_errors():
     assert ei.value.code == LOR_EGEOM
     op = LOR.general(2, t(corners), t(edofs), N, t(ess))
     with pytest.raises(LORError) as ei:
-        op.discrete_gradient()
+        op.lor_mesh()
     assert ei.value.code == LOR_ESTATE
+    op.close()
+
+
+@pytest.mark.parametrize("dims,p", [((2, 2, 2), 1), ((2, 3, 1), 3), ((1, 2, 1), 6)])
+def test_general_discrete_gradient_and_vertices(dims, p):
+    """The LOR edges of the renumbered, rotated mesh are the renumbered edges
+    of the structured one (each from its lower to its higher DOF, ordered by
+    (tail, head)); the vertex coordinates are the renumbered oracle ones."""
+    prob, mesh, op, perm, *_ = make(dims, p)
+    rp, ci, v = op.discrete_gradient()
+    orp, oci, ov = oracle.discrete_gradient(*dims, p)
+    a, b = perm[oci[0::2]], perm[oci[1::2]]
+    ref = np.stack([np.minimum(a, b), np.maximum(a, b)], 1)
+    ref = ref[np.lexsort((ref[:, 1], ref[:, 0]))]
+    ne = ref.shape[0]
+    assert op.edge_count() == ne
+    np.testing.assert_array_equal(rp.cpu().numpy(), 2 * np.arange(ne + 1))
+    np.testing.assert_array_equal(ci.cpu().numpy().reshape(-1, 2).astype(np.int64), ref)
+    np.testing.assert_array_equal(v.cpu().numpy().reshape(-1, 2), np.tile([-1.0, 1.0], (ne, 1)))
+    xyz = op.vertex_coordinates().cpu().numpy()
+    oxyz = oracle.dof_coordinates(mesh, p)
+    np.testing.assert_allclose(xyz[perm], oxyz, rtol=0, atol=1e-14)
     op.close()
