@@ -15,7 +15,9 @@ reaction term of the definite Helmholtz problem under "helmholtz"; the
 macro-element vs unstructured LOR assembly at ~4M DOFs per degree under
 "assembly_comparator"; the discrete gradient and vertex coordinates of the
 32^3 p = 6 LOR mesh under "hcurl_topology"; the step's kernels on the same
-workload handed over as a general mesh under "general_mesh".
+workload handed over as a general mesh under "general_mesh"; the error of
+every mixed-precision result against its FP64 counterpart under
+"mixed_precision_errors".
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
@@ -309,6 +311,9 @@ def run_gpu(args, rank, world, local_rank):
     general = None
     if not args.no_general:
         general = run_general(args, dev)
+    precision = None
+    if not args.no_precision:
+        precision = run_precision(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -326,7 +331,7 @@ def run_gpu(args, rank, world, local_rank):
                    "steps": e2e_steps},
            "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad,
            "helmholtz": helm, "assembly_comparator": comparator, "hcurl_topology": hcurl,
-           "general_mesh": general}
+           "general_mesh": general, "mixed_precision_errors": precision}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     op.close()
@@ -686,6 +691,52 @@ def run_general(args, dev):
     return out
 
 
+def run_precision(args, dev):
+    """Error of every mixed-precision result against its FP64 counterpart on
+    the 16^3 p=4 workload (the FP64 path matches the FP64 oracle to 1e-12,
+    see the parity tests): LOR values (max relative error per row maximum),
+    SpMV, the Chebyshev-Jacobi preconditioned vector, and the PCG solution to
+    1e-8 (relative max-norm difference and the true FP64 residual of each)."""
+    import numpy as np
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import power_start_vector, workload
+
+    prob = workload(STEP_WORKLOAD)
+    op = LOR(prob.p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    op.set_coefficient(torch.tensor(prob.kappa.reshape(-1), device=dev), check=True)
+    rp, _ = op.build_pattern()
+    op.build_pattern_internal()
+    v64 = op.assemble(torch.float64)
+    v32 = op.assemble(torch.float32).double()
+    rows = torch.repeat_interleave(torch.arange(op.ndof, device=dev), rp[1:] - rp[:-1])
+    rowmax = torch.zeros(op.ndof, dtype=torch.float64, device=dev).scatter_reduce(0, rows, v64.abs(), "amax")
+    val_err = float(((v32 - v64).abs() / rowmax[rows]).max())
+    x = torch.tensor(np.random.default_rng(8).standard_normal(op.ndof), device=dev)
+    b = torch.tensor(prob.rhs, device=dev)
+    v0 = torch.tensor(power_start_vector(op.ndof), device=dev)
+    out = {"workload": STEP_WORKLOAD, "lor_values_f32_max_rel_err": val_err}
+    res = {}
+    for dt in (torch.float64, torch.float32):
+        op.assemble_internal(dt)
+        lam = op.precond_setup("cheb", dt, degree=3, power_iters=20, v0=v0)
+        res[dt] = {"lam": lam, "spmv": op.spmv(x, dt), "z": op.precond_apply(b)}
+        u, it, rel = op.pcg_solve(b, 1e-8, 20000)
+        true_rel = float((b - op.apply(u)).norm() / b.norm())
+        res[dt].update(u=u, it=it, true_rel=true_rel)
+    rel = lambda a, r: float((a - r).abs().max() / r.abs().max())
+    out.update({
+        "lambda_max_f32_rel_err": abs(res[torch.float32]["lam"] - res[torch.float64]["lam"]) / res[torch.float64]["lam"],
+        "spmv_f32_max_rel_err": rel(res[torch.float32]["spmv"], res[torch.float64]["spmv"]),
+        "precond_f32_max_rel_err": rel(res[torch.float32]["z"], res[torch.float64]["z"]),
+        "pcg_iterations_f64_mixed": [res[torch.float64]["it"], res[torch.float32]["it"]],
+        "pcg_true_rel_residual_f64_mixed": [res[torch.float64]["true_rel"], res[torch.float32]["true_rel"]],
+        "pcg_solution_mixed_vs_f64_max_rel_diff": rel(res[torch.float32]["u"], res[torch.float64]["u"])})
+    op.close()
+    return out
+
+
 def run_sweep(args, dev):
     """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
     JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
@@ -846,6 +897,7 @@ def main(argv=None):
     ap.add_argument("--no-grad", action="store_true", help="skip the 24^3 p=5 adjoint-gradient timing")
     ap.add_argument("--no-hcurl", action="store_true", help="skip the discrete-gradient / vertex-coordinate timing")
     ap.add_argument("--no-general", action="store_true", help="skip the general-mesh (element-restriction) timing")
+    ap.add_argument("--no-precision", action="store_true", help="skip the mixed-precision error report")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip the macro-element vs unstructured LOR assembly comparison")
     ap.add_argument("--no-helmholtz", action="store_true",
