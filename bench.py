@@ -376,6 +376,24 @@ def run_pcg(args, dev, rank):
                       "setup_s": ev[0].elapsed_time(ev[2]) / 1e3,
                       "s_per_iteration": solve_s / max(it, 1)}
     res["mixed_speedup"] = res["fp64"]["solve_s"] / res["mixed"]["solve_s"]
+    if args.pcg_degrees:
+        # supplementary: the Chebyshev degree trade-off (the FP32 smoother is
+        # cheap next to the FP64 apply), mixed precision and FP64, same lambda
+        lam = res["mixed"]["lambda_max"]
+        res["degree_sweep"] = []
+        for k in args.pcg_degrees:
+            row = {"degree": k}
+            for label, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+                op.assemble_internal(dt)
+                op.precond_setup("cheb", dt, degree=k, lambda_max=lam)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, it, _ = op.pcg_solve(b, 1e-8, 20000)
+                e1.record()
+                torch.cuda.synchronize()
+                row[label] = {"solve_s": e0.elapsed_time(e1) / 1e3, "iterations": it}
+            res["degree_sweep"].append(row)
     op.close()
     return res
 
@@ -906,6 +924,8 @@ def main(argv=None):
     ap.add_argument("--pcg-maxit", type=int, default=20000,
                     help="iteration cap of the PCG comparison (a small cap is for profiling only)")
     ap.add_argument("--pcg-only", action="store_true", help="run only the PCG comparison (profiling)")
+    ap.add_argument("--pcg-degrees", type=int, nargs="*", default=None,
+                    help="also solve with these Chebyshev degrees (supplementary degree trade-off)")
     ap.add_argument("--sweep", action="store_true", help="per-kernel throughput versus p at ~20M DOFs")
     ap.add_argument("--sweep-p", type=int, nargs="*", default=list(range(2, 11)))
     ap.add_argument("--sweep-reps", type=int, default=5)
