@@ -43,10 +43,13 @@ struct Sz {
   // elements per CTA and CTA size: the z stage (the heaviest) gets about one
   // line per thread, and high-degree CTAs stay small so that several share an
   // SM (the FP64 pipe then stays busy while one CTA waits at a barrier)
-  static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 3 : P == 6 ? 2
-                         : P == 7 ? 3 : P <= 9 ? 2 : 1;
-  static constexpr int EB = E;
+  static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 4
+                         : P == 7 ? 3 : P == 8 ? 3 : P == 9 ? 2 : 2;
   static constexpr int T = ((E * Q * Q + 31) / 32) * 32;
+  // the backward holds two fields per element (twice the shared memory)
+  static constexpr int EB = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 3 : P == 6 ? 2
+                          : P == 7 ? 3 : P <= 9 ? 2 : 1;
+  static constexpr int TBW = ((EB * Q * Q + 31) / 32) * 32;
   // folded tables in shared memory (doubles)
   static constexpr int TB = Q * N;                  // B_1D, d_1D
   static constexpr int TF = Q * (NH > 0 ? NH : 1);  // BE, BO, DE, DO: [g][i], g < Q, i < NH
@@ -92,18 +95,28 @@ __device__ __forceinline__ Tab<P> load_tables(const LorTables& T, double* s) {
   return t;
 }
 
-// ---- 1D line operators (u has n entries, y has q entries, or the reverse) ----
+// Table entry k of a 1D table in shared memory, read as volatile: the
+// compiler then re-reads the entry at each use instead of holding the
+// loop-invariant tables in registers across the line loops (which, with the
+// tables of degree 6 and up, needs more than 255 registers and spills; below
+// that it only costs occupancy).  A shared-memory read is far cheaper than
+// the FP64 multiply-add it feeds.
+template <int P>
+__device__ __forceinline__ double tabv(const double* tbl, int k) {
+  return static_cast<const volatile double*>(tbl)[k];
+}
+
 // y = B_1D u, from the folded input e_i = u_i + u_{n-1-i}, o_i = u_i - u_{n-1-i}, um = u_mid
 template <int P>
 __device__ __forceinline__ void fwd_B(const Tab<P>& t, const double* e, const double* o, double um, double* y) {
   using Z = Sz<P>;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
-    double ev = Z::NODD ? t.B[g * Z::N + Z::NM] * um : 0.0, od = 0.0;
+    double ev = Z::NODD ? tabv<P>(t.B, g * Z::N + Z::NM) * um : 0.0, od = 0.0;
 #pragma unroll
     for (int i = 0; i < Z::NH; ++i) {
-      ev += t.BE[g * Z::NH + i] * e[i];
-      od += t.BO[g * Z::NH + i] * o[i];
+      ev += tabv<P>(t.BE, g * Z::NH + i) * e[i];
+      od += tabv<P>(t.BO, g * Z::NH + i) * o[i];
     }
     y[g] = ev + od;
     y[Z::Q - 1 - g] = ev - od;
@@ -111,7 +124,7 @@ __device__ __forceinline__ void fwd_B(const Tab<P>& t, const double* e, const do
   if (Z::QODD) {
     double ev = 0.0;
 #pragma unroll
-    for (int i = 0; i < Z::NH; ++i) ev += t.BE[Z::QM * Z::NH + i] * e[i];
+    for (int i = 0; i < Z::NH; ++i) ev += tabv<P>(t.BE, Z::QM * Z::NH + i) * e[i];
     y[Z::QM] = ev;
   }
 }
@@ -121,11 +134,11 @@ __device__ __forceinline__ void fwd_D(const Tab<P>& t, const double* e, const do
   using Z = Sz<P>;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
-    double s = Z::NODD ? t.D[g * Z::N + Z::NM] * um : 0.0, d = 0.0;
+    double s = Z::NODD ? tabv<P>(t.D, g * Z::N + Z::NM) * um : 0.0, d = 0.0;
 #pragma unroll
     for (int i = 0; i < Z::NH; ++i) {
-      s += t.DE[g * Z::NH + i] * e[i];
-      d += t.DO[g * Z::NH + i] * o[i];
+      s += tabv<P>(t.DE, g * Z::NH + i) * e[i];
+      d += tabv<P>(t.DO, g * Z::NH + i) * o[i];
     }
     y[g] = d + s;
     y[Z::Q - 1 - g] = d - s;
@@ -133,7 +146,7 @@ __device__ __forceinline__ void fwd_D(const Tab<P>& t, const double* e, const do
   if (Z::QODD) {
     double d = 0.0;
 #pragma unroll
-    for (int i = 0; i < Z::NH; ++i) d += t.DO[Z::QM * Z::NH + i] * o[i];
+    for (int i = 0; i < Z::NH; ++i) d += tabv<P>(t.DO, Z::QM * Z::NH + i) * o[i];
     y[Z::QM] = d;
   }
 }
@@ -170,18 +183,18 @@ __device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const dou
   for (int i = 0; i < Z::NH; ++i) {
     double a1 = 0.0, a2 = 0.0;
     if (Z::QODD) {
-      if (USE_B) a1 += t.B[Z::QM * Z::N + i] * m1;
-      if (USE_D) a2 += t.D[Z::QM * Z::N + i] * m2;
+      if (USE_B) a1 += tabv<P>(t.B, Z::QM * Z::N + i) * m1;
+      if (USE_D) a2 += tabv<P>(t.D, Z::QM * Z::N + i) * m2;
     }
 #pragma unroll
     for (int g = 0; g < Z::QH; ++g) {
       if (USE_B) {
-        a1 += t.BE[g * Z::NH + i] * e1[g];
-        a2 += t.BO[g * Z::NH + i] * o1[g];
+        a1 += tabv<P>(t.BE, g * Z::NH + i) * e1[g];
+        a2 += tabv<P>(t.BO, g * Z::NH + i) * o1[g];
       }
       if (USE_D) {
-        a1 += t.DE[g * Z::NH + i] * o2[g];
-        a2 += t.DO[g * Z::NH + i] * e2[g];
+        a1 += tabv<P>(t.DE, g * Z::NH + i) * o2[g];
+        a2 += tabv<P>(t.DO, g * Z::NH + i) * e2[g];
       }
     }
     y[i] = a1 + a2;
@@ -191,8 +204,8 @@ __device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const dou
     double s = 0.0;
 #pragma unroll
     for (int g = 0; g < Z::QH; ++g) {
-      if (USE_B) s += t.B[g * Z::N + Z::NM] * e1[g];
-      if (USE_D) s += t.D[g * Z::N + Z::NM] * o2[g];
+      if (USE_B) s += tabv<P>(t.B, g * Z::N + Z::NM) * e1[g];
+      if (USE_D) s += tabv<P>(t.D, g * Z::N + Z::NM) * o2[g];
     }
     y[Z::NM] = s;
   }
@@ -469,7 +482,7 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
 // gx = A_p gy (with the reaction term if present) through the same
 // transposed stages as the apply.
 template <int P, bool MASS, bool GEN>
-__global__ void __launch_bounds__(Sz<P>::T, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
+__global__ void __launch_bounds__(Sz<P>::TBW, P <= 6 ? 2 : 1) k_apply_backward(LorMesh m, LorTables T,
                                                              const double* __restrict__ Dq,
                                                              const double* __restrict__ Mq,
                                                              const double* __restrict__ kappa,
@@ -569,7 +582,7 @@ cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, c
   cudaError_t err = configure(k_apply_backward<P, MASS, GEN>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::EB - 1) / Z::EB;
-  k_apply_backward<P, MASS, GEN><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
+  k_apply_backward<P, MASS, GEN><<<(unsigned)blocks, Z::TBW, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
   lor_count_launch();
   return cudaGetLastError();
 }
