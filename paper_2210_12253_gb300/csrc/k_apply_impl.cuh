@@ -46,9 +46,9 @@ struct Sz {
   static constexpr int E = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 4
                          : P == 7 ? 3 : P == 8 ? 3 : P == 9 ? 2 : 2;
   static constexpr int T = ((E * Q * Q + 31) / 32) * 32;
-  // the backward holds two fields per element (twice the shared memory)
-  static constexpr int EB = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 3 : P == 6 ? 2
-                          : P == 7 ? 3 : P <= 9 ? 2 : 1;
+  // the backward holds two fields per element (twice the shared memory; at
+  // p = 10 two elements would exceed the 227 KB a CTA may use)
+  static constexpr int EB = P == 6 ? 2 : P == 10 ? 1 : E;
   static constexpr int TBW = ((EB * Q * Q + 31) / 32) * 32;
   // folded tables in shared memory (doubles)
   static constexpr int TB = Q * N;                  // B_1D, d_1D
