@@ -404,12 +404,15 @@ def run_pcg(args, dev, rank):
         u, it, rel = op.pcg_solve(b, 1e-8, args.pcg_maxit, raise_on_noconv=args.pcg_maxit >= 20000)
         e1.record()
         torch.cuda.synchronize()
+        if label == "fp64":
+            u64 = u.clone()
         solve_s = e0.elapsed_time(e1) / 1e3
         res[label] = {"solve_s": solve_s, "wall_s": time.perf_counter() - t0, "iterations": it,
                       "final_rel_residual": rel, "lambda_max": lam,
                       "setup_s": ev[0].elapsed_time(ev[2]) / 1e3,
                       "s_per_iteration": solve_s / max(it, 1)}
     res["mixed_speedup"] = res["fp64"]["solve_s"] / res["mixed"]["solve_s"]
+    res.update(run_refinement(args, op, b, res, u64))
     if args.pcg_degrees:
         # supplementary: the Chebyshev degree trade-off (the FP32 smoother is
         # cheap next to the FP64 apply), mixed precision and FP64, same lambda
@@ -430,6 +433,76 @@ def run_pcg(args, dev, rank):
             res["degree_sweep"].append(row)
     op.close()
     return res
+
+
+def run_refinement(args, op, b, res, u64):
+    """Mixed-precision iterative refinement on the PCG workload (same FP32 LOR
+    matrix and smoother as "mixed"): FP64 outer residuals, inner PCG with the
+    FP32-arithmetic operator to inner_rtol; and the FP32 apply kernel against
+    the FP64 one (D larger than L2 at this size, so no flush is needed)."""
+    import torch
+
+    from paper_2210_12253_gb300.perfmodel import FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
+
+    out = {}
+    hbm, hbm_src = hbm_peak_gbs()
+    x = torch.randn(op.ndof, dtype=torch.float64, device=b.device)
+    y = torch.empty_like(x)
+    kern = {}
+    for label, fn, kind in (("apply_f64", op.apply, "apply"), ("apply_f32", op.apply_f32, "apply_f32")):
+        fn(x, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            fn(x, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        flops, byts = kernel_work(kind, op.p, op.ndof, op.nel, op.nnz)
+        peak = FP32_PEAK_TFLOPS if kind == "apply_f32" else FP64_PEAK_TFLOPS
+        kern[label] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9, "gbs": byts / (ms * 1e-3) / 1e9,
+                       "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                       "tflops": flops / (ms * 1e-3) / 1e12, "frac_alu": flops / (ms * 1e-3) / 1e12 / peak,
+                       "alu": "fp32" if kind == "apply_f32" else "fp64"}
+    y32 = op.apply_f32(x)
+    y64 = op.apply(x)
+    kern["apply_f32_max_rel_err"] = ((y32 - y64).abs().max() / y64.abs().max()).item()
+    kern["hbm_peak_gbs"] = hbm
+    kern["hbm_peak_source"] = hbm_src
+    kern["note"] = ("both include the FP64 output initialisation launch; ms per apply, 10 back-to-back "
+                    "applies (D: 805 MB FP64 / 403 MB FP32, larger than L2)")
+    out["apply_kernels"] = kern
+
+    op.assemble_internal(torch.float32)
+    op.precond_setup("cheb", torch.float32, degree=3, lambda_max=res["mixed"]["lambda_max"])
+    xs = torch.empty_like(b)
+    op.pcg_solve_ir(b, 1e-8, args.ir_inner_rtol, 3, x=xs, raise_on_noconv=False)  # warm-up
+    rows = []
+    for inner_rtol in [args.ir_inner_rtol] + [r for r in (args.ir_sweep or []) if r != args.ir_inner_rtol]:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        u, outer, inner, rel = op.pcg_solve_ir(b, 1e-8, inner_rtol, args.pcg_maxit, x=xs,
+                                               raise_on_noconv=args.pcg_maxit >= 20000)
+        e1.record()
+        torch.cuda.synchronize()
+        solve_s = e0.elapsed_time(e1) / 1e3
+        rows.append({"inner_rtol": inner_rtol, "solve_s": solve_s, "wall_s": time.perf_counter() - t0,
+                     "outer_iterations": outer, "inner_iterations": inner, "final_rel_residual": rel,
+                     "s_per_inner_iteration": solve_s / max(inner, 1),
+                     "speedup_vs_fp64": res["fp64"]["solve_s"] / solve_s,
+                     "speedup_vs_mixed": res["mixed"]["solve_s"] / solve_s,
+                     "solution_vs_fp64_max_rel_diff": ((u - u64).abs().max() / u64.abs().max()).item()})
+    out["mixed_ir"] = rows[0]
+    out["mixed_ir"]["scheme"] = ("iterative refinement: r = b - A_p x with the FP64 operator each outer step; "
+                                 "correction by PCG (FP32 LOR Chebyshev deg 3, FP64 dots/recurrences) with the "
+                                 "FP32-arithmetic operator to inner_rtol; stop on the FP64 residual")
+    if len(rows) > 1:
+        out["mixed_ir_inner_rtol_sweep"] = rows
+    return out
 
 
 def run_gradient(args, dev):
@@ -958,6 +1031,10 @@ def main(argv=None):
     ap.add_argument("--pcg-maxit", type=int, default=20000,
                     help="iteration cap of the PCG comparison (a small cap is for profiling only)")
     ap.add_argument("--pcg-only", action="store_true", help="run only the PCG comparison (profiling)")
+    ap.add_argument("--ir-inner-rtol", type=float, default=1e-4,
+                    help="inner tolerance of the mixed-precision iterative refinement")
+    ap.add_argument("--ir-sweep", type=float, nargs="*", default=None,
+                    help="also time the refinement at these inner tolerances")
     ap.add_argument("--pcg-degrees", type=int, nargs="*", default=None,
                     help="also solve with these Chebyshev degrees (supplementary degree trade-off)")
     ap.add_argument("--sweep", action="store_true", help="per-kernel throughput versus p at ~20M DOFs")

@@ -240,6 +240,16 @@ int lor_vertex_coordinates(lor_ctx* ctx, double* d_xyz, void* stream);
  * alias. */
 int lor_apply(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
 
+/* y = A_p x as lor_apply computes it, but with FP32 arithmetic inside the
+ * kernel: the 1D tables, the stage buffers and D (and beta w detJ) are FP32
+ * (rounded copies of the FP64 factors, made by the first FP32 call after
+ * lor_set_coefficient / lor_set_reaction); x is read and y accumulated in
+ * FP64.  Relative error about 1e-6 of |A_p| |x|.  It is the operator of the
+ * inner solves of lor_pcg_solve_ir; the FP64 lor_apply stays the operator of
+ * every residual that decides convergence.  d_x, d_y: f64[N], must not alias.
+ * The paper has no counterpart (it runs the operator in FP64 only). */
+int lor_apply_f32(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
+
 /* Backward of y = A_p(kappa) x for the cotangent d_gy (FP64):
  *   d_gx     = A_p gy (with the reaction term if set)     (f64[N], may be NULL)
  *   d_gkappa = d(gy^T A_p x)/d kappa = grad_ref(x)^T (D/kappa) grad_ref(gy)
@@ -308,6 +318,25 @@ int lor_precond_apply_noalloc(lor_ctx* ctx, const double* d_r, double* d_z, void
  * the stream (it reads the residual norm on the host). */
 int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int maxit, int* iters,
                   double* final_rel_residual, void* stream);
+
+/* Mixed-precision iterative refinement (Wilkinson; Moler 1967) for the same
+ * system, with x_0 = 0:
+ *   repeat: r = b - A_p x            (FP64 operator, FP64 vectors)
+ *           stop if |r|/|b| <= rtol
+ *           solve A_p d = r by PCG from d_0 = 0 until |r_k| <= inner_rtol |r|,
+ *             with the FP32 operator of lor_apply_f32 and the preconditioner
+ *             of lor_precond_setup (dots and recurrences FP64)
+ *           x += d
+ * so the stopping residual is always the FP64 one, while the inner
+ * iterations run the FP32 operator (on this GPU the FP32 pipe is about 60x
+ * the FP64 one).  maxit bounds the inner iterations over all outer steps;
+ * at most 64 outer steps.  *outer_iters, *inner_iters, *final_rel_residual
+ * (host, may be NULL) receive the counts and the final FP64 relative
+ * residual.  LOR_ENOCONV when maxit or the outer limit is reached first, or
+ * when an outer step does not reduce the residual.  Synchronises the stream.
+ * The paper has no counterpart: it solves with PCG in FP64. */
+int lor_pcg_solve_ir(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, double inner_rtol, int maxit,
+                     int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream);
 
 #ifdef __cplusplus
 }

@@ -44,7 +44,14 @@ cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, co
                                         const double* x, double* y, cudaStream_t s) {
   if (m.edofs) return lor_apply_general_dispatch(m, T, Dq, Mq, x, y, s);
   if (Mq) return lor_apply_mass_dispatch(m, T, Dq, Mq, x, y, s);
-  return apply_dispatch<false, false>(m, T, Dq, nullptr, x, y, s);
+  return apply_dispatch<false, false, double>(m, T, Dq, nullptr, x, y, s);
+}
+
+cudaError_t lor_launch_apply_f32(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                 const double* x, double* y, cudaStream_t s) {
+  cudaError_t err = init_output(m, x, y, s);
+  if (err != cudaSuccess) return err;
+  return lor_launch_apply_f32_accumulate(m, T, Dq, Mq, x, y, s);
 }
 
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,

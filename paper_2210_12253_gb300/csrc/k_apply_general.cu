@@ -6,8 +6,8 @@
 
 cudaError_t lor_apply_general_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                        const double* x, double* y, cudaStream_t s) {
-  if (Mq) return apply_dispatch<true, true>(m, T, Dq, Mq, x, y, s);
-  return apply_dispatch<false, true>(m, T, Dq, nullptr, x, y, s);
+  if (Mq) return apply_dispatch<true, true, double>(m, T, Dq, Mq, x, y, s);
+  return apply_dispatch<false, true, double>(m, T, Dq, nullptr, x, y, s);
 }
 
 cudaError_t lor_backward_general_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,

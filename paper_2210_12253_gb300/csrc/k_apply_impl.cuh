@@ -58,33 +58,33 @@ struct Sz {
 
 // Folded tables: BE = (B[g][i] + B[g][n-1-i]) / 2, BO = (B[g][i] - B[g][n-1-i]) / 2
 // (same for d), for i < n/2.
-template <int P>
+template <int P, typename R>
 struct Tab {
-  const double *B, *D, *BE, *BO, *DE, *DO;
+  const R *B, *D, *BE, *BO, *DE, *DO;
 };
 
-template <int P>
-__device__ __forceinline__ Tab<P> load_tables(const LorTables& T, double* s) {
+template <int P, typename R>
+__device__ __forceinline__ Tab<P, R> load_tables(const LorTables& T, R* s) {
   using Z = Sz<P>;
-  Tab<P> t;
-  double* B = s;
-  double* D = s + Z::TB;
-  double* BE = s + 2 * Z::TB;
-  double* BO = BE + Z::TF;
-  double* DE = BO + Z::TF;
-  double* DO = DE + Z::TF;
+  Tab<P, R> t;
+  R* B = s;
+  R* D = s + Z::TB;
+  R* BE = s + 2 * Z::TB;
+  R* BO = BE + Z::TF;
+  R* DE = BO + Z::TF;
+  R* DO = DE + Z::TF;
   for (int x = threadIdx.x; x < Z::TB; x += blockDim.x) {
-    B[x] = T.B[x];
-    D[x] = T.Dm[x];
+    B[x] = (R)T.B[x];
+    D[x] = (R)T.Dm[x];
   }
   for (int x = threadIdx.x; x < Z::Q * Z::NH; x += blockDim.x) {
     const int g = x / Z::NH, i = x % Z::NH;
     const double b0 = T.B[g * Z::N + i], b1 = T.B[g * Z::N + Z::N - 1 - i];
     const double d0 = T.Dm[g * Z::N + i], d1 = T.Dm[g * Z::N + Z::N - 1 - i];
-    BE[g * Z::NH + i] = 0.5 * (b0 + b1);
-    BO[g * Z::NH + i] = 0.5 * (b0 - b1);
-    DE[g * Z::NH + i] = 0.5 * (d0 + d1);
-    DO[g * Z::NH + i] = 0.5 * (d0 - d1);
+    BE[g * Z::NH + i] = (R)(0.5 * (b0 + b1));
+    BO[g * Z::NH + i] = (R)(0.5 * (b0 - b1));
+    DE[g * Z::NH + i] = (R)(0.5 * (d0 + d1));
+    DO[g * Z::NH + i] = (R)(0.5 * (d0 - d1));
   }
   t.B = B;
   t.D = D;
@@ -101,111 +101,117 @@ __device__ __forceinline__ Tab<P> load_tables(const LorTables& T, double* s) {
 // tables of degree 6 and up, needs more than 255 registers and spills; below
 // that it only costs occupancy).  A shared-memory read is far cheaper than
 // the FP64 multiply-add it feeds.
-template <int P>
-__device__ __forceinline__ double tabv(const double* tbl, int k) {
-  return static_cast<const volatile double*>(tbl)[k];
+//
+// In FP32 the tables are small enough to live in registers and the FP32
+// pipe is 64 times faster than the FP64 one, so there the entries are plain
+// loads the compiler may hoist (a shared-memory read per multiply-add would
+// bound the kernel).
+template <int P, typename R>
+__device__ __forceinline__ R tabv(const R* tbl, int k) {
+  if constexpr (sizeof(R) == sizeof(double)) return static_cast<const volatile R*>(tbl)[k];
+  else return tbl[k];
 }
 
 // y = B_1D u, from the folded input e_i = u_i + u_{n-1-i}, o_i = u_i - u_{n-1-i}, um = u_mid
-template <int P>
-__device__ __forceinline__ void fwd_B(const Tab<P>& t, const double* e, const double* o, double um, double* y) {
+template <int P, typename R>
+__device__ __forceinline__ void fwd_B(const Tab<P, R>& t, const R* e, const R* o, R um, R* y) {
   using Z = Sz<P>;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
-    double ev = Z::NODD ? tabv<P>(t.B, g * Z::N + Z::NM) * um : 0.0, od = 0.0;
+    R ev = Z::NODD ? tabv<P, R>(t.B, g * Z::N + Z::NM) * um : (R)0, od = 0;
 #pragma unroll
     for (int i = 0; i < Z::NH; ++i) {
-      ev += tabv<P>(t.BE, g * Z::NH + i) * e[i];
-      od += tabv<P>(t.BO, g * Z::NH + i) * o[i];
+      ev += tabv<P, R>(t.BE, g * Z::NH + i) * e[i];
+      od += tabv<P, R>(t.BO, g * Z::NH + i) * o[i];
     }
     y[g] = ev + od;
     y[Z::Q - 1 - g] = ev - od;
   }
   if (Z::QODD) {
-    double ev = 0.0;
+    R ev = 0.0;
 #pragma unroll
-    for (int i = 0; i < Z::NH; ++i) ev += tabv<P>(t.BE, Z::QM * Z::NH + i) * e[i];
+    for (int i = 0; i < Z::NH; ++i) ev += tabv<P, R>(t.BE, Z::QM * Z::NH + i) * e[i];
     y[Z::QM] = ev;
   }
 }
 // y = d_1D u
-template <int P>
-__device__ __forceinline__ void fwd_D(const Tab<P>& t, const double* e, const double* o, double um, double* y) {
+template <int P, typename R>
+__device__ __forceinline__ void fwd_D(const Tab<P, R>& t, const R* e, const R* o, R um, R* y) {
   using Z = Sz<P>;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
-    double s = Z::NODD ? tabv<P>(t.D, g * Z::N + Z::NM) * um : 0.0, d = 0.0;
+    R s = Z::NODD ? tabv<P, R>(t.D, g * Z::N + Z::NM) * um : (R)0, d = 0;
 #pragma unroll
     for (int i = 0; i < Z::NH; ++i) {
-      s += tabv<P>(t.DE, g * Z::NH + i) * e[i];
-      d += tabv<P>(t.DO, g * Z::NH + i) * o[i];
+      s += tabv<P, R>(t.DE, g * Z::NH + i) * e[i];
+      d += tabv<P, R>(t.DO, g * Z::NH + i) * o[i];
     }
     y[g] = d + s;
     y[Z::Q - 1 - g] = d - s;
   }
   if (Z::QODD) {
-    double d = 0.0;
+    R d = 0.0;
 #pragma unroll
-    for (int i = 0; i < Z::NH; ++i) d += tabv<P>(t.DO, Z::QM * Z::NH + i) * o[i];
+    for (int i = 0; i < Z::NH; ++i) d += tabv<P, R>(t.DO, Z::QM * Z::NH + i) * o[i];
     y[Z::QM] = d;
   }
 }
-template <int P>
-__device__ __forceinline__ void fold_n(const double* u, double* e, double* o, double& um) {
+template <int P, typename R>
+__device__ __forceinline__ void fold_n(const R* u, R* e, R* o, R& um) {
   using Z = Sz<P>;
 #pragma unroll
   for (int i = 0; i < Z::NH; ++i) {
     e[i] = u[i] + u[Z::N - 1 - i];
     o[i] = u[i] - u[Z::N - 1 - i];
   }
-  um = Z::NODD ? u[Z::NM] : 0.0;
+  um = Z::NODD ? u[Z::NM] : (R)0;
 }
-template <int P>
-__device__ __forceinline__ void fold_q(const double* v, double* e, double* o, double& vm) {
+template <int P, typename R>
+__device__ __forceinline__ void fold_q(const R* v, R* e, R* o, R& vm) {
   using Z = Sz<P>;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
     e[g] = v[g] + v[Z::Q - 1 - g];
     o[g] = v[g] - v[Z::Q - 1 - g];
   }
-  vm = Z::QODD ? v[Z::QM] : 0.0;
+  vm = Z::QODD ? v[Z::QM] : (R)0;
 }
 // y = B_1D^T v1 + d_1D^T v2 (either part may be switched off); v1, v2 folded
 // as (e, o, middle) over the q Gauss points.
-template <int P, bool USE_B, bool USE_D>
-__device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const double* o1, double m1,
-                                    const double* e2, const double* o2, double m2, double* y) {
+template <int P, bool USE_B, bool USE_D, typename R>
+__device__ __forceinline__ void bwd(const Tab<P, R>& t, const R* e1, const R* o1, R m1,
+                                    const R* e2, const R* o2, R m2, R* y) {
   using Z = Sz<P>;
   // B^T part: Ev_i = sum_g BE[g][i] e1_g (+ B[qm][i] m1), Od_i = sum_g BO[g][i] o1_g
   // d^T part: S_i = sum_g DO[g][i] e2_g (+ d[qm][i] m2),  T_i = sum_g DE[g][i] o2_g
   // y_i = (Ev + T) + (Od + S), y_{n-1-i} = (Ev + T) - (Od + S)
 #pragma unroll
   for (int i = 0; i < Z::NH; ++i) {
-    double a1 = 0.0, a2 = 0.0;
+    R a1 = 0.0, a2 = 0.0;
     if (Z::QODD) {
-      if (USE_B) a1 += tabv<P>(t.B, Z::QM * Z::N + i) * m1;
-      if (USE_D) a2 += tabv<P>(t.D, Z::QM * Z::N + i) * m2;
+      if (USE_B) a1 += tabv<P, R>(t.B, Z::QM * Z::N + i) * m1;
+      if (USE_D) a2 += tabv<P, R>(t.D, Z::QM * Z::N + i) * m2;
     }
 #pragma unroll
     for (int g = 0; g < Z::QH; ++g) {
       if (USE_B) {
-        a1 += tabv<P>(t.BE, g * Z::NH + i) * e1[g];
-        a2 += tabv<P>(t.BO, g * Z::NH + i) * o1[g];
+        a1 += tabv<P, R>(t.BE, g * Z::NH + i) * e1[g];
+        a2 += tabv<P, R>(t.BO, g * Z::NH + i) * o1[g];
       }
       if (USE_D) {
-        a1 += tabv<P>(t.DE, g * Z::NH + i) * o2[g];
-        a2 += tabv<P>(t.DO, g * Z::NH + i) * e2[g];
+        a1 += tabv<P, R>(t.DE, g * Z::NH + i) * o2[g];
+        a2 += tabv<P, R>(t.DO, g * Z::NH + i) * e2[g];
       }
     }
     y[i] = a1 + a2;
     y[Z::N - 1 - i] = a1 - a2;
   }
   if (Z::NODD) {
-    double s = 0.0;
+    R s = 0.0;
 #pragma unroll
     for (int g = 0; g < Z::QH; ++g) {
-      if (USE_B) s += tabv<P>(t.B, g * Z::N + Z::NM) * e1[g];
-      if (USE_D) s += tabv<P>(t.D, g * Z::N + Z::NM) * o2[g];
+      if (USE_B) s += tabv<P, R>(t.B, g * Z::N + Z::NM) * e1[g];
+      if (USE_D) s += tabv<P, R>(t.D, g * Z::N + Z::NM) * o2[g];
     }
     y[Z::NM] = s;
   }
@@ -214,9 +220,9 @@ __device__ __forceinline__ void bwd(const Tab<P>& t, const double* e1, const dou
 // ---- stages over all lines of E elements (e_first .. e_first+E-1) ----
 // X: u (gathered from global, masked) -> A1[c][k][j][g0] = (B u, d u) along x.
 // GEN: through the general element-to-DOF map and essential mask.
-template <int P, bool GEN>
-__device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
-                                        const double* __restrict__ x, double* A) {
+template <int P, bool GEN, typename R>
+__device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E,
+                                        const double* __restrict__ x, R* A) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
   for (int w = threadIdx.x; w < E * N * N; w += blockDim.x) {
@@ -224,13 +230,13 @@ __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64
     const int64_t e = e_first + le;
     if (e >= m.nel) continue;
     const int j = jk % N, k = jk / N;
-    double u[N];
+    R u[N];
     if constexpr (GEN) {
       const int64_t* dm = m.edofs + e * (N * N * N) + jk * N;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t d = dm[i];
-        u[i] = m.ess[d] ? 0.0 : x[d];
+        u[i] = m.ess[d] ? (R)0 : (R)x[d];
       }
     } else {
       const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
@@ -240,15 +246,15 @@ __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t I = ex * P + i;
-        u[i] = (row_ess || I == 0 || I == m.nx - 1) ? 0.0 : xr[i];
+        u[i] = (row_ess || I == 0 || I == m.nx - 1) ? (R)0 : (R)xr[i];
       }
     }
-    double e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], um;
+    R e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], um;
     fold_n<P>(u, e_, o_, um);
-    double yb[Q], yd[Q];
+    R yb[Q], yd[Q];
     fwd_B<P>(t, e_, o_, um, yb);
     fwd_D<P>(t, e_, o_, um, yd);
-    double* a = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
+    R* a = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
 #pragma unroll
     for (int g = 0; g < Q; ++g) {
       a[g] = yb[g];
@@ -258,27 +264,27 @@ __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P>& t, int64
 }
 
 // Y: A1 -> A2[c][k][g1][g0] with c = 0: B_y Bu (BB), 1: B_y du (BD), 2: d_y Bu (DB).
-template <int P>
-__device__ __forceinline__ void stage_y(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E, double* A) {
+template <int P, typename R>
+__device__ __forceinline__ void stage_y(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E, R* A) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
   for (int w = threadIdx.x; w < E * N * Q; w += blockDim.x) {
     const int le = w / (N * Q), r = w % (N * Q);
     if (e_first + le >= m.nel) continue;
     const int g0 = r % Q, k = r / Q;
-    const double* a1 = A + (size_t)le * Z::PER_ELEM;
-    double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
-    double bu[N], du[N];
+    const R* a1 = A + (size_t)le * Z::PER_ELEM;
+    R* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+    R bu[N], du[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       bu[j] = a1[(k * N + j) * Q + g0];
       du[j] = a1[N * N * Q + (k * N + j) * Q + g0];
     }
-    double eb[Z::NH > 0 ? Z::NH : 1], ob[Z::NH > 0 ? Z::NH : 1], mb, ed[Z::NH > 0 ? Z::NH : 1],
+    R eb[Z::NH > 0 ? Z::NH : 1], ob[Z::NH > 0 ? Z::NH : 1], mb, ed[Z::NH > 0 ? Z::NH : 1],
         od[Z::NH > 0 ? Z::NH : 1], md;
     fold_n<P>(bu, eb, ob, mb);
     fold_n<P>(du, ed, od, md);
-    double y[Q];
+    R y[Q];
     fwd_B<P>(t, eb, ob, mb, y);
 #pragma unroll
     for (int g = 0; g < Q; ++g) a2[(k * Q + g) * Q + g0] = y[g];
@@ -293,12 +299,12 @@ __device__ __forceinline__ void stage_y(const LorMesh& m, const Tab<P>& t, int64
 
 // Reference gradient along one z line (g0, g1) from A2: g[c][g2]; with the
 // reaction term also the values u[g2] = B_z BB (the mass basis operator).
-template <int P, bool MASS>
-__device__ __forceinline__ void line_gradient(const Tab<P>& t, const double* a2, int g01, double (*g)[Sz<P>::Q],
-                                              double* u) {
+template <int P, bool MASS, typename R>
+__device__ __forceinline__ void line_gradient(const Tab<P, R>& t, const R* a2, int g01, R (*g)[Sz<P>::Q],
+                                              R* u) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
-  double v[N], e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], vm;
+  R v[N], e_[Z::NH > 0 ? Z::NH : 1], o_[Z::NH > 0 ? Z::NH : 1], vm;
   // d/dxi0 = B_z BD
 #pragma unroll
   for (int k = 0; k < N; ++k) v[k] = a2[N * Q * Q + k * Q * Q + g01];
@@ -320,12 +326,12 @@ __device__ __forceinline__ void line_gradient(const Tab<P>& t, const double* a2,
 // Z' on one line: v[c][g2] -> T0 = B_z^T v0, T1 = B_z^T v1, T2 = d_z^T v2
 // (+ B_z^T u with the reaction term) stored over A2[c][k][g1][g0] (the line's
 // own entries).
-template <int P, bool MASS>
-__device__ __forceinline__ void line_transpose_z(const Tab<P>& t, double (*v)[Sz<P>::Q], const double* u, double* a2,
+template <int P, bool MASS, typename R>
+__device__ __forceinline__ void line_transpose_z(const Tab<P, R>& t, R (*v)[Sz<P>::Q], const R* u, R* a2,
                                                  int g01) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
-  double e_[Z::QH], o_[Z::QH], m_, y[N];
+  R e_[Z::QH], o_[Z::QH], m_, y[N];
   fold_q<P>(v[0], e_, o_, m_);
   bwd<P, true, false>(t, e_, o_, m_, e_, o_, m_, y);
 #pragma unroll
@@ -335,7 +341,7 @@ __device__ __forceinline__ void line_transpose_z(const Tab<P>& t, double (*v)[Sz
 #pragma unroll
   for (int k = 0; k < N; ++k) a2[N * Q * Q + k * Q * Q + g01] = y[k];
   if constexpr (MASS) {
-    double e2[Z::QH], o2[Z::QH], m2;
+    R e2[Z::QH], o2[Z::QH], m2;
     fold_q<P>(u, e_, o_, m_);
     fold_q<P>(v[2], e2, o2, m2);
     bwd<P, true, true>(t, e_, o_, m_, e2, o2, m2, y);
@@ -348,24 +354,24 @@ __device__ __forceinline__ void line_transpose_z(const Tab<P>& t, double (*v)[Sz
 }
 
 // u <- (beta w detJ) u at the q points of a z line (Mq[e][q^3])
-template <int P>
-__device__ __forceinline__ void line_apply_M(const double* __restrict__ Me, int g01, double* u) {
+template <int P, typename R>
+__device__ __forceinline__ void line_apply_M(const R* __restrict__ Me, int g01, R* u) {
   constexpr int Q = Sz<P>::Q, Q2 = Q * Q;
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) u[g2] *= Me[g01 + Q2 * g2];
 }
 
 // v <- D v at the q points of a z line (D[e][6][q^3], pt = g01 + q^2 g2)
-template <int P>
-__device__ __forceinline__ void line_apply_D(const double* __restrict__ De, int g01, double (*v)[Sz<P>::Q]) {
+template <int P, typename R>
+__device__ __forceinline__ void line_apply_D(const R* __restrict__ De, int g01, R (*v)[Sz<P>::Q]) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q;
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
     const int pt = g01 + Q2 * g2;
-    const double a = v[0][g2], b = v[1][g2], c = v[2][g2];
-    const double d00 = De[pt], d01 = De[Q3 + pt], d02 = De[2 * Q3 + pt];
-    const double d11 = De[3 * Q3 + pt], d12 = De[4 * Q3 + pt], d22 = De[5 * Q3 + pt];
+    const R a = v[0][g2], b = v[1][g2], c = v[2][g2];
+    const R d00 = De[pt], d01 = De[Q3 + pt], d02 = De[2 * Q3 + pt];
+    const R d11 = De[3 * Q3 + pt], d12 = De[4 * Q3 + pt], d22 = De[5 * Q3 + pt];
     v[0][g2] = d00 * a + d01 * b + d02 * c;
     v[1][g2] = d01 * a + d11 * b + d12 * c;
     v[2][g2] = d02 * a + d12 * b + d22 * c;
@@ -373,17 +379,17 @@ __device__ __forceinline__ void line_apply_D(const double* __restrict__ De, int 
 }
 
 // Y': A2 (T0, T1, T2) -> A1[c][k][j][g0]: U0 = B_y^T T0, U1 = d_y^T T1 + B_y^T T2.
-template <int P>
-__device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E, double* A) {
+template <int P, typename R>
+__device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E, R* A) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
   for (int w = threadIdx.x; w < E * N * Q; w += blockDim.x) {
     const int le = w / (N * Q), r = w % (N * Q);
     if (e_first + le >= m.nel) continue;
     const int g0 = r % Q, k = r / Q;
-    double* a1 = A + (size_t)le * Z::PER_ELEM;
-    const double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
-    double v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, y[N];
+    R* a1 = A + (size_t)le * Z::PER_ELEM;
+    const R* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+    R v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, y[N];
 #pragma unroll
     for (int g = 0; g < Q; ++g) v[g] = a2[(k * Q + g) * Q + g0];
     fold_q<P>(v, e1, o1, m1);
@@ -403,9 +409,9 @@ __device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P>& t, int
 }
 
 // X': A1 (U0, U1) -> y_line = d_x^T U0 + B_x^T U1, scatter-added into y.
-template <int P, bool GEN>
-__device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int64_t e_first, int E,
-                                          const double* A, double* __restrict__ y) {
+template <int P, bool GEN, typename R>
+__device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E,
+                                          const R* A, double* __restrict__ y) {
   using Z = Sz<P>;
   constexpr int N = Z::N, Q = Z::Q;
   for (int w = threadIdx.x; w < E * N * N; w += blockDim.x) {
@@ -413,8 +419,8 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int
     const int64_t e = e_first + le;
     if (e >= m.nel) continue;
     const int j = jk % N, k = jk / N;
-    const double* a1 = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
-    double v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, yl[N];
+    const R* a1 = A + (size_t)le * Z::PER_ELEM + (k * N + j) * Q;
+    R v[Q], e1[Z::QH], o1[Z::QH], m1, e2[Z::QH], o2[Z::QH], m2, yl[N];
 #pragma unroll
     for (int g = 0; g < Q; ++g) v[g] = a1[N * N * Q + g];  // U1 (B^T)
     fold_q<P>(v, e1, o1, m1);
@@ -427,7 +433,7 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t d = dm[i];
-        if (!m.ess[d]) atomicAdd(y + d, yl[i]);
+        if (!m.ess[d]) atomicAdd(y + d, (double)yl[i]);
       }
     } else {
       const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
@@ -437,21 +443,22 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P>& t, int
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t I = ex * P + i;
-        if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, yl[i]);
+        if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, (double)yl[i]);
       }
     }
   }
 }
 
-template <int P, bool MASS, bool GEN>
-__global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const double* __restrict__ Dq,
-                                                    const double* __restrict__ Mq, const double* __restrict__ x,
+template <int P, bool MASS, bool GEN, typename R>
+__global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const R* __restrict__ Dq,
+                                                    const R* __restrict__ Mq, const double* __restrict__ x,
                                                     double* __restrict__ y) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E;
-  extern __shared__ double smem[];
-  const Tab<P> t = load_tables<P>(T, smem);
-  double* A = smem + Z::TABLES;
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  R* sm = reinterpret_cast<R*>(apply_smem);
+  const Tab<P, R> t = load_tables<P>(T, sm);
+  R* A = sm + Z::TABLES;
   __syncthreads();
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
     stage_x<P, GEN>(m, t, e_first, E, x, A);
@@ -462,8 +469,8 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
       const int le = w / Q2, g01 = w % Q2;
       const int64_t e = e_first + le;
       if (e >= m.nel) continue;
-      double* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
-      double v[3][Q], u[MASS ? Q : 1];
+      R* a2 = A + (size_t)le * Z::PER_ELEM + Z::A1;
+      R v[3][Q], u[MASS ? Q : 1];
       line_gradient<P, MASS>(t, a2, g01, v, u);
       line_apply_D<P>(Dq + e * 6 * Q3, g01, v);
       if constexpr (MASS) line_apply_M<P>(Mq + e * Q3, g01, u);
@@ -492,8 +499,9 @@ __global__ void __launch_bounds__(Sz<P>::TBW, P <= 6 ? 2 : 1) k_apply_backward(L
                                                              double* __restrict__ gkappa) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::EB;
-  extern __shared__ double smem[];
-  const Tab<P> t = load_tables<P>(T, smem);
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  double* smem = reinterpret_cast<double*>(apply_smem);
+  const Tab<P, double> t = load_tables<P>(T, smem);
   double* A = smem + Z::TABLES;                    // gy: element slots 0..E-1
   double* AX = A + (size_t)E * Z::PER_ELEM;        // x:  element slots E..2E-1
   __syncthreads();
@@ -514,7 +522,7 @@ __global__ void __launch_bounds__(Sz<P>::TBW, P <= 6 ? 2 : 1) k_apply_backward(L
       line_gradient<P, MASS>(t, a2, g01, v, u);
       if (gkappa) {
         double gxl[3][Q];
-        line_gradient<P, false>(t, AX + (size_t)le * Z::PER_ELEM + Z::A1, g01, gxl, nullptr);
+        line_gradient<P, false, double>(t, AX + (size_t)le * Z::PER_ELEM + Z::A1, g01, gxl, nullptr);
 #pragma unroll
         for (int g2 = 0; g2 < Q; ++g2) {
           const int pt = g01 + Q2 * g2;
@@ -560,16 +568,16 @@ cudaError_t configure(K kernel, size_t bytes, unsigned* mask) {
   return cudaSuccess;
 }
 
-template <int P, bool MASS, bool GEN>
-cudaError_t apply_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
+template <int P, bool MASS, bool GEN, typename R>
+cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const double* x,
                     double* y, cudaStream_t s) {
   using Z = Sz<P>;
-  const size_t bytes = sizeof(double) * (Z::TABLES + (size_t)Z::E * Z::PER_ELEM);
+  const size_t bytes = sizeof(R) * (Z::TABLES + (size_t)Z::E * Z::PER_ELEM);
   static unsigned mask = 0;
-  cudaError_t err = configure(k_apply<P, MASS, GEN>, bytes, &mask);
+  cudaError_t err = configure(k_apply<P, MASS, GEN, R>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply<P, MASS, GEN><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
+  k_apply<P, MASS, GEN, R><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -587,12 +595,12 @@ cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, c
   return cudaGetLastError();
 }
 
-template <bool MASS, bool GEN>
-cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* x,
+template <bool MASS, bool GEN, typename R>
+cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const double* x,
                            double* y, cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: return apply_p<P, MASS, GEN>(m, T, Dq, Mq, x, y, s);
+  case P: return apply_p<P, MASS, GEN, R>(m, T, Dq, Mq, x, y, s);
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

@@ -6,7 +6,7 @@
 
 cudaError_t lor_apply_mass_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                     const double* x, double* y, cudaStream_t s) {
-  return apply_dispatch<true, false>(m, T, Dq, Mq, x, y, s);
+  return apply_dispatch<true, false, double>(m, T, Dq, Mq, x, y, s);
 }
 
 cudaError_t lor_backward_mass_dispatch(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,

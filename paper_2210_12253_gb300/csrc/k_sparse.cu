@@ -486,7 +486,7 @@ cudaError_t cheb_step(lor_ctx* c, const VT* vals, const VT* dinv, const double* 
 
 // ---------------------------------------------------------------- PCG vector kernels
 // Device scalars (slots of ctx->red after the partials).
-enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_COUNT = 5 };
+enum { S_PQ = 0, S_RR = 1, S_BB = 2, S_RZ0 = 3, S_RZ1 = 4, S_IR = 5, S_COUNT = 6 };
 
 __global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
                            double* __restrict__ r) {
@@ -750,10 +750,16 @@ cudaError_t pcg_update(lor_ctx* c, const VT* dinv, double* S, int cur, const dou
   return cudaGetLastError();
 }
 
-}  // namespace
+__global__ void k_add(int64_t n, double* __restrict__ x, const double* __restrict__ d) {
+  LOR_GRID_STRIDE(i, n) x[i] += d[i];
+}
 
-int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
-                 cudaStream_t s) {
+// PCG with x_0 = 0.  f32_apply: the operator is the FP32-arithmetic apply
+// (the inner solves of the refinement), else the FP64 one.  confirm: a
+// converged recurrence residual is checked against the true residual
+// b - A x (FP64 operator) before the solve counts as converged.
+int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, bool f32_apply, bool confirm,
+             int* iters, double* relres, cudaStream_t s) {
   const int64_t n = c->m.ndof;
   double* r = c->pcg_work;
   double* z = r + n;
@@ -791,7 +797,9 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
     dot(r, z, S + cur);
     k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
     while (it < maxit) {
-      err = lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
+      err = f32_apply
+                ? lor_launch_apply_f32_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s)
+                : lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
       if (err != cudaSuccess) return fail(c, err, "pcg apply");
       dot(p, q, S + S_PQ);
       const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
@@ -805,6 +813,10 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
       ++it;
       rel = sqrt(hs[0]) / nb;
       bool restarted = false;
+      if (rel <= rtol && !confirm) {
+        status = LOR_OK;
+        break;
+      }
       if (rel <= rtol) {
         // confirm on the true residual b - A x
         err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
@@ -840,6 +852,79 @@ int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit,
   if (iters) *iters = it;
   if (relres) *relres = rel;
   if (status == LOR_ENOCONV) c->err = "pcg: no convergence within maxit";
+  return status;
+}
+
+}  // namespace
+
+int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+                 cudaStream_t s) {
+  return pcg_core(c, b, x, rtol, maxit, false, true, iters, relres, s);
+}
+
+// Iterative refinement: the outer residual b - A x with the FP64 operator,
+// the corrections by PCG with the FP32 operator to inner_rtol.
+int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit,
+                    int* outer_iters, int* inner_iters, double* relres, cudaStream_t s) {
+  int rc = lor_ensure_f32_factors(c, s);
+  if (!rc) rc = lor_alloc_ir_work(c);
+  if (rc) return rc;
+  const int64_t n = c->m.ndof;
+  double* rr = c->ir_work;  // outer residual
+  double* dd = rr + n;      // correction (and A x scratch)
+  double* S = c->red + LOR_RED_BLOCKS;
+  double* hs = c->h_scalar;
+  const int g = grid_rows(n);
+  const int g_dot = pcg_grid(k_pcg_dot);
+  auto norm2 = [&](const double* a, double* out) -> cudaError_t {
+    k_pcg_dot<<<g_dot, kThreads, 0, s>>>(n, a, a, pcg_partials(c), c->red_count, S + S_IR); lor_count_launch();
+    cudaError_t e = cudaMemcpyAsync(hs, S + S_IR, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *out = hs[0];
+    return e;
+  };
+  cudaError_t err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(rr, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  double bb = 0.0;
+  if (err == cudaSuccess) err = norm2(b, &bb);
+  if (err != cudaSuccess) return fail(c, err, "pcg_ir");
+  const double nb = sqrt(bb);
+  int outer = 0, inner = 0, status = LOR_ENOCONV;
+  const char* why = "pcg_ir: no convergence within the limits";
+  double rel = nb == 0.0 ? 0.0 : 1.0, prev = HUGE_VAL;
+  while (true) {
+    if (rel <= rtol) {
+      status = LOR_OK;
+      break;
+    }
+    if (outer >= 64 || inner >= maxit) break;
+    if (!(rel < prev)) {
+      why = "pcg_ir: an outer step did not reduce the residual";
+      break;
+    }
+    prev = rel;
+    int it = 0;
+    double rin = 0.0;
+    rc = pcg_core(c, rr, dd, inner_rtol, maxit - inner, true, false, &it, &rin, s);
+    if (rc != LOR_OK && rc != LOR_ENOCONV) return rc;
+    inner += it;
+    ++outer;
+    k_add<<<g, kThreads, 0, s>>>(n, x, dd); lor_count_launch();
+    err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, dd, s);
+    if (err == cudaSuccess) {
+      k_residual<<<g, kThreads, 0, s>>>(n, b, dd, rr); lor_count_launch();
+      err = cudaGetLastError();
+    }
+    double r2 = 0.0;
+    if (err == cudaSuccess) err = norm2(rr, &r2);
+    if (err != cudaSuccess) return fail(c, err, "pcg_ir");
+    if (int trc = timed_out(c, "pcg_ir")) return trc;
+    rel = sqrt(r2) / nb;
+  }
+  if (outer_iters) *outer_iters = outer;
+  if (inner_iters) *inner_iters = inner;
+  if (relres) *relres = rel;
+  if (status == LOR_ENOCONV) c->err = why;
   return status;
 }
 

@@ -201,6 +201,9 @@ void free_all(lor_ctx* c) {
   cudaFree(c->ess);
   cudaFree(c->etail);
   cudaFree(c->ehead);
+  cudaFree(c->Dq32);
+  cudaFree(c->Mq32);
+  cudaFree(c->ir_work);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
 }
 
@@ -215,6 +218,21 @@ int read_status(lor_ctx* c, cudaStream_t s, int* flags) {
 }  // namespace
 
 void lor_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int lor_ensure_f32_factors(lor_ctx* c, cudaStream_t s) {
+  if (c->have_d32) return LOR_OK;
+  const int64_t nq = c->m.nel * (int64_t)c->T.q * c->T.q * c->T.q;
+  int rc = alloc(c, &c->Dq32, 6 * nq, "FP32 D");
+  if (!rc && c->have_beta) rc = alloc(c, &c->Mq32, nq, "FP32 beta w detJ");
+  if (rc) return rc;
+  cudaError_t e = lor_launch_to_f32(c->Dq, c->Dq32, 6 * nq, s);
+  if (e == cudaSuccess && c->have_beta) e = lor_launch_to_f32(c->Mq, c->Mq32, nq, s);
+  if (e != cudaSuccess) return cuda_err(c, e, "FP32 operator factors");
+  c->have_d32 = true;
+  return LOR_OK;
+}
+
+int lor_alloc_ir_work(lor_ctx* c) { return alloc(c, &c->ir_work, 2 * c->m.ndof, "refinement work"); }
 
 extern "C" {
 
@@ -396,11 +414,13 @@ int lor_set_coefficient(lor_ctx* c, const double* d_kappa, void* stream) {
   cudaError_t e = lor_launch_setup(c->m, c->T, d_kappa, c->kappa, c->Dq, c->d_status, S(stream));
   if (e != cudaSuccess) return cuda_err(c, e, "lor_set_coefficient");
   c->have_coeff = true;
+  c->have_d32 = false;
   return LOR_OK;
 }
 
 int lor_set_reaction(lor_ctx* c, const double* d_beta, void* stream) {
   if (!c) return LOR_EINVAL;
+  c->have_d32 = false;
   if (!d_beta) {
     c->have_beta = false;
     return LOR_OK;
@@ -539,6 +559,16 @@ int lor_apply(lor_ctx* c, const double* d_x, double* d_y, void* stream) {
   return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_apply");
 }
 
+int lor_apply_f32(lor_ctx* c, const double* d_x, double* d_y, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_x || !d_y || d_x == d_y) return set_err(c, LOR_EINVAL, "lor_apply_f32: x, y must be distinct device arrays");
+  if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_apply_f32: call lor_set_coefficient first");
+  int rc = lor_ensure_f32_factors(c, S(stream));
+  if (rc) return rc;
+  cudaError_t e = lor_launch_apply_f32(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, d_x, d_y, S(stream));
+  return e == cudaSuccess ? LOR_OK : cuda_err(c, e, "lor_apply_f32");
+}
+
 int lor_apply_backward(lor_ctx* c, const double* d_x, const double* d_gy, double* d_gx, double* d_gkappa,
                        void* stream) {
   if (!c) return LOR_EINVAL;
@@ -625,6 +655,17 @@ int lor_pcg_solve(lor_ctx* c, const double* d_b, double* d_x, double rtol, int m
   if (!(rtol > 0) || maxit < 0) return set_err(c, LOR_EINVAL, "lor_pcg_solve: need rtol > 0 and maxit >= 0");
   if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_pcg_solve: call lor_set_coefficient first");
   return lor_pcg_impl(c, d_b, d_x, rtol, maxit, iters, final_rel_residual, S(stream));
+}
+
+int lor_pcg_solve_ir(lor_ctx* c, const double* d_b, double* d_x, double rtol, double inner_rtol, int maxit,
+                     int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream) {
+  if (!c) return LOR_EINVAL;
+  if (!d_b || !d_x || d_b == d_x) return set_err(c, LOR_EINVAL, "lor_pcg_solve_ir: b, x must be distinct device arrays");
+  if (!(rtol > 0) || !(inner_rtol > 0) || !(inner_rtol < 1) || maxit < 0)
+    return set_err(c, LOR_EINVAL, "lor_pcg_solve_ir: need rtol > 0, 0 < inner_rtol < 1 and maxit >= 0");
+  if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_pcg_solve_ir: call lor_set_coefficient first");
+  return lor_pcg_ir_impl(c, d_b, d_x, rtol, inner_rtol, maxit, outer_iters, inner_iters, final_rel_residual,
+                         S(stream));
 }
 
 }  // extern "C"

@@ -86,6 +86,13 @@ struct lor_ctx {
   double* red = nullptr;       // reduction partials (LOR_RED_BLOCKS), 16 scalars, 2 x LOR_PCG_MAX_BLOCKS fused-PCG partials
   unsigned* red_count = nullptr;  // arrival counters of the last-block reductions (kept at 0 between uses)
   double* h_scalar = nullptr;  // pinned host scalars
+  // FP32 copies of the operator factors for the FP32 apply (made on first use
+  // after the coefficient or reaction term changes) and the refinement's
+  // outer residual and correction (2 N)
+  float* Dq32 = nullptr;
+  float* Mq32 = nullptr;
+  bool have_d32 = false;
+  double* ir_work = nullptr;
 };
 
 // Process-wide count of kernels launched by liblor (reported by lor_launch_count).
@@ -258,6 +265,14 @@ cudaError_t lor_launch_apply(const LorMesh& m, const LorTables& T, const double*
 // already hold x on essential DOFs and 0 elsewhere).
 cudaError_t lor_launch_apply_accumulate(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                         const double* x, double* y, cudaStream_t s);
+// The apply in FP32 arithmetic (FP32 tables and D / M factors, FP64 x and y
+// with FP64 atomics), with and without the output initialisation.
+cudaError_t lor_launch_apply_f32(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                 const double* x, double* y, cudaStream_t s);
+cudaError_t lor_launch_apply_f32_accumulate(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                            const double* x, double* y, cudaStream_t s);
+// b = (float) a, n elements
+cudaError_t lor_launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                       const double* kappa, const double* x, const double* gy, double* gx,
                                       double* gkappa, cudaStream_t s);
@@ -298,3 +313,10 @@ int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t 
 int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s);
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                  cudaStream_t s);
+// Mixed-precision iterative refinement around PCG (k_sparse.cu).
+int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit,
+                    int* outer_iters, int* inner_iters, double* relres, cudaStream_t s);
+// FP32 copies of D (and beta w detJ) for the FP32 apply, made when stale;
+// the refinement's work vectors (lor_abi.cu).
+int lor_ensure_f32_factors(lor_ctx* c, cudaStream_t s);
+int lor_alloc_ir_work(lor_ctx* c);

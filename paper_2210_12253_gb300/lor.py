@@ -22,7 +22,8 @@ EXPORTED = [
     "lor_build_pattern", "lor_assemble", "lor_apply", "lor_apply_backward", "lor_load_vector", "lor_spmv",
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
     "lor_precond_apply_noalloc", "lor_set_reaction", "lor_lor_mesh", "lor_assemble_unstructured",
-    "lor_discrete_gradient", "lor_vertex_coordinates", "lor_create_general",
+    "lor_discrete_gradient", "lor_vertex_coordinates", "lor_create_general", "lor_apply_f32",
+    "lor_pcg_solve_ir",
 ]
 
 
@@ -79,6 +80,10 @@ def load_library(path=LIB):
     L.lor_assemble.argtypes = [vp, vp, i, vp]
     L.lor_apply.restype = i
     L.lor_apply.argtypes = [vp, vp, vp, vp]
+    L.lor_apply_f32.restype = i
+    L.lor_apply_f32.argtypes = [vp, vp, vp, vp]
+    L.lor_pcg_solve_ir.restype = i
+    L.lor_pcg_solve_ir.argtypes = [vp, vp, vp, d, d, i, C.POINTER(i), C.POINTER(i), C.POINTER(d), vp]
     L.lor_apply_backward.restype = i
     L.lor_apply_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.lor_load_vector.restype = i
@@ -325,6 +330,14 @@ class LOR:
         self._call("lor_apply", _ptr(x), _ptr(y))
         return y
 
+    def apply_f32(self, x, out=None):
+        """y = A_p x with FP32 arithmetic inside the kernel (FP64 x and y); the
+        operator of the refinement's inner solves."""
+        _dev(x, torch.float64, self.ndof, "x")
+        y = self._new(self.ndof) if out is None else _dev(out, torch.float64, self.ndof, "out")
+        self._call("lor_apply_f32", _ptr(x), _ptr(y))
+        return y
+
     def apply_backward(self, x, gy, want_gx=True, want_gkappa=True, gx_out=None, gk_out=None):
         """(A_p gy, d(gy^T A_p x)/d kappa)."""
         _dev(gy, torch.float64, self.ndof, "gy")
@@ -390,6 +403,19 @@ class LOR:
         if rc != LOR_OK and (rc != LOR_ENOCONV or raise_on_noconv):
             raise LORError(rc, self._lib.lor_last_error(self._h).decode())
         return x, it.value, rel.value
+
+    def pcg_solve_ir(self, b, rtol=1e-8, inner_rtol=1e-4, maxit=20000, x=None, raise_on_noconv=True):
+        """Mixed-precision iterative refinement: FP64 outer residuals, inner PCG
+        with the FP32 operator to inner_rtol.  Returns (x, outer steps, inner
+        iterations, FP64 relative residual)."""
+        _dev(b, torch.float64, self.ndof, "b")
+        x = self._new(self.ndof) if x is None else _dev(x, torch.float64, self.ndof, "x")
+        no, ni, rel = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        rc = self._lib.lor_pcg_solve_ir(self._h, _ptr(b), _ptr(x), float(rtol), float(inner_rtol), int(maxit),
+                                        C.byref(no), C.byref(ni), C.byref(rel), _stream())
+        if rc != LOR_OK and (rc != LOR_ENOCONV or raise_on_noconv):
+            raise LORError(rc, self._lib.lor_last_error(self._h).decode())
+        return x, no.value, ni.value, rel.value
 
     # ------------------------------------------------------------------ autograd glue
     def ensure_coefficient(self, kappa):

@@ -7,14 +7,16 @@ E = elements, nq = E (p+2)^3 Gauss points, S = E p^3 LOR sub-hexes.
 
 Peaks: FP64 has no entry in MEASURED_PEAKS.json, so the FP64 peak is derived
 from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz =
-1.2586 TFLOP/s (an own DFMA loop measured 1.19 TFLOP/s, 1.90 DFMA/clk/SM).
+1.2586 TFLOP/s (an own DFMA loop measured 1.19 TFLOP/s, 1.90 DFMA/clk/SM);
+likewise FP32: 152 x 128 FFMA/clk/SM x 2 x 2.07 GHz = 80.55 TFLOP/s.
 The HBM peak is MEASURED_PEAKS.json's copy bandwidth.
 """
 import json
 import os
 
-SMS, DFMA_PER_CLK_SM, MAX_SM_GHZ = 152, 2, 2.07
+SMS, DFMA_PER_CLK_SM, FFMA_PER_CLK_SM, MAX_SM_GHZ = 152, 2, 128, 2.07
 FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * MAX_SM_GHZ / 1e3  # 1.2586
+FP32_PEAK_TFLOPS = SMS * FFMA_PER_CLK_SM * 2 * MAX_SM_GHZ / 1e3  # 80.55 (an own FFMA loop: 74.6)
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -89,6 +91,9 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
         return assemble_flops_per_subhex() * nsub, vbytes * nnz + 8 * nq
     if kind == "apply":
         return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
+    if kind == "apply_f32":
+        # the same contractions in FP32 (flops are FP32 here); D read as FP32
+        return apply_flops_per_element(p) * nel, 16 * ndof + 24 * nq
     if kind == "backward":
         return backward_flops_per_element(p) * nel, 24 * ndof + 64 * nq
     if kind == "reaction_setup":
