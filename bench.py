@@ -478,30 +478,71 @@ def run_refinement(args, op, b, res, u64):
     op.assemble_internal(torch.float32)
     op.precond_setup("cheb", torch.float32, degree=3, lambda_max=res["mixed"]["lambda_max"])
     xs = torch.empty_like(b)
-    op.pcg_solve_ir(b, 1e-8, args.ir_inner_rtol, 3, x=xs, raise_on_noconv=False)  # warm-up
+    for scheme in ("replace", "restart"):  # warm-up
+        op.pcg_solve_ir(b, 1e-8, args.ir_inner_rtol, 3, x=xs, raise_on_noconv=False, scheme=scheme)
     rows = []
-    for inner_rtol in [args.ir_inner_rtol] + [r for r in (args.ir_sweep or []) if r != args.ir_inner_rtol]:
+    runs = [("replace", args.ir_inner_rtol), ("restart", args.ir_inner_rtol)]
+    runs += [(sch, r) for r in (args.ir_sweep or []) if r != args.ir_inner_rtol for sch in ("replace", "restart")]
+    for scheme, inner_rtol in runs:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         e0.record()
-        u, outer, inner, rel = op.pcg_solve_ir(b, 1e-8, inner_rtol, args.pcg_maxit, x=xs,
+        u, outer, inner, rel = op.pcg_solve_ir(b, 1e-8, inner_rtol, args.pcg_maxit, x=xs, scheme=scheme,
                                                raise_on_noconv=args.pcg_maxit >= 20000)
         e1.record()
         torch.cuda.synchronize()
         solve_s = e0.elapsed_time(e1) / 1e3
-        rows.append({"inner_rtol": inner_rtol, "solve_s": solve_s, "wall_s": time.perf_counter() - t0,
+        rows.append({"scheme": scheme, "inner_rtol": inner_rtol, "solve_s": solve_s,
+                     "wall_s": time.perf_counter() - t0,
                      "outer_iterations": outer, "inner_iterations": inner, "final_rel_residual": rel,
                      "s_per_inner_iteration": solve_s / max(inner, 1),
                      "speedup_vs_fp64": res["fp64"]["solve_s"] / solve_s,
                      "speedup_vs_mixed": res["mixed"]["solve_s"] / solve_s,
                      "solution_vs_fp64_max_rel_diff": ((u - u64).abs().max() / u64.abs().max()).item()})
     out["mixed_ir"] = rows[0]
-    out["mixed_ir"]["scheme"] = ("iterative refinement: r = b - A_p x with the FP64 operator each outer step; "
-                                 "correction by PCG (FP32 LOR Chebyshev deg 3, FP64 dots/recurrences) with the "
-                                 "FP32-arithmetic operator to inner_rtol; stop on the FP64 residual")
-    if len(rows) > 1:
+    out["mixed_ir"]["description"] = (
+        "mixed-precision refinement, residual-replacement scheme: one PCG (FP32 LOR Chebyshev deg 3, FP64 "
+        "dots/recurrences) on the FP32-arithmetic operator; after each inner_rtol reduction of its recurrence "
+        "residual the FP64 residual b - A_p x replaces it; stop on the FP64 residual")
+    out["mixed_ir_restart"] = rows[1]
+    if len(rows) > 2:
         out["mixed_ir_inner_rtol_sweep"] = rows
+    return out
+
+
+def run_apply_kernels(args, dev):
+    """FP64 and FP32 high-order applies on an NEX^3 unit-cube mesh of degree
+    P (jitter 10%, lognormal kappa, seed 2): two untimed applies each, then 10
+    timed back-to-back (CUDA events)."""
+    import torch
+
+    from paper_2210_12253_gb300 import LOR
+    from paper_2210_12253_gb300.inputs import make_problem
+    from paper_2210_12253_gb300.perfmodel import hbm_peak_gbs, kernel_work
+
+    nex, p = args.apply_kernels
+    prob = make_problem("apply", nex, nex, nex, p, seed=2, jitter=0.1, kappa="lognormal", rhs="normal")
+    op = LOR(p, nex, nex, nex, torch.tensor(prob.vertices, device=dev))
+    op.set_coefficient(torch.tensor(prob.kappa.reshape(-1), device=dev))
+    x = torch.randn(op.ndof, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    hbm, _ = hbm_peak_gbs()
+    out = {"workload": "%d^3 elements, p=%d, %d DOFs" % (nex, p, op.ndof)}
+    for label, fn, kind in (("apply_f32", op.apply_f32, "apply_f32"), ("apply_f64", op.apply, "apply")):
+        for _ in range(2):
+            fn(x, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            fn(x, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        _, byts = kernel_work(kind, p, op.ndof, op.nel, op.nnz)
+        out[label] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm}
+    op.close()
     return out
 
 
@@ -1042,6 +1083,9 @@ def main(argv=None):
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--sweep-workloads", nargs="*", default=None,
                     help="run the sweep's kernel set on these named workloads instead (e.g. c4_24x24x24_p5)")
+    ap.add_argument("--apply-kernels", type=int, nargs=2, default=None, metavar=("NEX", "P"),
+                    help="time only the FP64 and FP32 high-order applies on an NEX^3 cube of degree P "
+                         "(a small case for kernel profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -1062,6 +1106,13 @@ def main(argv=None):
         build()
         torch.cuda.set_device(local_rank)
         run_sweep(args, torch.device("cuda", local_rank))
+        return 0
+    if args.apply_kernels:
+        import torch
+        from paper_2210_12253_gb300.build import build
+        build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(run_apply_kernels(args, torch.device("cuda", local_rank))))
         return 0
     if args.pcg_only:
         import torch

@@ -76,6 +76,8 @@ enum lor_status {
 enum lor_dtype { LOR_F64 = 0, LOR_F32 = 1 };
 
 enum lor_precond { LOR_PRECOND_NONE = 0, LOR_PRECOND_JACOBI = 1, LOR_PRECOND_CHEB = 2 };
+/* Schemes of lor_pcg_solve_ir. */
+enum lor_ir_scheme { LOR_IR_RESTART = 0, LOR_IR_REPLACE = 1 };
 
 typedef struct lor_ctx lor_ctx;
 
@@ -320,23 +322,30 @@ int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int
                   double* final_rel_residual, void* stream);
 
 /* Mixed-precision iterative refinement (Wilkinson; Moler 1967) for the same
- * system, with x_0 = 0:
- *   repeat: r = b - A_p x            (FP64 operator, FP64 vectors)
- *           stop if |r|/|b| <= rtol
- *           solve A_p d = r by PCG from d_0 = 0 until |r_k| <= inner_rtol |r|,
- *             with the FP32 operator of lor_apply_f32 and the preconditioner
- *             of lor_precond_setup (dots and recurrences FP64)
- *           x += d
- * so the stopping residual is always the FP64 one, while the inner
+ * system, x_0 = 0, in one of two schemes:
+ *   LOR_IR_RESTART:
+ *     repeat: r = b - A_p x          (FP64 operator, FP64 vectors)
+ *             stop if |r|/|b| <= rtol
+ *             solve A_p d = r by PCG from d_0 = 0 until |r_k| <= inner_rtol |r|,
+ *               with the FP32 operator of lor_apply_f32 and the preconditioner
+ *               of lor_precond_setup (dots and recurrences FP64)
+ *             x += d
+ *   LOR_IR_REPLACE (residual replacement, van der Vorst and Ye 2000): one PCG
+ *     on the FP32 operator; whenever its recurrence residual has fallen by
+ *     inner_rtol since the last outer step, the FP64 residual b - A_p x is
+ *     formed, the solve stops if it meets rtol, and otherwise it replaces the
+ *     recurrence residual (the search direction is kept).
+ * Either way the stopping residual is always the FP64 one, while the inner
  * iterations run the FP32 operator (on this GPU the FP32 pipe is about 60x
  * the FP64 one).  maxit bounds the inner iterations over all outer steps;
- * at most 64 outer steps.  *outer_iters, *inner_iters, *final_rel_residual
- * (host, may be NULL) receive the counts and the final FP64 relative
- * residual.  LOR_ENOCONV when maxit or the outer limit is reached first, or
- * when an outer step does not reduce the residual.  Synchronises the stream.
+ * LOR_IR_RESTART takes at most 64 outer steps.  *outer_iters (FP64
+ * residuals formed), *inner_iters, *final_rel_residual (host, may be NULL)
+ * receive the counts and the final FP64 relative residual.  LOR_ENOCONV when
+ * maxit or the outer limit is reached first, or when an outer step does not
+ * lower the FP64 residual.  Synchronises the stream.
  * The paper has no counterpart: it solves with PCG in FP64. */
 int lor_pcg_solve_ir(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, double inner_rtol, int maxit,
-                     int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream);
+                     int scheme, int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream);
 
 #ifdef __cplusplus
 }

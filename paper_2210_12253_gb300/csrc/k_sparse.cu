@@ -754,12 +754,17 @@ __global__ void k_add(int64_t n, double* __restrict__ x, const double* __restric
   LOR_GRID_STRIDE(i, n) x[i] += d[i];
 }
 
-// PCG with x_0 = 0.  f32_apply: the operator is the FP32-arithmetic apply
-// (the inner solves of the refinement), else the FP64 one.  confirm: a
-// converged recurrence residual is checked against the true residual
-// b - A x (FP64 operator) before the solve counts as converged.
+// PCG with x_0 = 0.  f32_apply: the operator is the FP32-arithmetic apply,
+// else the FP64 one.  confirm: a converged recurrence residual is checked
+// against the true residual b - A x (FP64 operator) before the solve counts
+// as converged; if it fails, the iteration continues from the true residual
+// (keeping the search direction).  replace > 0 (with confirm): the true
+// residual is also formed, and substituted, whenever the recurrence residual
+// has fallen by the factor `replace` since the last substitution (residual
+// replacement); *replacements counts them.  A replacement that does not
+// lower the true residual ends the solve (LOR_ENOCONV).
 int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, bool f32_apply, bool confirm,
-             int* iters, double* relres, cudaStream_t s) {
+             double replace, int* iters, double* relres, int* replacements, cudaStream_t s) {
   const int64_t n = c->m.ndof;
   double* r = c->pcg_work;
   double* z = r + n;
@@ -785,9 +790,10 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return fail(c, err, "pcg");
   const double nb = sqrt(hs[0]);
-  int it = 0;
-  double rel = 0.0;
+  int it = 0, nrep = 0;
+  double rel = 0.0, last_true = 1.0;
   int status = LOR_ENOCONV;
+  const char* why = "pcg: no convergence within maxit";
   if (nb == 0.0) {
     status = LOR_OK;
   } else {
@@ -813,11 +819,12 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
       ++it;
       rel = sqrt(hs[0]) / nb;
       bool restarted = false;
-      if (rel <= rtol && !confirm) {
+      const double trigger = replace > 0.0 ? fmax(rtol, replace * last_true) : rtol;
+      if (rel <= trigger && !confirm) {
         status = LOR_OK;
         break;
       }
-      if (rel <= rtol) {
+      if (rel <= trigger) {
         // confirm on the true residual b - A x
         err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
         if (err == cudaSuccess) {
@@ -831,6 +838,14 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
         if (rel <= rtol) {
           status = LOR_OK;
           break;
+        }
+        if (replace > 0.0) {
+          if (!(rel < last_true)) {
+            why = "pcg: a residual replacement did not lower the true residual";
+            break;
+          }
+          last_true = rel;
+          ++nrep;
         }
         // continue from the true residual: precondition it afresh
         rc = lor_precond_apply_impl(c, r, z, s);
@@ -851,7 +866,8 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   }
   if (iters) *iters = it;
   if (relres) *relres = rel;
-  if (status == LOR_ENOCONV) c->err = "pcg: no convergence within maxit";
+  if (replacements) *replacements = nrep;
+  if (status == LOR_ENOCONV) c->err = why;
   return status;
 }
 
@@ -859,15 +875,27 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
 
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                  cudaStream_t s) {
-  return pcg_core(c, b, x, rtol, maxit, false, true, iters, relres, s);
+  return pcg_core(c, b, x, rtol, maxit, false, true, 0.0, iters, relres, nullptr, s);
 }
 
 // Iterative refinement: the outer residual b - A x with the FP64 operator,
 // the corrections by PCG with the FP32 operator to inner_rtol.
-int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit,
+int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit, int scheme,
                     int* outer_iters, int* inner_iters, double* relres, cudaStream_t s) {
   int rc = lor_ensure_f32_factors(c, s);
-  if (!rc) rc = lor_alloc_ir_work(c);
+  if (rc) return rc;
+  if (scheme == LOR_IR_REPLACE) {
+    // one PCG on the FP32 operator; the FP64 residual replaces the recurrence
+    // residual each time the latter has fallen by inner_rtol
+    int it = 0, nrep = 0;
+    double rel = 0.0;
+    rc = pcg_core(c, b, x, rtol, maxit, true, true, inner_rtol, &it, &rel, &nrep, s);
+    if (outer_iters) *outer_iters = it > 0 ? nrep + 1 : 0;
+    if (inner_iters) *inner_iters = it;
+    if (relres) *relres = rel;
+    return rc;
+  }
+  rc = lor_alloc_ir_work(c);
   if (rc) return rc;
   const int64_t n = c->m.ndof;
   double* rr = c->ir_work;  // outer residual
@@ -905,7 +933,7 @@ int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double 
     prev = rel;
     int it = 0;
     double rin = 0.0;
-    rc = pcg_core(c, rr, dd, inner_rtol, maxit - inner, true, false, &it, &rin, s);
+    rc = pcg_core(c, rr, dd, inner_rtol, maxit - inner, true, false, 0.0, &it, &rin, nullptr, s);
     if (rc != LOR_OK && rc != LOR_ENOCONV) return rc;
     inner += it;
     ++outer;

@@ -658,13 +658,15 @@ int lor_pcg_solve(lor_ctx* c, const double* d_b, double* d_x, double rtol, int m
 }
 
 int lor_pcg_solve_ir(lor_ctx* c, const double* d_b, double* d_x, double rtol, double inner_rtol, int maxit,
-                     int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream) {
+                     int scheme, int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream) {
   if (!c) return LOR_EINVAL;
   if (!d_b || !d_x || d_b == d_x) return set_err(c, LOR_EINVAL, "lor_pcg_solve_ir: b, x must be distinct device arrays");
   if (!(rtol > 0) || !(inner_rtol > 0) || !(inner_rtol < 1) || maxit < 0)
     return set_err(c, LOR_EINVAL, "lor_pcg_solve_ir: need rtol > 0, 0 < inner_rtol < 1 and maxit >= 0");
+  if (scheme != LOR_IR_RESTART && scheme != LOR_IR_REPLACE)
+    return set_err(c, LOR_EINVAL, "lor_pcg_solve_ir: unknown scheme");
   if (!c->have_coeff) return set_err(c, LOR_ESTATE, "lor_pcg_solve_ir: call lor_set_coefficient first");
-  return lor_pcg_ir_impl(c, d_b, d_x, rtol, inner_rtol, maxit, outer_iters, inner_iters, final_rel_residual,
+  return lor_pcg_ir_impl(c, d_b, d_x, rtol, inner_rtol, maxit, scheme, outer_iters, inner_iters, final_rel_residual,
                          S(stream));
 }
 

@@ -314,7 +314,7 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                  cudaStream_t s);
 // Mixed-precision iterative refinement around PCG (k_sparse.cu).
-int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit,
+int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double inner_rtol, int maxit, int scheme,
                     int* outer_iters, int* inner_iters, double* relres, cudaStream_t s);
 // FP32 copies of D (and beta w detJ) for the FP32 apply, made when stale;
 // the refinement's work vectors (lor_abi.cu).

@@ -15,6 +15,7 @@ from .build import LIB
 LOR_OK, LOR_EINVAL, LOR_EGEOM, LOR_ENOMEM, LOR_ECUDA, LOR_ENOCONV, LOR_ETIMEOUT, LOR_ESTATE = 0, 1, 2, 3, 4, 5, 6, 7
 LOR_F64, LOR_F32 = 0, 1
 LOR_PRECOND_NONE, LOR_PRECOND_JACOBI, LOR_PRECOND_CHEB = 0, 1, 2
+LOR_IR_RESTART, LOR_IR_REPLACE = 0, 1
 LOR_MAX_P = 10
 
 EXPORTED = [
@@ -83,7 +84,7 @@ def load_library(path=LIB):
     L.lor_apply_f32.restype = i
     L.lor_apply_f32.argtypes = [vp, vp, vp, vp]
     L.lor_pcg_solve_ir.restype = i
-    L.lor_pcg_solve_ir.argtypes = [vp, vp, vp, d, d, i, C.POINTER(i), C.POINTER(i), C.POINTER(d), vp]
+    L.lor_pcg_solve_ir.argtypes = [vp, vp, vp, d, d, i, i, C.POINTER(i), C.POINTER(i), C.POINTER(d), vp]
     L.lor_apply_backward.restype = i
     L.lor_apply_backward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.lor_load_vector.restype = i
@@ -404,14 +405,18 @@ class LOR:
             raise LORError(rc, self._lib.lor_last_error(self._h).decode())
         return x, it.value, rel.value
 
-    def pcg_solve_ir(self, b, rtol=1e-8, inner_rtol=1e-4, maxit=20000, x=None, raise_on_noconv=True):
+    def pcg_solve_ir(self, b, rtol=1e-8, inner_rtol=1e-4, maxit=20000, x=None, raise_on_noconv=True,
+                     scheme="replace"):
         """Mixed-precision iterative refinement: FP64 outer residuals, inner PCG
-        with the FP32 operator to inner_rtol.  Returns (x, outer steps, inner
-        iterations, FP64 relative residual)."""
+        iterations with the FP32 operator; scheme "restart" (a fresh PCG per
+        correction, to inner_rtol) or "replace" (one PCG whose residual is
+        replaced by the FP64 one after each inner_rtol reduction).  Returns
+        (x, outer steps, inner iterations, FP64 relative residual)."""
         _dev(b, torch.float64, self.ndof, "b")
         x = self._new(self.ndof) if x is None else _dev(x, torch.float64, self.ndof, "x")
+        code = {"restart": LOR_IR_RESTART, "replace": LOR_IR_REPLACE}[scheme]
         no, ni, rel = C.c_int(0), C.c_int(0), C.c_double(0.0)
-        rc = self._lib.lor_pcg_solve_ir(self._h, _ptr(b), _ptr(x), float(rtol), float(inner_rtol), int(maxit),
+        rc = self._lib.lor_pcg_solve_ir(self._h, _ptr(b), _ptr(x), float(rtol), float(inner_rtol), int(maxit), code,
                                         C.byref(no), C.byref(ni), C.byref(rel), _stream())
         if rc != LOR_OK and (rc != LOR_ENOCONV or raise_on_noconv):
             raise LORError(rc, self._lib.lor_last_error(self._h).decode())

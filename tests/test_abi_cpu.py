@@ -59,3 +59,17 @@ def test_product_path_needs_cuda_tensors(libpath):
     from paper_2210_12253_gb300 import LOR
     with pytest.raises(TypeError):
         LOR(2, 1, 1, 1, torch.zeros(8 * 3, dtype=torch.float64))
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator and status code the header defines has the same value
+    in the binding."""
+    import re
+    from paper_2210_12253_gb300 import lor as B
+    text = open(os.path.join(ROOT, "include", "lor.h")).read()
+    pairs = re.findall(r"\b(LOR_[A-Z0-9_]+)\s*=\s*(\d+)", text)
+    pairs += re.findall(r"#define\s+(LOR_[A-Z0-9_]+)\s+(\d+)\b", text)
+    assert len(pairs) >= 15
+    for name, value in pairs:
+        assert hasattr(B, name), name
+        assert getattr(B, name) == int(value), name

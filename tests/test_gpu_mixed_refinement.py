@@ -97,8 +97,9 @@ def test_apply_f32_general_mesh(dims, p):
     op.close()
 
 
+@pytest.mark.parametrize("scheme", ["restart", "replace"])
 @pytest.mark.parametrize("inner_rtol", [1e-2, 1e-4])
-def test_refinement_matches_oracle(inner_rtol):
+def test_refinement_matches_oracle(inner_rtol, scheme):
     dims, p = (3, 3, 4), 3
     prob, mesh, op = setup(dims, p)
     op.build_pattern_internal()
@@ -108,7 +109,7 @@ def test_refinement_matches_oracle(inner_rtol):
     lam = oracle.power_lambda_max(*csr, v0, 20)
     op.precond_setup("cheb", torch.float32, degree=3, lambda_max=lam)
     b = t(prob.rhs)
-    x, outer, inner, rel = op.pcg_solve_ir(b, 1e-10, inner_rtol, 4000)
+    x, outer, inner, rel = op.pcg_solve_ir(b, 1e-10, inner_rtol, 4000, scheme=scheme)
     # the reported residual is the FP64 one
     r = b - op.apply(x)
     true_rel = (torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)).item()
@@ -131,12 +132,13 @@ def test_refinement_general_mesh_with_reaction():
     op.precond_setup("cheb", torch.float32, degree=3, power_iters=20)
     bn = np.empty(op.ndof)
     bn[perm] = prob.rhs
-    x, outer, inner, rel = op.pcg_solve_ir(t(bn), 1e-10, 1e-4, 4000)
-    assert rel <= 1e-10
-    # against the oracle's FP64 operator: residual of the permuted solution
-    xs = x.cpu().numpy()[perm]
-    r = prob.rhs - oracle.ho_apply(mesh, p, p + 2, prob.kappa, xs, beta=beta)
-    assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(prob.rhs)
+    for scheme in ("restart", "replace"):
+        x, outer, inner, rel = op.pcg_solve_ir(t(bn), 1e-10, 1e-4, 4000, scheme=scheme)
+        assert rel <= 1e-10
+        # against the oracle's FP64 operator: residual of the permuted solution
+        xs = x.cpu().numpy()[perm]
+        r = prob.rhs - oracle.ho_apply(mesh, p, p + 2, prob.kappa, xs, beta=beta)
+        assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(prob.rhs)
     op.close()
 
 
@@ -145,11 +147,18 @@ def test_refinement_limits_and_errors():
     prob, mesh, op = setup((2, 2, 2), 3)
     op.precond_setup("none")
     b = t(prob.rhs)
-    x, outer, inner, rel = op.pcg_solve_ir(b, 1e-14, 1e-4, 3, raise_on_noconv=False)
-    assert inner == 3 and rel > 1e-14
-    with pytest.raises(LORError) as ei:
-        op.pcg_solve_ir(b, 1e-14, 1e-4, 3)
-    assert ei.value.code == 5
+    for scheme in ("restart", "replace"):
+        x, outer, inner, rel = op.pcg_solve_ir(b, 1e-14, 1e-4, 3, raise_on_noconv=False, scheme=scheme)
+        assert inner == 3 and rel > 1e-14
+        with pytest.raises(LORError) as ei:
+            op.pcg_solve_ir(b, 1e-14, 1e-4, 3, scheme=scheme)
+        assert ei.value.code == 5
+    import ctypes
+    no, ni, rel = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = op._lib.lor_pcg_solve_ir(op._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1e-8, 1e-4,
+                                  100, 7, ctypes.byref(no), ctypes.byref(ni), ctypes.byref(rel),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 1
     with pytest.raises(LORError) as ei:
         op.pcg_solve_ir(b, 1e-8, 1.5, 100)
     assert ei.value.code == 1
