@@ -420,13 +420,16 @@ def run_pcg(args, dev, rank):
         res["degree_sweep"] = []
         for k in args.pcg_degrees:
             row = {"degree": k}
-            for label, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+            for label, dt in (("mixed", torch.float32), ("mixed_ir", torch.float32), ("fp64", torch.float64)):
                 op.assemble_internal(dt)
                 op.precond_setup("cheb", dt, degree=k, lambda_max=lam)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                _, it, _ = op.pcg_solve(b, 1e-8, 20000)
+                if label == "mixed_ir":
+                    _, _, it, _ = op.pcg_solve_ir(b, 1e-8, args.ir_inner_rtol, 20000)
+                else:
+                    _, it, _ = op.pcg_solve(b, 1e-8, 20000)
                 e1.record()
                 torch.cuda.synchronize()
                 row[label] = {"solve_s": e0.elapsed_time(e1) / 1e3, "iterations": it}

@@ -718,6 +718,20 @@ __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, cons
   R* A = sm + L::TABLES;
   __syncthreads();
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
+    if constexpr (Lay<P, R>::F32) {
+      // L2 prefetch of the batch's D (and M), read by the z stage two barriers
+      // later: its latency then overlaps the x and y stages
+      const int64_t ne = m.nel - e_first < E ? m.nel - e_first : E;
+      const char* d0 = reinterpret_cast<const char*>(Dq + e_first * 6 * Q3);
+      const int64_t nb = ne * 6 * Q3 * (int64_t)sizeof(R);
+      for (int64_t off = (int64_t)threadIdx.x * 128; off < nb; off += (int64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(d0 + off));
+      if constexpr (MASS) {
+        const char* m0 = reinterpret_cast<const char*>(Mq + e_first * Q3);
+        for (int64_t off = (int64_t)threadIdx.x * 128; off < nb / 6; off += (int64_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(m0 + off));
+      }
+    }
     stage_x<P, GEN>(m, t, e_first, E, x, A);
     __syncthreads();
     stage_y<P>(m, t, e_first, E, A);

@@ -5,7 +5,8 @@
   high-order apply and backward, SpMV and the Chebyshev-Jacobi smoother
   against the oracle's own assembled CSR.
 * 32^3 elements, p = 6 (7,189,057 DOFs; the PCG workload): sampled LOR rows,
-  the full apply, and PCG to 1e-8 in FP64 and mixed precision whose true
+  the full apply (FP64 and FP32 arithmetic), and PCG to 1e-8 in FP64, mixed
+  precision and the mixed-precision refinement (both schemes), whose true
   residual is re-checked with the oracle's operator.
 * 24^3 elements, p = 5 (1,771,561 DOFs; the gradient workload): dJ/dtheta by
   the adjoint against fourth-order central differences on 16 random
@@ -109,6 +110,8 @@ def test_pcg_workload_32x32x32_p6():
     y = op.apply(t(x)).cpu().numpy()
     ry = oracle.ho_apply(mesh, p, q, prob.kappa, x)
     assert np.abs(y - ry).max() <= 1e-12 * np.abs(ry).max()
+    y32 = op.apply_f32(t(x)).cpu().numpy()
+    assert np.abs(y32 - ry).max() <= 2e-5 * np.abs(ry).max()
     b = t(prob.rhs)
     v0 = t(power_start_vector(op.ndof))
     op.build_pattern_internal()
@@ -122,6 +125,12 @@ def test_pcg_workload_32x32x32_p6():
         assert np.linalg.norm(r) <= 1.000001e-8 * np.linalg.norm(prob.rhs), dt
     # mixed precision reaches the same tolerance with a similar iteration count
     assert its[torch.float32] <= 1.25 * its[torch.float64]
+    # the refinement (FP32 operator in the iterations), FP32 smoother as above
+    for scheme in ("replace", "restart"):
+        u, outer, inner, rel = op.pcg_solve_ir(b, 1e-8, 1e-4, 20000, scheme=scheme)
+        r = prob.rhs - oracle.ho_apply(mesh, p, q, prob.kappa, u.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.000001e-8 * np.linalg.norm(prob.rhs), scheme
+        assert inner <= 1.5 * its[torch.float32], scheme
     op.close()
 
 
