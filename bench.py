@@ -142,9 +142,10 @@ def kernel_roofline(name, ms, work, hbm_peak, hbm_src):
     return out
 
 
-def read_traffic(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary of `kernel`, or None
-    when the summary is missing or was taken on a different source file."""
+def read_traffic(kernel, key="traffic_bytes_per_launch"):
+    """Per-launch DRAM bytes (or another `key: value` figure) from the committed
+    ncu summary of `kernel`, or None when the summary is missing or was taken
+    on a different source file."""
     import hashlib
     import re
     prof = os.path.join(ROOT, "profiles")
@@ -154,7 +155,7 @@ def read_traffic(kernel):
         if not fn.startswith(kernel) or not fn.endswith(".md"):
             continue
         txt = open(os.path.join(prof, fn)).read()
-        m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        m = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", txt)
         srcs = re.findall(r"source_sha256:\s*([0-9a-f]+)\s+(\S+)", txt)
         if not m or not srcs:
             continue
@@ -321,6 +322,7 @@ def run_gpu(args, rank, world, local_rank):
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64; no FP64 entry in "
                                "MEASURED_PEAKS.json)",
                 "traffic": traffic,
+                "fp64_pipe_active": read_traffic("k_" + dominant, "fp64_pipe_active_fraction"),
                 "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
                         "frac": dk["frac_hbm"]}}
     clk = clocks.stop()
