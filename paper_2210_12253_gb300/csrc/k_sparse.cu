@@ -292,6 +292,32 @@ enum StencilMode {
   ST_CHEB_DOT = 3    // the same step writing y (FP64) and finishing r.y into *out
 };
 
+// What each mode does with row i's product s = (A x)_i.
+template <typename VT, typename XT, int MODE>
+__device__ __forceinline__ void stencil_epilogue(int64_t i, VT s, const VT* __restrict__ dinv,
+                                                 const XT* __restrict__ x, const double* __restrict__ r,
+                                                 VT* __restrict__ d, VT c1, VT c2, VT* __restrict__ zout,
+                                                 double* __restrict__ y, double& acc) {
+  if constexpr (MODE == ST_SPMV) {
+    y[i] = (double)s;
+  } else if constexpr (MODE == ST_DINV_SPMV) {
+    y[i] = (double)(dinv[i] * s);
+  } else {
+    const double ri = r[i];
+    const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
+    const VT zn = (VT)x[i] + dn;
+    if constexpr (MODE == ST_CHEB_DOT) {
+      y[i] = (double)zn;
+      acc += ri * (double)zn;
+    } else if (y) {
+      y[i] = (double)zn;
+    } else {
+      d[i] = dn;
+      zout[i] = zn;
+    }
+  }
+}
+
 template <typename VT, typename XT, int MODE>
 __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __restrict__ vals,
                                                       const VT* __restrict__ dinv, const XT* __restrict__ x,
@@ -331,24 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     if (i < m.ndof) {
       const StencilRow row = stencil_row(m, i);
       const VT s = stencil_product<VT, XT>(m, row, sv + (row.start - base[b]), x);
-      if constexpr (MODE == ST_SPMV) {
-        y[i] = (double)s;
-      } else if constexpr (MODE == ST_DINV_SPMV) {
-        y[i] = (double)(dinv[i] * s);
-      } else {
-        const double ri = r[i];
-        const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
-        const VT zn = (VT)x[i] + dn;
-        if constexpr (MODE == ST_CHEB_DOT) {
-          y[i] = (double)zn;
-          acc += ri * (double)zn;
-        } else if (y) {
-          y[i] = (double)zn;
-        } else {
-          d[i] = dn;
-          zout[i] = zn;
-        }
-      }
+      stencil_epilogue<VT, XT, MODE>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
     }
     __syncthreads();  // every read of this buffer is done before it is refilled
   }
@@ -390,24 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restric
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (!valid || lane != 0) continue;
-    if constexpr (MODE == ST_SPMV) {
-      y[i] = (double)s;
-    } else if constexpr (MODE == ST_DINV_SPMV) {
-      y[i] = (double)(dinv[i] * s);
-    } else {
-      const double ri = r[i];
-      const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
-      const VT zn = (VT)x[i] + dn;
-      if constexpr (MODE == ST_CHEB_DOT) {
-        y[i] = (double)zn;
-        acc += ri * (double)zn;
-      } else if (y) {
-        y[i] = (double)zn;
-      } else {
-        d[i] = dn;
-        zout[i] = zn;
-      }
-    }
+    stencil_epilogue<VT, XT, MODE>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
   }
   if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
 }
