@@ -913,14 +913,16 @@ def run_sweep(args, dev):
     JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
     (the kappa-gradient kernel), one FP32 Chebyshev-Jacobi degree-3
     application), CUDA-event timed, median of `--sweep-reps` after one
-    warm-up, L2 flushed before each launch; then the time per PCG iteration
-    (30 iterations) in mixed precision and in FP64."""
+    warm-up, L2 flushed before each launch, and the FP32-arithmetic apply;
+    then the time per PCG iteration (30 iterations, the faster of two runs)
+    in mixed precision, in FP64 and in the refinement solver's inner
+    iterations (FP32 operator)."""
     import numpy as np
     import torch
 
     from paper_2210_12253_gb300 import LOR
     from paper_2210_12253_gb300.inputs import workload
-    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
+    from paper_2210_12253_gb300.perfmodel import FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
 
     hbm_peak, _ = hbm_peak_gbs()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -944,6 +946,7 @@ def run_sweep(args, dev):
             "assemble_f64": lambda: op.assemble_internal(torch.float64),
             "assemble_f32": lambda: op.assemble_internal(torch.float32),
             "apply": lambda: op.apply(x, out=y),
+            "apply_f32": lambda: op.apply_f32(x, out=y),
             "backward": lambda: op.apply_backward(x, x, gx_out=gx, gk_out=gk),
             "precond_f32": lambda: op.precond_apply(x, out=z),
         }
@@ -966,19 +969,31 @@ def run_sweep(args, dev):
             res[name] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
                          "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+            if name == "apply_f32":  # FP32 flops against the FP32 peak
+                del res[name]["frac_fp64"]
+                res[name]["frac_fp32"] = flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS
         # PCG per iteration (30 iterations from x0 = 0, fixed count), mixed
         # precision and FP64, with the same lambda_max
         b = torch.tensor(prob.rhs, device=dev)
-        for tag, dt in (("pcg_mixed", torch.float32), ("pcg_f64", torch.float64)):
+        for tag, dt in (("pcg_mixed", torch.float32), ("pcg_f64", torch.float64), ("pcg_ir", torch.float32)):
             op.precond_setup("cheb", dt, degree=3, lambda_max=lam)
-            op.pcg_solve(b, 1e-30, 3, raise_on_noconv=False)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            _, its, _ = op.pcg_solve(b, 1e-30, 30, raise_on_noconv=False)
-            e1.record()
-            torch.cuda.synchronize()
-            ms_it = e0.elapsed_time(e1) / its
+            if tag == "pcg_ir":
+                def solve(k):
+                    _, _, inner, _ = op.pcg_solve_ir(b, 1e-30, 1e-4, k, raise_on_noconv=False)
+                    return inner
+            else:
+                def solve(k):
+                    return op.pcg_solve(b, 1e-30, k, raise_on_noconv=False)[1]
+            solve(3)
+            ms_it = float("inf")
+            for _ in range(2):  # the faster of two runs (a one-off stall of ~0.2 s was seen once per process)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                its = solve(30)
+                e1.record()
+                torch.cuda.synchronize()
+                ms_it = min(ms_it, e0.elapsed_time(e1) / its)
             res[tag] = {"ms_per_iteration": ms_it, "gdofs_iterations": op.ndof / (ms_it * 1e-3) / 1e9}
         op.close()
         del op, kappa, x, y, z, gx, gk, b
