@@ -1,6 +1,8 @@
 // k_apply_impl.cuh -- kernels and launch templates of the high-order apply
-// and its backward, instantiated without the reaction term in k_apply.cu and
-// with it in k_apply_mass.cu (two translation units compile in parallel).
+// and its backward, instantiated without the reaction term in k_apply.cu,
+// with it in k_apply_mass.cu, on general meshes in k_apply_general.cu, and
+// the apply with FP32 arithmetic in k_apply_f32*.cu (the translation units
+// compile in parallel).
 //
 // y = G^T B^T D B G x (Eq. (4) on one rank) by sum factorisation, and its
 // backward (gradients with respect to x and to kappa at the Gauss points).
@@ -10,7 +12,10 @@
 // with the 1D interpolation matrix B_1D and derivative matrix d_1D (q x n,
 // n = p+1 GLL nodes, q = p+2 Gauss points), D the symmetric 3x3 factor stored
 // by the setup (Step S1.1), G the gather through the structured element map
-// (Dirichlet DOFs masked) and G^T FP64 atomics into y.  All arithmetic FP64.
+// (Dirichlet DOFs masked) and G^T FP64 atomics into y.  The arithmetic type R
+// is FP64 for the operator of Step S2.1 and its backward; R = float gives
+// the FP32 operator that the mixed-precision refinement iterates with (its
+// own table and shared-memory layout, Lay<P, float>).
 //
 // GB300 design (FP64 issue is the bound: 2 DFMA/clk/SM):
 //  * even-odd folding: GLL nodes and Gauss points are symmetric about 0, so

@@ -9,6 +9,9 @@
 // smoother reads the matrix k-1 times and touches each vector once per step.
 // In the mixed-precision mode the matrix, the diagonal and the smoother's
 // vectors are FP32; PCG's vectors, dot products and recurrences stay FP64.
+// The mixed-precision refinement (lor_pcg_ir_impl) runs the same PCG with
+// the FP32-arithmetic operator and forms every residual that decides
+// convergence with the FP64 one.
 #include <math.h>
 #include <string.h>
 
