@@ -866,8 +866,10 @@ def run_precision(args, dev):
     """Error of every mixed-precision result against its FP64 counterpart on
     the 16^3 p=4 workload (the FP64 path matches the FP64 oracle to 1e-12,
     see the parity tests): LOR values (max relative error per row maximum),
-    SpMV, the Chebyshev-Jacobi preconditioned vector, and the PCG solution to
-    1e-8 (relative max-norm difference and the true FP64 residual of each)."""
+    SpMV, the Chebyshev-Jacobi preconditioned vector, the PCG solution to
+    1e-8 (relative max-norm difference and the true FP64 residual of each);
+    the FP32-arithmetic apply and the refinement solver's solution (both
+    schemes) likewise."""
     import numpy as np
     import torch
 
@@ -904,6 +906,14 @@ def run_precision(args, dev):
         "pcg_iterations_f64_mixed": [res[torch.float64]["it"], res[torch.float32]["it"]],
         "pcg_true_rel_residual_f64_mixed": [res[torch.float64]["true_rel"], res[torch.float32]["true_rel"]],
         "pcg_solution_mixed_vs_f64_max_rel_diff": rel(res[torch.float32]["u"], res[torch.float64]["u"])})
+    # the FP32 operator and the refinement (FP32 LOR smoother, as "mixed")
+    out["apply_f32_max_rel_err"] = rel(op.apply_f32(x), op.apply(x))
+    for scheme in ("replace", "restart"):
+        u, outer, inner, _ = op.pcg_solve_ir(b, 1e-8, 1e-4, 20000, scheme=scheme)
+        out["refinement_%s" % scheme] = {
+            "inner_iterations": inner, "fp64_residuals": outer,
+            "true_rel_residual": float((b - op.apply(u)).norm() / b.norm()),
+            "solution_vs_f64_max_rel_diff": rel(u, res[torch.float64]["u"])}
     op.close()
     return out
 
