@@ -165,3 +165,31 @@ def test_refinement_limits_and_errors():
     z = torch.zeros_like(b)
     x, outer, inner, rel = op.pcg_solve_ir(z, 1e-8, 1e-4, 100)
     assert outer == 0 and inner == 0 and rel == 0.0 and torch.count_nonzero(x).item() == 0
+
+
+@pytest.mark.parametrize("dims,p,kind,degree", [((4, 3, 3), 1, "jacobi", 1), ((2, 2, 3), 2, "cheb", 1),
+                                                ((2, 2, 2), 4, "cheb", 2), ((1, 2, 1), 8, "cheb", 5)])
+def test_refinement_across_preconditioners_and_degrees(dims, p, kind, degree):
+    """Every preconditioner mode of the fused PCG update (Jacobi, Chebyshev of
+    degree 1 and >= 2) under both schemes, against the oracle's FP64 solve."""
+    prob, mesh, op = setup(dims, p)
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float32)
+    csr = oracle.lor_assemble(mesh, p, p + 2, prob.kappa, True)
+    v0 = np.random.default_rng(7).standard_normal(op.ndof)
+    lam = oracle.power_lambda_max(*csr, v0, 20)
+    if kind == "jacobi":
+        op.precond_setup("jacobi", torch.float32)
+        ref = oracle.pcg(mesh, p, p + 2, prob.kappa, csr, prob.rhs, 1e-10, 4000, oracle.PRECOND_JACOBI)
+    else:
+        op.precond_setup("cheb", torch.float32, degree=degree, lambda_max=lam)
+        ref = oracle.pcg(mesh, p, p + 2, prob.kappa, csr, prob.rhs, 1e-10, 4000, oracle.PRECOND_CHEB, degree,
+                         lam / 30, 1.1 * lam)
+    xo = ref[0]
+    b = t(prob.rhs)
+    for scheme in ("replace", "restart"):
+        x, outer, inner, rel = op.pcg_solve_ir(b, 1e-10, 1e-3, 4000, scheme=scheme)
+        r = prob.rhs - oracle.ho_apply(mesh, p, p + 2, prob.kappa, x.cpu().numpy())
+        assert rel <= 1e-10 and np.linalg.norm(r) <= 2e-10 * np.linalg.norm(prob.rhs), scheme
+        assert np.abs(x.cpu().numpy() - xo).max() <= 1e-8 * np.abs(xo).max(), scheme
+    op.close()
