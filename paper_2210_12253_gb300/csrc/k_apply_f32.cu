@@ -8,6 +8,8 @@
 
 cudaError_t lor_apply_f32_general_dispatch(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
                                            const double* x, double* y, cudaStream_t s);
+cudaError_t lor_apply_f32v_general_dispatch(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                            const float* x, float* y, cudaStream_t s);
 
 namespace {
 
@@ -30,4 +32,13 @@ cudaError_t lor_launch_apply_f32_accumulate(const LorMesh& m, const LorTables& T
   if (m.edofs) return lor_apply_f32_general_dispatch(m, T, Dq, Mq, x, y, s);
   if (Mq) return apply_dispatch<true, false, float>(m, T, Dq, Mq, x, y, s);
   return apply_dispatch<false, false, float>(m, T, Dq, nullptr, x, y, s);
+}
+
+// The same with FP32 input and output vectors (FP32 atomics into y), for the
+// refinement's inner iterations whose vectors are FP32.
+cudaError_t lor_launch_apply_f32v_accumulate(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                             const float* x, float* y, cudaStream_t s) {
+  if (m.edofs) return lor_apply_f32v_general_dispatch(m, T, Dq, Mq, x, y, s);
+  if (Mq) return apply_dispatch<true, false, float, float>(m, T, Dq, Mq, x, y, s);
+  return apply_dispatch<false, false, float, float>(m, T, Dq, nullptr, x, y, s);
 }

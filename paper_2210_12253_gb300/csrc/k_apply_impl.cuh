@@ -224,6 +224,10 @@ __device__ __forceinline__ R to_r(double v) {
     return __uint_as_float((hi & 0x80000000u) | mag);
   }
 }
+template <typename R>
+__device__ __forceinline__ R to_r(float v) {
+  return (R)v;
+}
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) {
   const unsigned f = __float_as_uint(v);
@@ -231,6 +235,13 @@ __device__ __forceinline__ double to_f64(float v) {
   const bool zero = ((f >> 23) & 0xffu) == 0u;
   const unsigned hi = zero ? sign : (sign | (((f & 0x7fffffffu) >> 3) + (896u << 20)));
   return __hiloint2double((int)hi, zero ? 0 : (int)(f << 29));
+}
+
+// A result of the compute type R into the output vector type XV.
+template <typename XV, typename R>
+__device__ __forceinline__ XV to_out(R v) {
+  if constexpr (sizeof(XV) == sizeof(double)) return to_f64(v);
+  else return (XV)v;
 }
 
 // CNT consecutive FP32 table entries from a 16-byte aligned, padded row
@@ -475,9 +486,9 @@ __device__ __forceinline__ void bwd(const Tab<P, R>& t, const R* e1, const R* o1
 // ---- stages over all lines of E elements (e_first .. e_first+E-1) ----
 // X: u (gathered from global, masked) -> A1[c][k][j][g0] = (B u, d u) along x.
 // GEN: through the general element-to-DOF map and essential mask.
-template <int P, bool GEN, typename R>
+template <int P, bool GEN, typename R, typename XV>
 __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E,
-                                        const double* __restrict__ x, R* A) {
+                                        const XV* __restrict__ x, R* A) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
   constexpr int N = Z::N, Q = Z::Q;
@@ -498,7 +509,7 @@ __device__ __forceinline__ void stage_x(const LorMesh& m, const Tab<P, R>& t, in
       const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
       const int64_t J = ey * P + j, K = ez * P + k;
       const bool row_ess = J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1;
-      const double* xr = x + (ex * P) + m.nx * (J + m.ny * K);
+      const XV* xr = x + (ex * P) + m.nx * (J + m.ny * K);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t I = ex * P + i;
@@ -669,9 +680,9 @@ __device__ __forceinline__ void stage_y_t(const LorMesh& m, const Tab<P, R>& t, 
 }
 
 // X': A1 (U0, U1) -> y_line = d_x^T U0 + B_x^T U1, scatter-added into y.
-template <int P, bool GEN, typename R>
+template <int P, bool GEN, typename R, typename XV>
 __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P, R>& t, int64_t e_first, int E,
-                                          const R* A, double* __restrict__ y) {
+                                          const R* A, XV* __restrict__ y) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
   constexpr int N = Z::N, Q = Z::Q;
@@ -694,26 +705,26 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P, R>& t, 
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t d = dm[i];
-        if (!m.ess[d]) atomicAdd(y + d, to_f64(yl[i]));
+        if (!m.ess[d]) atomicAdd(y + d, to_out<XV>(yl[i]));
       }
     } else {
       const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
       const int64_t J = ey * P + j, K = ez * P + k;
       if (J == 0 || K == 0 || J == m.ny - 1 || K == m.nz - 1) continue;
-      double* yr = y + (ex * P) + m.nx * (J + m.ny * K);
+      XV* yr = y + (ex * P) + m.nx * (J + m.ny * K);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const int64_t I = ex * P + i;
-        if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, to_f64(yl[i]));
+        if (I != 0 && I != m.nx - 1) atomicAdd(yr + i, to_out<XV>(yl[i]));
       }
     }
   }
 }
 
-template <int P, bool MASS, bool GEN, typename R>
+template <int P, bool MASS, bool GEN, typename R, typename XV>
 __global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const R* __restrict__ Dq,
-                                                    const R* __restrict__ Mq, const double* __restrict__ x,
-                                                    double* __restrict__ y) {
+                                                    const R* __restrict__ Mq, const XV* __restrict__ x,
+                                                    XV* __restrict__ y) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E;
@@ -845,17 +856,17 @@ cudaError_t configure(K kernel, size_t bytes, unsigned* mask) {
   return cudaSuccess;
 }
 
-template <int P, bool MASS, bool GEN, typename R>
-cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const double* x,
-                    double* y, cudaStream_t s) {
+template <int P, bool MASS, bool GEN, typename R, typename XV>
+cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const XV* x, XV* y,
+                    cudaStream_t s) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
   const size_t bytes = sizeof(R) * (L::TABLES + (size_t)Z::E * L::PER_ELEM);
   static unsigned mask = 0;
-  cudaError_t err = configure(k_apply<P, MASS, GEN, R>, bytes, &mask);
+  cudaError_t err = configure(k_apply<P, MASS, GEN, R, XV>, bytes, &mask);
   if (err != cudaSuccess) return err;
   const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply<P, MASS, GEN, R><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
+  k_apply<P, MASS, GEN, R, XV><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
@@ -874,12 +885,12 @@ cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, c
   return cudaGetLastError();
 }
 
-template <bool MASS, bool GEN, typename R>
-cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const double* x,
-                           double* y, cudaStream_t s) {
+template <bool MASS, bool GEN, typename R, typename XV = double>
+cudaError_t apply_dispatch(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const XV* x, XV* y,
+                           cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: return apply_p<P, MASS, GEN, R>(m, T, Dq, Mq, x, y, s);
+  case P: return apply_p<P, MASS, GEN, R, XV>(m, T, Dq, Mq, x, y, s);
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE

@@ -15,6 +15,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "lor_internal.cuh"
 
 namespace {
@@ -29,15 +31,21 @@ int grid_rows(int64_t n) {
 #define LOR_GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// Vectors of the solve are FP64, except in the refinement's inner
+// iterations (V = float).  A thread's partial sums accumulate in the vector
+// precision (a few dozen terms per thread) and the CTA and grid sums in FP64.
+template <typename V>
+using Acc = std::conditional_t<sizeof(V) == sizeof(float), float, double>;
+
 // Chebyshev step 0 from z_0 = 0: d = z = D^-1 r / theta.  If zout64 is set
 // (degree 1) the result goes straight to the FP64 output.
-template <typename VT>
-__global__ void k_cheb_first(int64_t n, const VT* __restrict__ dinv, const double* __restrict__ r, VT inv_theta,
-                             VT* __restrict__ z, VT* __restrict__ d, double* __restrict__ zout64) {
+template <typename VT, typename V = double>
+__global__ void k_cheb_first(int64_t n, const VT* __restrict__ dinv, const V* __restrict__ r, VT inv_theta,
+                             VT* __restrict__ z, VT* __restrict__ d, V* __restrict__ zout64) {
   LOR_GRID_STRIDE(i, n) {
     const VT v = dinv[i] * (VT)r[i] * inv_theta;
     if (zout64) {
-      zout64[i] = (double)v;
+      zout64[i] = (V)v;
     } else {
       z[i] = v;
       d[i] = v;
@@ -53,10 +61,9 @@ __global__ void k_scale(double* __restrict__ v, int64_t n, double a) {
   LOR_GRID_STRIDE(i, n) v[i] *= a;
 }
 
-template <typename VT>
-__global__ void k_jacobi(int64_t n, const VT* __restrict__ dinv, const double* __restrict__ r,
-                         double* __restrict__ z) {
-  LOR_GRID_STRIDE(i, n) z[i] = (double)(dinv[i] * (VT)r[i]);
+template <typename VT, typename V = double>
+__global__ void k_jacobi(int64_t n, const VT* __restrict__ dinv, const V* __restrict__ r, V* __restrict__ z) {
+  LOR_GRID_STRIDE(i, n) z[i] = (V)(dinv[i] * (VT)r[i]);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -296,24 +303,24 @@ enum StencilMode {
 };
 
 // What each mode does with row i's product s = (A x)_i.
-template <typename VT, typename XT, int MODE>
+template <typename VT, typename XT, int MODE, typename V>
 __device__ __forceinline__ void stencil_epilogue(int64_t i, VT s, const VT* __restrict__ dinv,
-                                                 const XT* __restrict__ x, const double* __restrict__ r,
+                                                 const XT* __restrict__ x, const V* __restrict__ r,
                                                  VT* __restrict__ d, VT c1, VT c2, VT* __restrict__ zout,
-                                                 double* __restrict__ y, double& acc) {
+                                                 V* __restrict__ y, Acc<V>& acc) {
   if constexpr (MODE == ST_SPMV) {
-    y[i] = (double)s;
+    y[i] = (V)s;
   } else if constexpr (MODE == ST_DINV_SPMV) {
-    y[i] = (double)(dinv[i] * s);
+    y[i] = (V)(dinv[i] * s);
   } else {
-    const double ri = r[i];
+    const V ri = r[i];
     const VT dn = c1 * d[i] + c2 * dinv[i] * ((VT)ri - s);
     const VT zn = (VT)x[i] + dn;
     if constexpr (MODE == ST_CHEB_DOT) {
-      y[i] = (double)zn;
-      acc += ri * (double)zn;
+      y[i] = (V)zn;
+      acc += ri * (V)zn;
     } else if (y) {
-      y[i] = (double)zn;
+      y[i] = (V)zn;
     } else {
       d[i] = dn;
       zout[i] = zn;
@@ -321,11 +328,11 @@ __device__ __forceinline__ void stencil_epilogue(int64_t i, VT s, const VT* __re
   }
 }
 
-template <typename VT, typename XT, int MODE>
+template <typename VT, typename XT, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __restrict__ vals,
                                                       const VT* __restrict__ dinv, const XT* __restrict__ x,
-                                                      const double* __restrict__ r, VT* __restrict__ d, VT c1, VT c2,
-                                                      VT* __restrict__ zout, double* __restrict__ y,
+                                                      const V* __restrict__ r, VT* __restrict__ d, VT c1, VT c2,
+                                                      VT* __restrict__ zout, V* __restrict__ y,
                                                       double* __restrict__ partial, unsigned* __restrict__ counter,
                                                       double* __restrict__ out, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     if ((int64_t)blockIdx.x < ntiles) base[0] = issue_tile<VT>(m, vals, blockIdx.x, buf0, &bar[0]);
   }
   __syncthreads();
-  double acc = 0.0;
+  Acc<V> acc = 0;
   int it = 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += stride, ++it) {
     const int b = it & 1;
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     if (i < m.ndof) {
       const StencilRow row = stencil_row(m, i);
       const VT s = stencil_product<VT, XT>(m, row, sv + (row.start - base[b]), x);
-      stencil_epilogue<VT, XT, MODE>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
+      stencil_epilogue<VT, XT, MODE, V>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
     }
     __syncthreads();  // every read of this buffer is done before it is refilled
   }
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     const int b = it & 1;
     if (blockIdx.x + (int64_t)(it + 1) * stride < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
   }
-  if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
+  if constexpr (MODE == ST_CHEB_DOT) finish_sums((double)acc, 0.0, 1, partial, counter, out, nullptr);
 }
 
 // ---- the same modes on an explicit CSR pattern (general meshes, whose LOR
@@ -380,17 +387,17 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
 // can finish in the last CTA.
 constexpr int kLanes = 4;
 
-template <typename VT, typename XT, int MODE>
+template <typename VT, typename XT, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restrict__ vals, const VT* __restrict__ dinv,
-                                                  const XT* __restrict__ x, const double* __restrict__ r,
+                                                  const XT* __restrict__ x, const V* __restrict__ r,
                                                   VT* __restrict__ d, VT c1, VT c2, VT* __restrict__ zout,
-                                                  double* __restrict__ y, double* __restrict__ partial,
+                                                  V* __restrict__ y, double* __restrict__ partial,
                                                   unsigned* __restrict__ counter, double* __restrict__ out) {
   const int64_t n = m.ndof;
   const int64_t rows_per_round = (int64_t)gridDim.x * blockDim.x / kLanes;
   const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kLanes;
   const int group = (threadIdx.x & 31) / kLanes, lane = threadIdx.x & (kLanes - 1);
-  double acc = 0.0;
+  Acc<V> acc = 0;
   for (int64_t base = warp_first; base < n; base += rows_per_round) {
     const int64_t i = base + group;
     const bool valid = i < n;
@@ -402,15 +409,15 @@ __global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restric
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (!valid || lane != 0) continue;
-    stencil_epilogue<VT, XT, MODE>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
+    stencil_epilogue<VT, XT, MODE, V>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
   }
-  if constexpr (MODE == ST_CHEB_DOT) finish_sums(acc, 0.0, 1, partial, counter, out, nullptr);
+  if constexpr (MODE == ST_CHEB_DOT) finish_sums((double)acc, 0.0, 1, partial, counter, out, nullptr);
 }
 
 // Persistent grid: every SM filled to the kernel's occupancy (at most one CTA
 // per tile; the reducing mode at most LOR_PCG_MAX_BLOCKS CTAs).  The shared
 // memory limit is raised once per device.
-template <typename VT, typename XT, int MODE>
+template <typename VT, typename XT, int MODE, typename V>
 cudaError_t stencil_grid(const LorMesh& m, int* grid) {
   static int per_device[64] = {};
   int dev = 0;
@@ -418,12 +425,12 @@ cudaError_t stencil_grid(const LorMesh& m, int* grid) {
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!per_device[dev]) {
-    err = cudaFuncSetAttribute(k_stencil<VT, XT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_stencil<VT, XT, MODE, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)stencil_smem<VT>());
     int sms = 0, occ = 0;
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err == cudaSuccess)
-      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil<VT, XT, MODE>, kThreads,
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil<VT, XT, MODE, V>, kThreads,
                                                           stencil_smem<VT>());
     if (err != cudaSuccess) return err;
     per_device[dev] = sms * (occ > 0 ? occ : 1);
@@ -435,23 +442,23 @@ cudaError_t stencil_grid(const LorMesh& m, int* grid) {
   return cudaSuccess;
 }
 
-template <typename VT, typename XT, int MODE>
-cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, const XT* x, const double* r, VT* d,
-                           double c1, double c2, VT* zout, double* y, double* partial, unsigned* counter,
+template <typename VT, typename XT, int MODE, typename V = double>
+cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, const XT* x, const V* r, VT* d,
+                           double c1, double c2, VT* zout, V* y, double* partial, unsigned* counter,
                            double* out, int* status, cudaStream_t s) {
   if (m.rowptr) {  // general mesh: explicit CSR pattern
     const int64_t want = (m.ndof * kLanes + kThreads - 1) / kThreads;
     const int64_t cap = MODE == ST_CHEB_DOT ? LOR_PCG_MAX_BLOCKS : 152 * 8;
     const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_csr<VT, XT, MODE><<<grid, kThreads, 0, s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y, partial, counter,
+    k_csr<VT, XT, MODE, V><<<grid, kThreads, 0, s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y, partial, counter,
                                                   out);
     lor_count_launch();
     return cudaGetLastError();
   }
   int grid = 0;
-  cudaError_t err = stencil_grid<VT, XT, MODE>(m, &grid);
+  cudaError_t err = stencil_grid<VT, XT, MODE, V>(m, &grid);
   if (err != cudaSuccess) return err;
-  k_stencil<VT, XT, MODE><<<grid, kThreads, stencil_smem<VT>(), s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y,
+  k_stencil<VT, XT, MODE, V><<<grid, kThreads, stencil_smem<VT>(), s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y,
                                                                     partial, counter, out, status); lor_count_launch();
   return cudaGetLastError();
 }
@@ -472,11 +479,11 @@ __global__ void k_diag_inv(LorMesh m, const VT* __restrict__ vals, VT* __restric
 }
 
 // One Chebyshev step j >= 1 (see ST_CHEB); the last one writes z64.
-template <typename VT>
-cudaError_t cheb_step(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, const VT* zin, VT* zout, VT* d,
-                      double c1, double c2, double* z64, cudaStream_t s) {
-  return launch_stencil<VT, VT, ST_CHEB>(c->m, vals, dinv, zin, r, d, c1, c2, zout, z64, nullptr, nullptr, nullptr,
-                                         c->d_status, s);
+template <typename VT, typename V = double>
+cudaError_t cheb_step(lor_ctx* c, const VT* vals, const VT* dinv, const V* r, const VT* zin, VT* zout, VT* d,
+                      double c1, double c2, V* z64, cudaStream_t s) {
+  return launch_stencil<VT, VT, ST_CHEB, V>(c->m, vals, dinv, zin, r, d, c1, c2, zout, z64, nullptr, nullptr, nullptr,
+                                            c->d_status, s);
 }
 
 // ---------------------------------------------------------------- PCG vector kernels
@@ -488,13 +495,12 @@ __global__ void k_residual(int64_t n, const double* __restrict__ b, const double
   LOR_GRID_STRIDE(i, n) r[i] = b[i] - Ax[i];
 }
 
-template <typename VT>
-cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
-                            cudaStream_t s) {
+template <typename VT, typename V = double>
+cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const V* r, V* z, cudaStream_t s) {
   const int64_t n = c->m.ndof;
   const int g = grid_rows(n);
   if (c->pc_kind == LOR_PRECOND_JACOBI) {
-    k_jacobi<VT><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
+    k_jacobi<VT, V><<<g, kThreads, 0, s>>>(n, dinv, r, z); lor_count_launch();
     return cudaGetLastError();
   }
   VT* zA = (VT*)c->pc_work;
@@ -503,14 +509,15 @@ cudaError_t precond_apply_t(lor_ctx* c, const VT* vals, const VT* dinv, const do
   const double theta = 0.5 * (c->pc_hi + c->pc_lo), delta = 0.5 * (c->pc_hi - c->pc_lo);
   const double sigma = theta / delta;
   const int k = c->pc_degree;
-  k_cheb_first<VT><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr); lor_count_launch();
+  k_cheb_first<VT, V><<<g, kThreads, 0, s>>>(n, dinv, r, (VT)(1.0 / theta), zA, d, k == 1 ? z : nullptr);
+  lor_count_launch();
   double rho = 1.0 / sigma;
   VT* zin = zA;
   VT* zout = zB;
   for (int j = 1; j < k; ++j) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
-    const cudaError_t err = cheb_step<VT>(c, vals, dinv, r, zin, zout, d, c1, c2, j == k - 1 ? z : nullptr, s);
+    const cudaError_t err = cheb_step<VT, V>(c, vals, dinv, r, zin, zout, d, c1, c2, j == k - 1 ? z : nullptr, s);
     if (err != cudaSuccess) return err;
     rho = rho_new;
     VT* t = zin;
@@ -559,22 +566,33 @@ cudaError_t lor_launch_diag_inv(const LorMesh& m, const void* vals, int dtype, v
 cudaError_t lor_launch_spmv(const LorMesh& m, const void* vals, int dtype, const double* x, double* y, int* status,
                             cudaStream_t s) {
   if (dtype == LOR_F64)
-    return launch_stencil<double, double, ST_SPMV>(m, (const double*)vals, nullptr, x, nullptr, nullptr, 0.0, 0.0,
-                                                   nullptr, y, nullptr, nullptr, nullptr, status, s);
-  return launch_stencil<float, double, ST_SPMV>(m, (const float*)vals, nullptr, x, nullptr, nullptr, 0.0, 0.0, nullptr,
-                                                y, nullptr, nullptr, nullptr, status, s);
+    return launch_stencil<double, double, ST_SPMV, double>(m, (const double*)vals, nullptr, x, nullptr, nullptr, 0.0,
+                                                           0.0, nullptr, y, nullptr, nullptr, nullptr, status, s);
+  return launch_stencil<float, double, ST_SPMV, double>(m, (const float*)vals, nullptr, x, nullptr, nullptr, 0.0, 0.0,
+                                                        nullptr, y, nullptr, nullptr, nullptr, status, s);
 }
 
-int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s) {
+namespace {
+
+// z = B_h r for vectors of type V (FP64, or FP32 in the refinement's inner
+// iterations).
+template <typename V>
+int precond_apply_v(lor_ctx* c, const V* r, V* z, cudaStream_t s) {
   cudaError_t err;
   if (c->pc_kind == LOR_PRECOND_NONE) {
-    err = cudaMemcpyAsync(z, r, sizeof(double) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
+    err = cudaMemcpyAsync(z, r, sizeof(V) * c->m.ndof, cudaMemcpyDeviceToDevice, s);
   } else if (c->pc_dtype == LOR_F64) {
-    err = precond_apply_t<double>(c, c->vals64, c->dinv64, r, z, s);
+    err = precond_apply_t<double, V>(c, c->vals64, c->dinv64, r, z, s);
   } else {
-    err = precond_apply_t<float>(c, c->vals32, c->dinv32, r, z, s);
+    err = precond_apply_t<float, V>(c, c->vals32, c->dinv32, r, z, s);
   }
   return err == cudaSuccess ? LOR_OK : fail(c, err, "precond_apply");
+}
+
+}  // namespace
+
+int lor_precond_apply_impl(lor_ctx* c, const double* r, double* z, cudaStream_t s) {
+  return precond_apply_v<double>(c, r, z, s);
 }
 
 int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, double* lambda, cudaStream_t s) {
@@ -593,10 +611,12 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
   double lam = 0.0;
   for (int it = 0; it < iters; ++it) {
     err = dtype == LOR_F64
-              ? launch_stencil<double, double, ST_DINV_SPMV>(c->m, c->vals64, c->dinv64, v, nullptr, nullptr, 0.0, 0.0,
-                                                             nullptr, w, nullptr, nullptr, nullptr, c->d_status, s)
-              : launch_stencil<float, double, ST_DINV_SPMV>(c->m, c->vals32, c->dinv32, v, nullptr, nullptr, 0.0, 0.0,
-                                                            nullptr, w, nullptr, nullptr, nullptr, c->d_status, s);
+              ? launch_stencil<double, double, ST_DINV_SPMV, double>(c->m, c->vals64, c->dinv64, v, nullptr, nullptr,
+                                                                     0.0, 0.0, nullptr, w, nullptr, nullptr, nullptr,
+                                                                     c->d_status, s)
+              : launch_stencil<float, double, ST_DINV_SPMV, double>(c->m, c->vals32, c->dinv32, v, nullptr, nullptr,
+                                                                    0.0, 0.0, nullptr, w, nullptr, nullptr, nullptr,
+                                                                    c->d_status, s);
     if (err != cudaSuccess) return fail(c, err, "power iteration");
     dot_to(c, w, w, S + 0, s);
     dot_to(c, v, v, S + 1, s);
@@ -626,12 +646,13 @@ int lor_power_iteration(lor_ctx* c, int dtype, int iters, const double* v0, doub
 namespace {
 
 // ---------------------------------------------------------------- fused PCG kernels
-__global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const double* __restrict__ a,
-                                                      const double* __restrict__ b, double* __restrict__ partial,
-                                                      unsigned* __restrict__ counter, double* __restrict__ out) {
-  double s = 0.0;
+template <typename V = double>
+__global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const V* __restrict__ a, const V* __restrict__ b,
+                                                      double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                      double* __restrict__ out) {
+  Acc<V> s = 0;
   LOR_GRID_STRIDE(i, n) s += a[i] * b[i];
-  finish_sums(s, 0.0, 1, partial, counter, out, nullptr);
+  finish_sums((double)s, 0.0, 1, partial, counter, out, nullptr);
 }
 
 // x += alpha p, r -= alpha q (alpha = rz / pq on the device), r.r, and the
@@ -640,20 +661,21 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const double* _
 //   mode 2 (Chebyshev, degree 1): z = D^-1 r / theta;
 //   mode 3 (Chebyshev, degree >= 2): zA = d = D^-1 r / theta (smoother precision).
 // Modes 0-2 also form r.z (z is final there).
-template <typename VT>
+template <typename VT, typename V = double>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double* __restrict__ S, int rz_slot,
-                                                         const double* __restrict__ p, const double* __restrict__ q,
-                                                         double* __restrict__ x, double* __restrict__ r, int mode,
+                                                         const V* __restrict__ p, const V* __restrict__ q,
+                                                         double* __restrict__ x, V* __restrict__ r, int mode,
                                                          const VT* __restrict__ dinv, VT inv_theta,
-                                                         double* __restrict__ z, VT* __restrict__ zA,
+                                                         V* __restrict__ z, VT* __restrict__ zA,
                                                          VT* __restrict__ d, double* __restrict__ partial,
                                                          unsigned* __restrict__ counter, double* __restrict__ out_rr,
                                                          double* __restrict__ out_rz) {
   const double alpha = S[rz_slot] / S[S_PQ];
-  double srr = 0.0, srz = 0.0;
+  const V av = (V)alpha;
+  Acc<V> srr = 0, srz = 0;
   LOR_GRID_STRIDE(i, n) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
+    x[i] += alpha * (double)p[i];
+    const V ri = r[i] - av * q[i];
     r[i] = ri;
     srr += ri * ri;
     if (mode == 0) {
@@ -661,27 +683,43 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double
       srz += ri * ri;
     } else if (mode == 1 || mode == 2) {
       const VT zi = mode == 1 ? dinv[i] * (VT)ri : dinv[i] * (VT)ri * inv_theta;
-      z[i] = (double)zi;
-      srz += ri * (double)zi;
+      z[i] = (V)zi;
+      srz += ri * (V)zi;
     } else {
       const VT zi = dinv[i] * (VT)ri * inv_theta;
       zA[i] = zi;
       d[i] = zi;
     }
   }
-  finish_sums(srr, srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz);
+  finish_sums((double)srr, (double)srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz);
 }
 
 // p = z + beta p (beta = rz_new / rz_old; first: p = z) and the output of
 // the next apply initialised: q = p on essential DOFs, 0 elsewhere.
+template <typename V = double>
 __global__ void k_pcg_direction(LorMesh m, const double* __restrict__ S, int new_slot, int old_slot, int first,
-                                const double* __restrict__ z, double* __restrict__ p, double* __restrict__ q) {
-  const double beta = first ? 0.0 : S[new_slot] / S[old_slot];
+                                const V* __restrict__ z, V* __restrict__ p, V* __restrict__ q) {
+  const V beta = (V)(first ? 0.0 : S[new_slot] / S[old_slot]);
   LOR_GRID_STRIDE(i, m.ndof) {
-    const double pi = first ? z[i] : z[i] + beta * p[i];
+    const V pi = first ? z[i] : z[i] + beta * p[i];
     p[i] = pi;
-    q[i] = lor_dof_essential(m, i) ? pi : 0.0;
+    q[i] = lor_dof_essential(m, i) ? pi : (V)0;
   }
+}
+
+// r = b - A x rounded to V, and |b - A x|^2 (FP64) into *out.
+template <typename V>
+__global__ void __launch_bounds__(kThreads) k_residual_norm(int64_t n, const double* __restrict__ b,
+                                                            const double* __restrict__ Ax, V* __restrict__ r,
+                                                            double* __restrict__ partial,
+                                                            unsigned* __restrict__ counter, double* __restrict__ out) {
+  double s = 0.0;
+  LOR_GRID_STRIDE(i, n) {
+    const double ri = b[i] - Ax[i];
+    r[i] = (V)ri;
+    s += ri * ri;
+  }
+  finish_sums(s, 0.0, 1, partial, counter, out, nullptr);
 }
 
 // two partial sums per CTA, after the scalars
@@ -699,9 +737,9 @@ int pcg_grid(K kernel) {
   return g < 1 ? 1 : g > LOR_PCG_MAX_BLOCKS ? LOR_PCG_MAX_BLOCKS : g;
 }
 
-template <typename VT>
-cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const double* r, double* z,
-                             double* out_rz, cudaStream_t s) {
+template <typename VT, typename V = double>
+cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const V* r, V* z, double* out_rz,
+                             cudaStream_t s) {
   // Chebyshev steps 1 .. k-1 after k_pcg_update's step 0 (degree >= 2)
   const int64_t n = c->m.ndof;
   VT* zA = (VT*)c->pc_work;
@@ -717,12 +755,12 @@ cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const d
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
     if (j < k - 1) {
-      const cudaError_t err = cheb_step<VT>(c, vals, dinv, r, zin, zout, d, c1, c2, nullptr, s);
+      const cudaError_t err = cheb_step<VT, V>(c, vals, dinv, r, zin, zout, d, c1, c2, (V*)nullptr, s);
       if (err != cudaSuccess) return err;
     } else {
-      const cudaError_t err = launch_stencil<VT, VT, ST_CHEB_DOT>(c->m, vals, dinv, zin, r, d, c1, c2, nullptr, z,
-                                                                  pcg_partials(c), c->red_count, out_rz, c->d_status,
-                                                                  s);
+      const cudaError_t err = launch_stencil<VT, VT, ST_CHEB_DOT, V>(c->m, vals, dinv, zin, r, d, c1, c2, nullptr, z,
+                                                                     pcg_partials(c), c->red_count, out_rz,
+                                                                     c->d_status, s);
       if (err != cudaSuccess) return err;
     }
     rho = rho_new;
@@ -733,13 +771,13 @@ cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const d
   return cudaGetLastError();
 }
 
-template <typename VT>
-cudaError_t pcg_update(lor_ctx* c, const VT* dinv, double* S, int cur, const double* p, const double* q, double* x,
-                       double* r, double* z, int mode, double* out_rz, int grid, cudaStream_t s) {
+template <typename VT, typename V = double>
+cudaError_t pcg_update(lor_ctx* c, const VT* dinv, double* S, int cur, const V* p, const V* q, double* x, V* r,
+                       V* z, int mode, double* out_rz, int grid, cudaStream_t s) {
   const double theta = 0.5 * (c->pc_hi + c->pc_lo);
   VT* zA = (VT*)c->pc_work;
   VT* d = zA ? zA + 2 * c->m.ndof : nullptr;
-  k_pcg_update<VT><<<grid, kThreads, 0, s>>>(c->m.ndof, S, cur, p, q, x, r, mode, dinv,
+  k_pcg_update<VT, V><<<grid, kThreads, 0, s>>>(c->m.ndof, S, cur, p, q, x, r, mode, dinv,
                                                    (VT)(theta > 0 ? 1.0 / theta : 1.0), z, zA, d, pcg_partials(c),
                                                    c->red_count, S + S_RR, out_rz); lor_count_launch();
   return cudaGetLastError();
@@ -749,37 +787,49 @@ __global__ void k_add(int64_t n, double* __restrict__ x, const double* __restric
   LOR_GRID_STRIDE(i, n) x[i] += d[i];
 }
 
-// PCG with x_0 = 0.  f32_apply: the operator is the FP32-arithmetic apply,
-// else the FP64 one.  confirm: a converged recurrence residual is checked
-// against the true residual b - A x (FP64 operator) before the solve counts
-// as converged; if it fails, the iteration continues from the true residual
-// (keeping the search direction).  replace > 0 (with confirm): the true
-// residual is also formed, and substituted, whenever the recurrence residual
-// has fallen by the factor `replace` since the last substitution (residual
-// replacement); *replacements counts them.  A replacement that does not
-// lower the true residual ends the solve (LOR_ENOCONV).
+// PCG with x_0 = 0.  V: the type of the vectors r, z, p, q (x stays FP64).
+// f32_apply: the operator is the FP32-arithmetic apply, else the FP64 one
+// (V = float requires it).  confirm: a converged recurrence residual is
+// checked against the true residual b - A x (FP64 operator) before the solve
+// counts as converged; if it fails, the iteration continues from the true
+// residual (keeping the search direction).  replace > 0 (with confirm): the
+// true residual is also formed, and substituted, whenever the recurrence
+// residual has fallen by the factor `replace` since the last substitution
+// (residual replacement); *replacements counts them.  A replacement that does
+// not lower the true residual ends the solve (LOR_ENOCONV).
+template <typename V>
 int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, bool f32_apply, bool confirm,
              double replace, int* iters, double* relres, int* replacements, cudaStream_t s) {
+  constexpr bool VF = sizeof(V) == sizeof(float);
   const int64_t n = c->m.ndof;
-  double* r = c->pcg_work;
-  double* z = r + n;
-  double* p = z + n;
-  double* q = p + n;
+  // FP64: r, z, p, Ap in the 4 N doubles of pcg_work.  FP32: the same four
+  // in its first 2 N doubles' worth, and A x (FP64) for the true residual in
+  // the last N doubles.
+  V* r = reinterpret_cast<V*>(c->pcg_work);
+  V* z = r + n;
+  V* p = z + n;
+  V* q = p + n;
+  double* ax64 = c->pcg_work + 2 * n;
   double* S = c->red + LOR_RED_BLOCKS;  // S[0] = p.q, S[1] = r.r, S[2] = b.b, S[3], S[4] = r.z (alternating)
   double* hs = c->h_scalar;
   const int g = grid_rows(n);
   const bool f64 = c->pc_dtype == LOR_F64;
   // preconditioner mode of the fused update (see k_pcg_update)
   const int mode = c->pc_kind == LOR_PRECOND_NONE ? 0 : c->pc_kind == LOR_PRECOND_JACOBI ? 1 : c->pc_degree == 1 ? 2 : 3;
-  const int g_dot = pcg_grid(k_pcg_dot);
-  const int g_upd = f64 ? pcg_grid(k_pcg_update<double>) : pcg_grid(k_pcg_update<float>);
-  auto dot = [&](const double* a, const double* bb, double* out) {
-    k_pcg_dot<<<g_dot, kThreads, 0, s>>>(n, a, bb, pcg_partials(c), c->red_count, out); lor_count_launch();
+  const int g_dot = pcg_grid(k_pcg_dot<V>);
+  const int g_dot64 = pcg_grid(k_pcg_dot<double>);
+  const int g_upd = f64 ? pcg_grid(k_pcg_update<double, V>) : pcg_grid(k_pcg_update<float, V>);
+  auto dot = [&](const V* a, const V* bb, double* out) {
+    k_pcg_dot<V><<<g_dot, kThreads, 0, s>>>(n, a, bb, pcg_partials(c), c->red_count, out); lor_count_launch();
   };
   cudaError_t err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   if (err == cudaSuccess) {
-    dot(b, b, S + S_BB);
+    if constexpr (VF) err = lor_launch_to_f32(b, r, n, s);
+    else err = cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  }
+  if (err == cudaSuccess) {
+    k_pcg_dot<double><<<g_dot64, kThreads, 0, s>>>(n, b, b, pcg_partials(c), c->red_count, S + S_BB);
+    lor_count_launch();
     err = cudaMemcpyAsync(hs, S + S_BB, sizeof(double), cudaMemcpyDeviceToHost, s);
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
@@ -792,20 +842,24 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   if (nb == 0.0) {
     status = LOR_OK;
   } else {
-    int rc = lor_precond_apply_impl(c, r, z, s);
+    int rc = precond_apply_v<V>(c, r, z, s);
     if (rc) return rc;
     int cur = S_RZ0;
     dot(r, z, S + cur);
-    k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
+    k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
     while (it < maxit) {
-      err = f32_apply
-                ? lor_launch_apply_f32_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s)
-                : lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
+      if constexpr (VF) {
+        err = lor_launch_apply_f32v_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s);
+      } else {
+        err = f32_apply
+                  ? lor_launch_apply_f32_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s)
+                  : lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
+      }
       if (err != cudaSuccess) return fail(c, err, "pcg apply");
       dot(p, q, S + S_PQ);
       const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
-      err = f64 ? pcg_update<double>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s)
-                : pcg_update<float>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s);
+      err = f64 ? pcg_update<double, V>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s)
+                : pcg_update<float, V>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s);
       if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (err == cudaSuccess) err = queue_status_read(c, s);
       if (err == cudaSuccess) err = cudaStreamSynchronize(s);
@@ -820,12 +874,21 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
         break;
       }
       if (rel <= trigger) {
-        // confirm on the true residual b - A x
-        err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
-        if (err == cudaSuccess) {
-          k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
-          dot(r, r, S + S_RR);
-          err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+        // confirm on the true residual b - A x (FP64 operator)
+        if constexpr (VF) {
+          err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, ax64, s);
+          if (err == cudaSuccess) {
+            k_residual_norm<V><<<g_dot64, kThreads, 0, s>>>(n, b, ax64, r, pcg_partials(c), c->red_count, S + S_RR);
+            lor_count_launch();
+            err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+          }
+        } else {
+          err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
+          if (err == cudaSuccess) {
+            k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
+            dot(r, r, S + S_RR);
+            err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+          }
         }
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return fail(c, err, "pcg");
@@ -843,17 +906,17 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
           ++nrep;
         }
         // continue from the true residual: precondition it afresh
-        rc = lor_precond_apply_impl(c, r, z, s);
+        rc = precond_apply_v<V>(c, r, z, s);
         if (rc) return rc;
         dot(r, z, S + nxt);
         restarted = true;
       }
       if (!restarted && mode == 3) {
-        err = f64 ? pcg_precond_rest<double>(c, c->vals64, c->dinv64, r, z, S + nxt, s)
-                  : pcg_precond_rest<float>(c, c->vals32, c->dinv32, r, z, S + nxt, s);
+        err = f64 ? pcg_precond_rest<double, V>(c, c->vals64, c->dinv64, r, z, S + nxt, s)
+                  : pcg_precond_rest<float, V>(c, c->vals32, c->dinv32, r, z, S + nxt, s);
         if (err != cudaSuccess) return fail(c, err, "pcg precond");
       }
-      k_pcg_direction<<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q); lor_count_launch();
+      k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q); lor_count_launch();
       cur = nxt;
     }
     err = cudaGetLastError();
@@ -870,7 +933,7 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
 
 int lor_pcg_impl(lor_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
                  cudaStream_t s) {
-  return pcg_core(c, b, x, rtol, maxit, false, true, 0.0, iters, relres, nullptr, s);
+  return pcg_core<double>(c, b, x, rtol, maxit, false, true, 0.0, iters, relres, nullptr, s);
 }
 
 // Iterative refinement: the outer residual b - A x with the FP64 operator,
@@ -884,7 +947,7 @@ int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double 
     // residual each time the latter has fallen by inner_rtol
     int it = 0, nrep = 0;
     double rel = 0.0;
-    rc = pcg_core(c, b, x, rtol, maxit, true, true, inner_rtol, &it, &rel, &nrep, s);
+    rc = pcg_core<float>(c, b, x, rtol, maxit, true, true, inner_rtol, &it, &rel, &nrep, s);
     if (outer_iters) *outer_iters = it > 0 ? nrep + 1 : 0;
     if (inner_iters) *inner_iters = it;
     if (relres) *relres = rel;
@@ -898,9 +961,10 @@ int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double 
   double* S = c->red + LOR_RED_BLOCKS;
   double* hs = c->h_scalar;
   const int g = grid_rows(n);
-  const int g_dot = pcg_grid(k_pcg_dot);
+  const int g_dot = pcg_grid(k_pcg_dot<double>);
   auto norm2 = [&](const double* a, double* out) -> cudaError_t {
-    k_pcg_dot<<<g_dot, kThreads, 0, s>>>(n, a, a, pcg_partials(c), c->red_count, S + S_IR); lor_count_launch();
+    k_pcg_dot<double><<<g_dot, kThreads, 0, s>>>(n, a, a, pcg_partials(c), c->red_count, S + S_IR);
+    lor_count_launch();
     cudaError_t e = cudaMemcpyAsync(hs, S + S_IR, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     *out = hs[0];
@@ -928,7 +992,7 @@ int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double 
     prev = rel;
     int it = 0;
     double rin = 0.0;
-    rc = pcg_core(c, rr, dd, inner_rtol, maxit - inner, true, false, 0.0, &it, &rin, nullptr, s);
+    rc = pcg_core<double>(c, rr, dd, inner_rtol, maxit - inner, true, false, 0.0, &it, &rin, nullptr, s);
     if (rc != LOR_OK && rc != LOR_ENOCONV) return rc;
     inner += it;
     ++outer;

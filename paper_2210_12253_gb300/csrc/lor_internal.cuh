@@ -271,6 +271,9 @@ cudaError_t lor_launch_apply_f32(const LorMesh& m, const LorTables& T, const flo
                                  const double* x, double* y, cudaStream_t s);
 cudaError_t lor_launch_apply_f32_accumulate(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
                                             const double* x, double* y, cudaStream_t s);
+// ... and with FP32 x and y (FP32 atomics; y initialised by the caller).
+cudaError_t lor_launch_apply_f32v_accumulate(const LorMesh& m, const LorTables& T, const float* Dq, const float* Mq,
+                                             const float* x, float* y, cudaStream_t s);
 // b = (float) a, n elements
 cudaError_t lor_launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
