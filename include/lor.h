@@ -331,10 +331,12 @@ int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int
  *               of lor_precond_setup (dots and recurrences FP64)
  *             x += d
  *   LOR_IR_REPLACE (residual replacement, van der Vorst and Ye 2000): one PCG
- *     on the FP32 operator; whenever its recurrence residual has fallen by
- *     inner_rtol since the last outer step, the FP64 residual b - A_p x is
- *     formed, the solve stops if it meets rtol, and otherwise it replaces the
- *     recurrence residual (the search direction is kept).
+ *     on the FP32 operator whose vectors r, z, p, q are FP32 (x stays FP64;
+ *     dot products are summed in FP64 across threads); whenever its
+ *     recurrence residual has fallen by inner_rtol since the last outer step,
+ *     the FP64 residual b - A_p x is formed, the solve stops if it meets rtol,
+ *     and otherwise it replaces the recurrence residual (rounded to FP32; the
+ *     search direction is kept).
  * Either way the stopping residual is always the FP64 one, while the inner
  * iterations run the FP32 operator (on this GPU the FP32 pipe is about 60x
  * the FP64 one).  maxit bounds the inner iterations over all outer steps;
