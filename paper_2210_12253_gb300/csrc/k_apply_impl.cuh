@@ -90,6 +90,12 @@ struct Lay {
   static constexpr int TFF = Z::Q * NH4;  // BE, BO, DE, DO: [g][i], g < q
   static constexpr int TFT = NH4 * QH4;   // BEt, BOt, DEt, DOt: [i][g], g < q/2
   static constexpr int TABLES = F32 ? 4 * TFF + 4 * TFT + 2 * Q4 + 2 * NH4 : Z::TABLES;
+  // elements per CTA and CTA size of the apply: FP32 takes half the FP64
+  // count up to p = 8 (smaller CTAs, the same warps per SM, shorter
+  // barriers: 8-10% faster at p = 6..8, neutral below); at p = 9, 10 one
+  // element per CTA leaves too few warps, so the FP64 count stays
+  static constexpr int E = F32 && P <= 8 ? (Z::E + 1) / 2 : Z::E;
+  static constexpr int T = ((E * Z::Q * Z::Q + 31) / 32) * 32;
 };
 
 // Folded tables: BE = (B[g][i] + B[g][n-1-i]) / 2, BO = (B[g][i] - B[g][n-1-i]) / 2
@@ -722,12 +728,12 @@ __device__ __forceinline__ void stage_x_t(const LorMesh& m, const Tab<P, R>& t, 
 }
 
 template <int P, bool MASS, bool GEN, typename R, typename XV>
-__global__ void __launch_bounds__(Sz<P>::T) k_apply(LorMesh m, LorTables T, const R* __restrict__ Dq,
+__global__ void __launch_bounds__(Lay<P, R>::T) k_apply(LorMesh m, LorTables T, const R* __restrict__ Dq,
                                                     const R* __restrict__ Mq, const XV* __restrict__ x,
                                                     XV* __restrict__ y) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
-  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Lay<P, R>::E;
   extern __shared__ __align__(16) unsigned char apply_smem[];
   R* sm = reinterpret_cast<R*>(apply_smem);
   const Tab<P, R> t = load_tables<P>(T, sm);
@@ -861,12 +867,12 @@ cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* 
                     cudaStream_t s) {
   using Z = Sz<P>;
   using L = Lay<P, R>;
-  const size_t bytes = sizeof(R) * (L::TABLES + (size_t)Z::E * L::PER_ELEM);
+  const size_t bytes = sizeof(R) * (L::TABLES + (size_t)L::E * L::PER_ELEM);
   static unsigned mask = 0;
   cudaError_t err = configure(k_apply<P, MASS, GEN, R, XV>, bytes, &mask);
   if (err != cudaSuccess) return err;
-  const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply<P, MASS, GEN, R, XV><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
+  const int64_t blocks = (m.nel + L::E - 1) / L::E;
+  k_apply<P, MASS, GEN, R, XV><<<(unsigned)blocks, L::T, bytes, s>>>(m, T, Dq, Mq, x, y); lor_count_launch();
   return cudaGetLastError();
 }
 
