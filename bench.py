@@ -7,8 +7,10 @@ One step = one pass of the hot path over the 16^3-element, p = 4 workload
   high-order apply -> Chebyshev-Jacobi preconditioner (degree 3, FP64, with
   its diagonal) -> backward of the apply (gx and gkappa).
 value = DOFs processed per second over the timed steps (GDOF/s), summed over
-ranks.  The PCG time to 1e-8 (FP64 vs mixed precision) is measured on the
-32^3-element, p = 6 workload (7,189,057 DOFs) and reported under "pcg"; the
+ranks.  The PCG time to 1e-8 (FP64 vs mixed precision, and the
+mixed-precision refinement whose iterations run an FP32 operator) is
+measured on the 32^3-element, p = 6 workload (7,189,057 DOFs) and reported
+under "pcg" (with the FP64 and FP32 applies timed alone); the
 adjoint gradient dJ/dtheta (forward solve, adjoint solve, gradient kernel) on
 the 24^3-element, p = 5 workload under "gradient"; the same step with the
 reaction term of the definite Helmholtz problem under "helmholtz"; the
