@@ -89,7 +89,7 @@ def test_dof_coordinates_undistorted():
 # ------------------------------------------------------------------ HO operator
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_sum_factorisation_equals_brute_force(p):
-    mesh = jittered(2, 1, 2, seed=p)
+    mesh = jittered(2, 2, 2, seed=p)  # one interior vertex: a genuinely distorted mesh
     q = p + 2
     kappa = np.exp(np.random.default_rng(10 + p).standard_normal((mesh.nel, q ** 3)))
     A = dense_ho(mesh, p, q, kappa)
@@ -192,7 +192,7 @@ def test_constants_in_kernel_and_symmetry():
 def test_backward_against_brute_force():
     """gx = A gy and <gkappa, dk> = gy^T A(dk) x with x, gy masked on the
     boundary, A(dk) the brute-force matrix with coefficient dk."""
-    mesh = jittered(2, 1, 2, seed=9)
+    mesh = jittered(2, 2, 2, seed=9)  # distorted: the metric has off-diagonal entries
     p, q = 3, 5
     rng = np.random.default_rng(8)
     kap = np.exp(rng.standard_normal((mesh.nel, q ** 3)))

@@ -47,6 +47,21 @@ MUTATIONS = [
      "values[2 * e] = -1.0;", "values[2 * e] = 1.0;"),
     ("power iteration without the diagonal scaling",
      "for (int64_t i = 0; i < n; ++i) w[i] /= d[i];", ""),
+    ("load vector without detJ",
+     "s += wg[g0] * wg[g1] * wg[g2] * detJ[e * nq3 + g] * fv * L[g0][i] * L[g1][j] * L[g2][k];",
+     "s += wg[g0] * wg[g1] * wg[g2] * fv * L[g0][i] * L[g1][j] * L[g2][k];"),
+    ("kappa_s bins shifted by half an interval",
+     "      if (gll[m] < xg[g]) ++c;",
+     "      if (0.5 * (gll[m] + gll[m - 1]) < xg[g]) ++c;"),
+    ("kappa gradient with a wrong metric entry",
+     "          double v1 = Gq[1] * a + Gq[3] * b + Gq[4] * c;",
+     "          double v1 = Gq[2] * a + Gq[3] * b + Gq[4] * c;"),
+    ("discrete gradient head on the wrong axis",
+     "          colidx[2 * e + 1] = tail + stride[d];",
+     "          colidx[2 * e + 1] = tail + stride[(d + 1) % 3];"),
+    ("LOR Dirichlet diagonal left at zero",
+     "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
+     "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
 ]
 
 
