@@ -37,7 +37,7 @@ def test_discrete_gradient_bit_exact(dims, p):
     op.close()
 
 
-@pytest.mark.parametrize("dims,p", [((2, 3, 2), 1), ((3, 2, 2), 4), ((1, 2, 1), 7)])
+@pytest.mark.parametrize("dims,p", [((2, 3, 2), 1), ((3, 2, 2), 4), ((2, 2, 2), 7)])
 def test_vertex_coordinates(dims, p):
     prob, op = make_op(dims, p)
     xyz = op.vertex_coordinates().cpu().numpy()
