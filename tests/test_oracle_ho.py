@@ -215,6 +215,34 @@ def test_backward_against_brute_force():
     assert abs(gk[e, g] - gm @ dense_ho(mesh, p, q, dk) @ xm) < 1e-12 * max(1.0, abs(gk[e, g]))
 
 
+@pytest.mark.parametrize("p", [2, 4])
+def test_load_vector_variable_source_closed_form(p):
+    """f = x at the Gauss points of the unit cube and u = x(1-x)y(1-y)z(1-z)
+    interpolated at the GLL nodes (exact for p >= 2, zero on the boundary):
+    sum_i b_i u_i = int f u = (1/12)(1/6)(1/6) = 1/432, exact at q = p+2."""
+    nex, ney, nez = 2, 3, 2
+    q = p + 2
+    mesh = oracle.Mesh(nex, ney, nez, unit_cube_vertices(nex, ney, nez))
+    xg, _ = np.polynomial.legendre.leggauss(q)
+    f = np.zeros((mesh.nel, q ** 3))
+    for ez in range(nez):
+        for ey in range(ney):
+            for ex in range(nex):
+                e = ex + nex * (ey + ney * ez)
+                for g in range(q ** 3):
+                    f[e, g] = (ex + 0.5 * (xg[g % q] + 1.0)) / nex
+    b = oracle.load_vector(mesh, p, q, f)
+    t = gll_nodes(p)
+    def coords(ne):
+        c = np.zeros(ne * p + 1)
+        for e in range(ne):
+            c[e * p:e * p + p + 1] = (e + 0.5 * (t + 1.0)) / ne
+        return c
+    X, Y, Z = coords(nex), coords(ney), coords(nez)
+    u = np.einsum("k,j,i->kji", Z * (1 - Z), Y * (1 - Y), X * (1 - X)).ravel()
+    assert abs(b @ u - 1.0 / 432.0) < 1e-14
+
+
 @pytest.mark.parametrize("p", [1, 3])
 def test_load_vector_unit_source_closed_form(p):
     """f = 1 on box elements: b_i = prod_d (sum over elements of (h_d/2) w_i^GLL)."""

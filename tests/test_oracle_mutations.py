@@ -59,6 +59,13 @@ MUTATIONS = [
     ("discrete gradient head on the wrong axis",
      "          colidx[2 * e + 1] = tail + stride[d];",
      "          colidx[2 * e + 1] = tail + stride[(d + 1) % 3];"),
+    ("load vector reads f at the neighbouring Gauss point",
+     "double fv = f ? f[e * nq3 + g] : 1.0;", "double fv = f ? f[e * nq3 + (g + 1) % nq3] : 1.0;"),
+    ("apply with a wrong metric entry",
+     "gr[3 * g + 1] = k * (Gq[1] * a + Gq[3] * b + Gq[4] * c);", "gr[3 * g + 1] = k * (Gq[2] * a + Gq[3] * b + Gq[4] * c);"),
+    ("sub-hex coefficient of the transposed sub-hex",
+     "bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + a + p * (b + p * c)],",
+     "bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + b + p * (a + p * c)],"),
     ("LOR Dirichlet diagonal left at zero",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
