@@ -66,6 +66,10 @@ MUTATIONS = [
     ("sub-hex coefficient of the transposed sub-hex",
      "bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + a + p * (b + p * c)],",
      "bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + b + p * (a + p * c)],"),
+    ("CSR diagonal taken from the row's first entry",
+     "      if (colidx[j] == i) d[i] += values[j];", "      if (j == rowptr[i]) d[i] += values[j];"),
+    ("PCG step length against p.p",
+     "double alpha = rz / dot(N, pv, Ap);", "double alpha = rz / dot(N, pv, pv);"),
     ("LOR Dirichlet diagonal left at zero",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
