@@ -328,7 +328,8 @@ int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int
  *             stop if |r|/|b| <= rtol
  *             solve A_p d = r by PCG from d_0 = 0 until |r_k| <= inner_rtol |r|,
  *               with the FP32 operator of lor_apply_f32 and the preconditioner
- *               of lor_precond_setup (dots and recurrences FP64)
+ *               of lor_precond_setup (FP32 vectors, d and the dot products
+ *               summed in FP64)
  *             x += d
  *   LOR_IR_REPLACE (residual replacement, van der Vorst and Ye 2000): one PCG
  *     on the FP32 operator whose vectors r, z, p, q are FP32 (x stays FP64;

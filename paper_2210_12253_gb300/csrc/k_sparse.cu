@@ -992,7 +992,7 @@ int lor_pcg_ir_impl(lor_ctx* c, const double* b, double* x, double rtol, double 
     prev = rel;
     int it = 0;
     double rin = 0.0;
-    rc = pcg_core<double>(c, rr, dd, inner_rtol, maxit - inner, true, false, 0.0, &it, &rin, nullptr, s);
+    rc = pcg_core<float>(c, rr, dd, inner_rtol, maxit - inner, true, false, 0.0, &it, &rin, nullptr, s);
     if (rc != LOR_OK && rc != LOR_ENOCONV) return rc;
     inner += it;
     ++outer;
