@@ -73,3 +73,29 @@ def test_binding_constants_match_the_header():
     for name, value in pairs:
         assert hasattr(B, name), name
         assert getattr(B, name) == int(value), name
+
+
+def test_every_entry_point_rejects_a_null_context(libpath):
+    """The header's error contract on the host side: every call that takes a
+    context returns LOR_EINVAL for a NULL one (before touching the GPU), and
+    lor_destroy(NULL) is a no-op."""
+    from paper_2210_12253_gb300 import lor as B
+    L = B.load_library(libpath)
+    skip = {"lor_last_error", "lor_launch_count", "lor_create", "lor_destroy"}
+    checked = 0
+    for name in B.EXPORTED:
+        if name in skip:
+            continue
+        fn = getattr(L, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+                args.append(0)
+            elif t is ctypes.c_double:
+                args.append(0.0)
+            else:
+                args.append(None)  # pointers, the context and the stream
+        assert fn(*args) == B.LOR_EINVAL, name
+        checked += 1
+    assert checked >= 20
+    assert L.lor_destroy(None) == B.LOR_OK
