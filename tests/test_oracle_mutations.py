@@ -70,6 +70,12 @@ MUTATIONS = [
      "      if (colidx[j] == i) d[i] += values[j];", "      if (j == rowptr[i]) d[i] += values[j];"),
     ("PCG step length against p.p",
      "double alpha = rz / dot(N, pv, Ap);", "double alpha = rz / dot(N, pv, pv);"),
+    ("Chebyshev interval centre taken as its half-width",
+     "double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;",
+     "double theta = 0.5 * (hi - lo), delta = 0.5 * (hi - lo), sigma = theta / delta;"),
+    ("transposed y stage pairs the derivative with the wrong component",
+     "          s1 += D[g1 * n + j] * T1[(k * q + g1) * q + g0] + B[g1 * n + j] * T2[(k * q + g1) * q + g0];",
+     "          s1 += B[g1 * n + j] * T1[(k * q + g1) * q + g0] + D[g1 * n + j] * T2[(k * q + g1) * q + g0];"),
     ("LOR Dirichlet diagonal left at zero",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
