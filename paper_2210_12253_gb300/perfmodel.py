@@ -37,23 +37,39 @@ def sumfact_fma(p):
     return 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
 
 
-def setup_flops_per_point():
-    """Adjugate (3 cross products, 27), det (5), weight (2), kappa w / det (2),
-    six scaled dot products (36)."""
-    return 72
+def jacobian_columns_flops(L):
+    """Per element, the three Jacobian columns of the trilinear map at L x L
+    coordinate pairs (each column is bilinear in the two other coordinates):
+    36 half edge vectors (2 each), then per column, component and first
+    coordinate two edge interpolations (6) and L second-coordinate ones (3)."""
+    return 72 + 9 * L * (6 + 3 * L)
 
 
-def assemble_flops_per_subhex():
-    """One sub-hex block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form, as
-    the kernel evaluates it: per Gauss point adjugate (27), det (5), 1/det
-    (1), the six scaled metric entries (42) = 75 x 8; six 8-point Walsh
-    transforms, 24 additions each less the 12 whose outputs the diagonal
-    entries never use (108); the 84-term modal block (168); the
-    modal-to-nodal transform per axis, 8 additions for each of the 6
-    off-diagonal 2x2 blocks and 6 flops for each of the 4 diagonal ones
-    (3 x 72 = 216); kappa_s and scales (20).  (The direct nodal formula costs
-    3,936 flops per sub-hex.)"""
-    return 8 * 75 + 108 + 168 + 216 + 20
+def setup_flops_per_element(p):
+    """Jacobian columns at the q x q Gauss pairs, then per Gauss point the
+    adjugate rows (3 cross products, 27), det (5), its reciprocal (1), the
+    weight product (2), kappa w / det (2) and the six scaled dot products
+    (36): 73."""
+    q = p + 2
+    return jacobian_columns_flops(q) + 73 * q ** 3
+
+
+def assemble_flops_per_element(p):
+    """Jacobian columns at the 2p x 2p sub-hex Gauss pairs; per sub-hex, one
+    8x8 block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form, as the kernel
+    evaluates it: per Gauss point adjugate (27), det (5), 1/det (1), the six
+    scaled metric entries (42) = 75 x 8; six 8-point Walsh transforms, 24
+    additions each less the 12 whose outputs the diagonal entries never use
+    (108); the 84-term modal block (168); the modal-to-nodal transform per
+    axis, 8 additions for each of the 6 off-diagonal 2x2 blocks and 6 flops
+    for each of the 4 diagonal ones (3 x 72 = 216); the six scales F_ab (13).
+    Per element the kappa_s averages: 3 per high-order Gauss point and one
+    weight product per (y, z) point pair of each sub-hex column (p q^2).
+    (Evaluated directly, G grad(phi_j) and 36 dot products at each Gauss
+    point, the block costs 8 x (144 + 216) = 2,880 flops instead of the 492 of
+    the transforms, the modal block and the sandwich.)"""
+    q = p + 2
+    return jacobian_columns_flops(2 * p) + p ** 3 * (8 * 75 + 108 + 168 + 216 + 13) + 3 * q ** 3 + p * q * q
 
 
 def apply_flops_per_element(p):
@@ -64,8 +80,9 @@ def apply_flops_per_element(p):
 
 def backward_flops_per_element(p):
     """Two forward passes (x and gy), one transpose pass, and per point the
-    D product (15), the gkappa contraction x^T (D gy) / kappa (21)."""
-    return 6 * sumfact_fma(p) + 36 * (p + 2) ** 3
+    D product (15, shared by gx and gkappa) and gkappa = grad(x) . (D grad(gy))
+    / kappa (6)."""
+    return 6 * sumfact_fma(p) + 21 * (p + 2) ** 3
 
 
 def reaction_extra_apply_flops_per_element(p):
@@ -75,9 +92,11 @@ def reaction_extra_apply_flops_per_element(p):
     return 4 * q ** 3 * n + q ** 3
 
 
-def reaction_extra_assemble_flops_per_subhex():
-    """W(g) (8), its Walsh transform (24), 36 modal mass terms (72)."""
-    return 8 + 24 + 72
+def reaction_extra_assemble_flops_per_element(p):
+    """Per sub-hex: the scale beta_s r_a r_b r_c / 64 (4), W(g) (8), its Walsh
+    transform (24), 36 modal mass terms (72); per element the beta_s averages
+    (2 per high-order Gauss point, sharing the kappa_s weights)."""
+    return p ** 3 * (4 + 8 + 24 + 72) + 2 * (p + 2) ** 3
 
 
 def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
@@ -86,9 +105,9 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
     nq = nel * q ** 3
     nsub = nel * p ** 3
     if kind == "setup":
-        return setup_flops_per_point() * nq, 64 * nq  # kappa in, D (48) + kappa copy out
+        return setup_flops_per_element(p) * nel, 64 * nq  # kappa in, D (48) + kappa copy out
     if kind == "assemble":
-        return assemble_flops_per_subhex() * nsub, vbytes * nnz + 8 * nq
+        return assemble_flops_per_element(p) * nel, vbytes * nnz + 8 * nq
     if kind == "apply":
         return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
     if kind == "apply_f32":
@@ -101,7 +120,7 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
         return 8 * nq, 24 * nq
     if kind == "assemble_helmholtz":
         f, b = kernel_work("assemble", p, ndof, nel, nnz, vbytes)
-        return f + reaction_extra_assemble_flops_per_subhex() * nsub, b + 8 * nq
+        return f + reaction_extra_assemble_flops_per_element(p) * nel, b + 8 * nq
     if kind == "apply_helmholtz":
         f, b = kernel_work("apply", p, ndof, nel, nnz, vbytes)
         return f + reaction_extra_apply_flops_per_element(p) * nel, b + 8 * nq
