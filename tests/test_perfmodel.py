@@ -88,7 +88,7 @@ def one_element(p, seed):
 # Sum factorisation (the HO apply and its backward).
 # u is indexed i + n (j + n k), points qx + q (qy + q qz).
 # ---------------------------------------------------------------------------
-def grad_ref(u, B, D):
+def grad_ref(u, B, D, want_bb=False):
     q, n = B.shape
     U = lambda i, j, k: u[i + n * (j + n * k)]
     Bu = {(k, j, a): acc(B[a], [U(i, j, k) for i in range(n)]) for k in range(n) for j in range(n) for a in range(q)}
@@ -108,10 +108,12 @@ def grad_ref(u, B, D):
                 gx.append(acc(B[c], [BD[k, b, a] for k in range(n)]))
                 gy.append(acc(B[c], [DB[k, b, a] for k in range(n)]))
                 gz.append(acc(D[c], [BB[k, b, a] for k in range(n)]))
-    return gx, gy, gz
+    return (gx, gy, gz, BB) if want_bb else (gx, gy, gz)
 
 
-def grad_ref_t(vx, vy, vz, B, D):
+def grad_ref_t(vx, vy, vz, B, D, vm=None):
+    """The transposed pass; vm (reaction term): values at the points that
+    B_z^T adds into the same slot as the z-derivative part."""
     q, n = B.shape
     P = lambda a, b, c: a + q * (b + q * c)
     tx, ty, tz = {}, {}, {}
@@ -120,7 +122,11 @@ def grad_ref_t(vx, vy, vz, B, D):
             for a in range(q):
                 tx[k, b, a] = acc(B[:, k], [vx[P(a, b, c)] for c in range(q)])
                 ty[k, b, a] = acc(B[:, k], [vy[P(a, b, c)] for c in range(q)])
-                tz[k, b, a] = acc(D[:, k], [vz[P(a, b, c)] for c in range(q)])
+                if vm is None:
+                    tz[k, b, a] = acc(D[:, k], [vz[P(a, b, c)] for c in range(q)])
+                else:
+                    tz[k, b, a] = acc(list(D[:, k]) + list(B[:, k]),
+                                      [vz[P(a, b, c)] for c in range(q)] + [vm[P(a, b, c)] for c in range(q)])
     sB, sD = {}, {}
     for k in range(n):
         for j in range(n):
@@ -171,6 +177,29 @@ def test_apply_flops_evaluate_the_oracle_apply(p):
     y = grad_ref_t([t[0] for t in v], [t[1] for t in v], [t[2] for t in v], B, D)
     assert count(y) == pm.apply_flops_per_element(p)
     ref = oracle.ho_apply(mesh, p, q, kappa, x, dirichlet=False)
+    np.testing.assert_allclose(val(y), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_apply_reaction_flops_evaluate_the_oracle_apply(p):
+    """The reaction term's share: B_z on the BB lines the forward pass already
+    holds, the scaling by M = beta w detJ, B_z^T into the transposed pass."""
+    q, n = p + 2, p + 1
+    mesh, _, kappa, rng = one_element(p, 70 + p)
+    beta = np.exp(rng.standard_normal(q ** 3))
+    B, D = oracle.basis_1d(p, q)
+    detJ, G = oracle.geometry(mesh, q)
+    _, wg = oracle.gauss_legendre(q)
+    Dq = kappa[:, None] * G[0]
+    M = beta * np.einsum("c,b,a->cba", wg, wg, wg).ravel() * detJ[0]
+    x = rng.standard_normal(n ** 3)
+    gx, gy, gz, BB = grad_ref(leaves(x), B, D, want_bb=True)
+    v = [metric_product(Dq[pt], (gx[pt], gy[pt], gz[pt])) for pt in range(q ** 3)]
+    um = [acc(B[c], [BB[k, b, a] for k in range(n)]) * M[a + q * (b + q * c)]
+          for c in range(q) for b in range(q) for a in range(q)]
+    y = grad_ref_t([t[0] for t in v], [t[1] for t in v], [t[2] for t in v], B, D, vm=um)
+    assert count(y) == pm.apply_flops_per_element(p) + pm.reaction_extra_apply_flops_per_element(p)
+    ref = oracle.ho_apply(mesh, p, q, kappa, x, dirichlet=False, beta=beta)
     np.testing.assert_allclose(val(y), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
