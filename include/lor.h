@@ -98,8 +98,9 @@ const char* lor_last_error(const lor_ctx* ctx);
  * vertices (p_g = 1); the LOR mesh (Section 2.1) splits each element at the
  * Gauss-Lobatto points into p^3 sub-hexes.  Checks every Jacobian at the
  * Gauss points used by the high-order operator and by the LOR assembly and
- * returns LOR_EGEOM if one is <= 0.  Synchronises the stream.  *out receives
- * the context (NULL on failure). */
+ * returns LOR_EGEOM if one is <= 0.  LOR_EINVAL for p outside [1, LOR_MAX_P],
+ * an empty mesh or 2^31 or more DOFs (the CSR column indices are int32).
+ * Synchronises the stream.  *out receives the context (NULL on failure). */
 int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, void* stream);
 
 /* Create a context on a general conforming hex mesh given in the
@@ -117,7 +118,9 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
  * smoother read the explicit pattern.  lor_lor_mesh is for structured meshes
  * only (LOR_ESTATE); lor_discrete_gradient numbers the LOR edges of a general
  * mesh itself (see there).
- * LOR_EINVAL for a map entry out of range, LOR_EGEOM for detJ <= 0.  All
+ * LOR_EINVAL for a map entry out of range, 2^31 or more DOFs or more than
+ * 8.7e14 elements (the byte sizes of the element arrays would overflow
+ * int64), LOR_EGEOM for detJ <= 0.  All
  * input arrays are device memory, copied.  Synchronises the stream. */
 int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const double* d_corners,
                        const int64_t* d_elem_dofs, const uint8_t* d_ess, void* stream);

@@ -247,7 +247,8 @@ int lor_create(lor_ctx** out, const lor_config* cfg, const double* d_vertices, v
   if (cfg->nex < 1 || cfg->ney < 1 || cfg->nez < 1) return set_err(nullptr, LOR_EINVAL, "lor_create: empty mesh");
   const int64_t p = cfg->p;
   const int64_t nx = cfg->nex * p + 1, ny = cfg->ney * p + 1, nz = cfg->nez * p + 1;
-  if (nx * ny * nz >= (int64_t(1) << 31))
+  const int64_t lim = int64_t(1) << 31;  // each factor bounded before the next product: no int64 overflow
+  if (nx >= lim || ny >= lim || nz >= lim || nx * ny >= lim || nx * ny * nz >= lim)
     return set_err(nullptr, LOR_EINVAL, "lor_create: more than 2^31-1 DOFs (int32 column indices)");
   lor_ctx* c = new (std::nothrow) lor_ctx();
   if (!c) return set_err(nullptr, LOR_ENOMEM, "lor_create: host allocation failed");
@@ -315,6 +316,8 @@ int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const do
   if (nel < 1 || ndof < 1) return set_err(nullptr, LOR_EINVAL, "lor_create_general: empty mesh");
   if (ndof >= (int64_t(1) << 31))
     return set_err(nullptr, LOR_EINVAL, "lor_create_general: more than 2^31-1 DOFs (int32 column indices)");
+  if (nel > (INT64_MAX / 8) / ((int64_t)(LOR_MAX_P + 1) * (LOR_MAX_P + 1) * (LOR_MAX_P + 1)))
+    return set_err(nullptr, LOR_EINVAL, "lor_create_general: element count overflows the byte size of its arrays");
   lor_ctx* c = new (std::nothrow) lor_ctx();
   if (!c) return set_err(nullptr, LOR_ENOMEM, "lor_create_general: host allocation failed");
   c->cfg.p = p;

@@ -47,12 +47,19 @@ def test_create_error_without_context_is_reported(libpath):
     from paper_2210_12253_gb300 import lor as B
     L = B.load_library(libpath)
     h = ctypes.c_void_p()
-    for p, ne in ((0, 2), (B.LOR_MAX_P + 1, 2), (3, 0)):
-        cfg = B.lor_config(p, ne, ne, ne)
+    # the last two: 2^31 DOFs exactly, and 2^22 DOFs per axis, whose product wraps to 0 in int64
+    for p, nes in ((0, (2, 2, 2)), (B.LOR_MAX_P + 1, (2, 2, 2)), (3, (0, 0, 0)), (1, (2047, 1023, 1023)),
+                   (1, ((1 << 22) - 1,) * 3)):
+        cfg = B.lor_config(p, *nes)
         rc = L.lor_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None)
         assert rc == B.LOR_EINVAL
         assert L.lor_last_error(None)
+        assert not h.value
     assert L.lor_create(None, None, None, None) == B.LOR_EINVAL
+    fake = ctypes.c_void_p(16)  # never dereferenced: the sizes are rejected first
+    for p, nel, ndof in ((0, 8, 27), (3, 0, 27), (3, 8, 1 << 31), (3, 1 << 60, 1000)):
+        rc = L.lor_create_general(ctypes.byref(h), p, nel, ndof, fake, fake, None, None)
+        assert rc == B.LOR_EINVAL and not h.value
 
 
 def test_product_path_needs_cuda_tensors(libpath):
