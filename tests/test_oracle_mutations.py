@@ -76,6 +76,24 @@ MUTATIONS = [
     ("transposed y stage pairs the derivative with the wrong component",
      "          s1 += D[g1 * n + j] * T1[(k * q + g1) * q + g0] + B[g1 * n + j] * T2[(k * q + g1) * q + g0];",
      "          s1 += B[g1 * n + j] * T1[(k * q + g1) * q + g0] + D[g1 * n + j] * T2[(k * q + g1) * q + g0];"),
+    ("Gauss-Legendre weight without the 1 - x^2 factor",
+     "    w[i] = 2.0 / ((1.0 - t * t) * dP * dP);",
+     "    w[i] = 2.0 / (dP * dP);"),
+    ("Lagrange derivative without the 1/(x_j - x_l) factor",
+     "      double term = 1.0 / (nodes[j] - nodes[l]);",
+     "      double term = 1.0;"),
+    ("dense brute force maps reference gradients by J^-1 instead of J^-T",
+     "grad[3 * a + d] = Ji[0][d] * gr[0] + Ji[1][d] * gr[1] + Ji[2][d] * gr[2];",
+     "grad[3 * a + d] = Ji[d][0] * gr[0] + Ji[d][1] * gr[1] + Ji[d][2] * gr[2];"),
+    ("selected LOR rows take the sub-hex row with y and z swapped",
+     "          int rloc = (int)(I - sa) + 2 * (int)(J - sb) + 4 * (int)(Kk - sc);",
+     "          int rloc = (int)(I - sa) + 2 * (int)(Kk - sc) + 4 * (int)(J - sb);"),
+    ("DOF coordinates with the y and z reference coordinates swapped",
+     "              double xi[3] = {gll[i], gll[j], gll[k]}, J[3][3];",
+     "              double xi[3] = {gll[i], gll[k], gll[j]}, J[3][3];"),
+    ("SpMV reads x at the row instead of the column",
+     "    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) s += values[j] * x[colidx[j]];",
+     "    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) s += values[j] * x[i];"),
     ("LOR Dirichlet diagonal left at zero",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
