@@ -23,7 +23,9 @@ every mixed-precision result against its FP64 counterpart under
 
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
-`--impl reference` it times the CPU oracle instead (rank 0 only).
+`--impl reference` it times the CPU oracle instead (rank 0 only), each step
+on a sub-box of the 16^3 p = 4 recipe sized so the whole run takes about
+150 s.
 """
 import argparse
 import json
@@ -1016,7 +1018,13 @@ def run_sweep(args, dev):
 
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
-SAMPLE = "8x8x8 elements, p=4 (35,937 DOFs): the 16^3 p=4 workload's recipe on an 8^3 sub-box (seed 1)"
+REFERENCE_BUDGET_S = 150.0  # the whole --impl reference run (warm-up and timed steps)
+
+
+def sample_desc(ne):
+    n = 4 * ne + 1
+    return ("%dx%dx%d elements, p=4 (%s DOFs): the 16^3 p=4 workload's recipe on a sub-box of %d^3 elements "
+            "(seed 1)" % (ne, ne, ne, format(n ** 3, ","), ne))
 
 
 def oracle_step(sample):
@@ -1033,18 +1041,31 @@ def oracle_step(sample):
     return prob.ndof
 
 
-def make_sample():
+def make_sample(ne=8):
     import numpy as np
 
     import oracle
     from paper_2210_12253_gb300.inputs import make_problem
-    prob = make_problem("sample", 8, 8, 8, 4, seed=1, kappa="lognormal", rhs="normal")
-    mesh = oracle.Mesh(8, 8, 8, prob.vertices)
+    prob = make_problem("sample", ne, ne, ne, 4, seed=1, kappa="lognormal", rhs="normal")
+    mesh = oracle.Mesh(ne, ne, ne, prob.vertices)
     rng = np.random.default_rng(100)
     x, gy = rng.standard_normal(prob.ndof), rng.standard_normal(prob.ndof)
     csr = oracle.lor_assemble(mesh, prob.p, prob.q, prob.kappa, True)
     lam = oracle.power_lambda_max(*csr, np.ones(prob.ndof), 20)
     return prob, mesh, x, gy, lam
+
+
+def reference_box(steps, warmup, step_s, ne=8, budget_s=None):
+    """Edge (in elements) of the sub-box each reference step processes: the
+    largest of ne, ne/2, ... (at least 2) whose estimated run, (steps +
+    warmup) steps at step_s measured on the ne^3 box and scaled by the
+    element count, fits the budget (REFERENCE_BUDGET_S by default)."""
+    budget_s = REFERENCE_BUDGET_S if budget_s is None else budget_s
+    while ne > 2 and (steps + warmup) * step_s > budget_s:
+        nxt = max(2, ne // 2)
+        step_s *= (nxt / ne) ** 3
+        ne = nxt
+    return ne
 
 
 def cpu_baseline(seconds):
@@ -1059,14 +1080,20 @@ def cpu_baseline(seconds):
             break
     dt = time.perf_counter() - t0
     return {"value": dofs / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": SAMPLE + "; %d oracle steps in %.1f s, single-threaded FP64 C" % (n, dt)}
+            "sample": sample_desc(8) + "; %d oracle steps in %.1f s, single-threaded FP64 C" % (n, dt)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    sample = make_sample()
-    for _ in range(args.warmup):
+    sample = make_sample(8)
+    t0 = time.perf_counter()
+    oracle_step(sample)  # the first warm-up step, timed to size the sample
+    ne = reference_box(args.steps, args.warmup, time.perf_counter() - t0)
+    warm = args.warmup - 1
+    if ne != 8:
+        sample, warm = make_sample(ne), args.warmup
+    for _ in range(warm):
         oracle_step(sample)
     t0 = time.perf_counter()
     dofs = 0
@@ -1074,13 +1101,17 @@ def run_reference(args, rank, world):
         dofs += oracle_step(sample)
     dt = time.perf_counter() - t0
     value = dofs / dt / 1e9
+    desc = sample_desc(ne)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": STEP_WORKLOAD + " recipe, bounded sample: " + SAMPLE,
+            "config": {"workload": STEP_WORKLOAD + " recipe, bounded sample: " + desc,
                        "step": "oracle: LOR assembly + HO apply + Chebyshev-Jacobi deg 3 + apply backward"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc + "; the sub-box is the largest of 8^3, 4^3, 2^3 elements whose "
+                                              "%d steps fit about %d s" % (args.steps + args.warmup,
+                                                                           REFERENCE_BUDGET_S)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

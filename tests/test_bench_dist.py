@@ -56,3 +56,35 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
 
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(A(), 1, 2) is None
+
+
+def test_reference_sample_shrinks_with_the_step_count():
+    import bench
+    # 0.2 s per step on the 8^3 box (25 ms on 4^3): up to 750 steps fit 150 s
+    # on 8^3, up to 6,000 on 4^3
+    assert bench.reference_box(10, 3, 0.2) == 8
+    assert bench.reference_box(747, 3, 0.2) == 8
+    assert bench.reference_box(1000, 3, 0.2) == 4
+    assert bench.reference_box(3000, 3, 0.2) == 4
+    assert bench.reference_box(10000, 3, 0.2) == 2
+    assert bench.reference_box(10 ** 6, 3, 0.2) == 2  # never below 2^3
+
+
+def test_reference_arm_line(monkeypatch):
+    """The reference arm's JSON line on rank 0: the contract's keys, the
+    oracle's rate, and zero host-device bytes."""
+    import bench
+
+    class A:
+        steps, warmup = 2, 3
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 0.0)  # forces the smallest sub-box
+    out = bench.run_reference(A(), 0, 1)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["value"] > 0 and out["steps"] == 2
+    assert "2x2x2 elements" in out["config"]["workload"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
