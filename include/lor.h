@@ -64,7 +64,9 @@ enum lor_status {
   LOR_OK = 0,
   LOR_EINVAL = 1,   /* bad argument (size, pointer, degree, coefficient <= 0 or NaN) */
   LOR_EGEOM = 2,    /* a Jacobian determinant <= 0 (inverted or degenerate element) */
-  LOR_ENOMEM = 3,   /* device allocation failed */
+  LOR_ENOMEM = 3,   /* device allocation failed (also injected on the host: an environment
+                       variable LOR_DEVICE_ALLOC_LIMIT=<bytes> caps the device memory a
+                       context's own buffers may hold) */
   LOR_ECUDA = 4,    /* CUDA runtime error (message in lor_last_error) */
   LOR_ENOCONV = 5,  /* PCG hit maxit before reaching the tolerance */
   LOR_ETIMEOUT = 6, /* a bounded device-side wait expired (a bulk copy into shared

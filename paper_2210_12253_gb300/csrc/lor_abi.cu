@@ -13,6 +13,8 @@
 //     (Berrut & Trefethen, SIAM Review 2004) with l_j'/l_j = sum_{m!=j} 1/(t-x_m).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <atomic>
@@ -165,15 +167,33 @@ int cuda_err(lor_ctx* c, cudaError_t e, const char* what) {
   return set_err(c, LOR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Host-side fault injection: with LOR_DEVICE_ALLOC_LIMIT=<bytes> in the
+// environment, an allocation that would take a context's own device buffers
+// above that many bytes fails as a failed cudaMalloc does (LOR_ENOMEM), before
+// any device call.  Unset, empty or not a number: no limit.
+size_t device_alloc_limit() {
+  const char* s = getenv("LOR_DEVICE_ALLOC_LIMIT");
+  if (!s || !*s) return SIZE_MAX;
+  char* end = nullptr;
+  const unsigned long long v = strtoull(s, &end, 10);
+  return *end == 0 ? (size_t)v : SIZE_MAX;
+}
+
 template <typename T>
 int alloc(lor_ctx* c, T** p, size_t count, const char* what) {
   if (*p) return LOR_OK;
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+  const size_t bytes = sizeof(T) * (count ? count : 1), limit = device_alloc_limit();
+  if (c->device_bytes > limit || bytes > limit - c->device_bytes) {
+    *p = nullptr;
+    return set_err(c, LOR_ENOMEM, std::string("device allocation failed: ") + what + " (over LOR_DEVICE_ALLOC_LIMIT)");
+  }
+  cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return set_err(c, LOR_ENOMEM, std::string("device allocation failed: ") + what);
   }
+  c->device_bytes += bytes;
   return LOR_OK;
 }
 
@@ -619,6 +639,7 @@ int lor_precond_setup(lor_ctx* c, int kind, int dtype, int degree, double lo_rat
     if (c->pc_work && c->pc_dtype != dtype) {
       cudaFree(c->pc_work);
       c->pc_work = nullptr;
+      c->device_bytes -= (size_t)(3 * n * (c->pc_dtype == LOR_F64 ? 8 : 4));
     }
     rc = alloc(c, (char**)&c->pc_work, 3 * n * (dtype == LOR_F64 ? 8 : 4), "smoother work");
   }

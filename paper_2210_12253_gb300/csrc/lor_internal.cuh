@@ -55,6 +55,7 @@ struct lor_ctx {
   LorTables T;
   int device;
   std::string err;
+  size_t device_bytes = 0;  // held by the buffers below (allocated through alloc())
   // owned device buffers
   double* verts = nullptr;
   double* Dq = nullptr;        // [nel][6][q^3]: kappa w detJ J^-1 J^-T (00,01,02,11,12,22)

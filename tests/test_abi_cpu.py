@@ -62,6 +62,19 @@ def test_create_error_without_context_is_reported(libpath):
         assert rc == B.LOR_EINVAL and not h.value
 
 
+def test_device_allocation_failure_is_reported(libpath, monkeypatch):
+    """An allocation failure injected on the host (LOR_DEVICE_ALLOC_LIMIT)
+    comes back as LOR_ENOMEM with no context, before any device call."""
+    from paper_2210_12253_gb300 import lor as B
+    L = B.load_library(libpath)
+    h = ctypes.c_void_p()
+    cfg = B.lor_config(2, 2, 2, 2)
+    monkeypatch.setenv("LOR_DEVICE_ALLOC_LIMIT", "64")  # below the 648-byte vertex copy
+    rc = L.lor_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None)
+    assert rc == B.LOR_ENOMEM and not h.value
+    assert b"LOR_DEVICE_ALLOC_LIMIT" in L.lor_last_error(None)
+
+
 def test_product_path_needs_cuda_tensors(libpath):
     from paper_2210_12253_gb300 import LOR
     with pytest.raises(TypeError):

@@ -279,6 +279,30 @@ def test_inverted_element_rejected():
     assert ei.value.code == 2
 
 
+def test_injected_allocation_failure_leaves_the_context_usable(monkeypatch):
+    """LOR_DEVICE_ALLOC_LIMIT makes the context's next allocation fail on the
+    host: the call returns LOR_ENOMEM, and once the limit is lifted the same
+    context assembles and applies as usual."""
+    from paper_2210_12253_gb300 import LOR, LORError
+    from paper_2210_12253_gb300.inputs import make_problem
+    prob = make_problem("t", 2, 2, 2, 3, seed=4, jitter=0.1, kappa="lognormal", rhs="normal")
+    op = LOR(3, 2, 2, 2, t(prob.vertices).contiguous())
+    op.set_coefficient(t(prob.kappa).reshape(-1), check=True)
+    monkeypatch.setenv("LOR_DEVICE_ALLOC_LIMIT", "1")
+    with pytest.raises(LORError) as ei:
+        op.build_pattern_internal()
+    assert ei.value.code == 3 and "LOR_DEVICE_ALLOC_LIMIT" in str(ei.value)
+    monkeypatch.delenv("LOR_DEVICE_ALLOC_LIMIT")
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float64)
+    op.precond_setup("jacobi", torch.float64)
+    mesh = oracle.Mesh(2, 2, 2, prob.vertices)
+    x = np.random.default_rng(3).standard_normal(op.ndof)
+    ref = oracle.ho_apply(mesh, 3, 5, prob.kappa, x)
+    assert np.abs(op.apply(t(x)).cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()
+
+
 def test_bad_coefficient_and_call_order():
     from paper_2210_12253_gb300 import LOR, LORError
     from paper_2210_12253_gb300.inputs import unit_cube_vertices
