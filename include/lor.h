@@ -91,7 +91,9 @@ typedef struct lor_config {
 } lor_config;
 
 /* Message for the last failed call on ctx (or, for ctx == NULL, the last
- * failed lor_create on this thread).  Valid until the next call. */
+ * failed lor_create on this thread).  Valid until the next call.  Plumbing
+ * (no passage of the paper).  Never fails: an empty string when nothing
+ * has failed. */
 const char* lor_last_error(const lor_ctx* ctx);
 
 /* Create a context for the order-p space on the structured hex mesh with
@@ -128,15 +130,17 @@ int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const do
                        const int64_t* d_elem_dofs, const uint8_t* d_ess, void* stream);
 
 /* Free the context and every device buffer it owns.  Synchronises the device
- * work of the context first.  NULL is accepted. */
+ * work of the context first.  Plumbing.  Always LOR_OK (NULL is accepted). */
 int lor_destroy(lor_ctx* ctx);
 
 /* Number of CUDA kernels liblor has launched in this process so far (all
- * contexts, all threads).  Host-only; for instrumentation. */
+ * contexts, all threads).  Host-only; for instrumentation (no passage).
+ * Errors: LOR_EINVAL if count is NULL. */
 int lor_launch_count(int64_t* count);
 
-/* Sizes: DOFs N = nx ny nz, LOR nonzeros (3nx-2)(3ny-2)(3nz-2), elements,
- * quadrature points nel q^3.  Any pointer may be NULL. */
+/* Sizes: DOFs N = nx ny nz, LOR nonzeros (3nx-2)(3ny-2)(3nz-2) (the count
+ * behind the sizes of Section 4.1), elements, quadrature points nel q^3.  Any
+ * output pointer may be NULL.  Errors: LOR_EINVAL for a NULL ctx. */
 int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int64_t* nqpt);
 
 /* Step S1.1 (high-order operator setup, partial assembly): from the mesh and
@@ -144,7 +148,8 @@ int lor_sizes(const lor_ctx* ctx, int64_t* ndof, int64_t* nnz, int64_t* nel, int
  *   D_g = kappa_g w_g detJ_g J_g^-1 J_g^-T
  * in FP64 and keep it (and a copy of kappa) in the context.  kappa must be
  * finite and > 0; a violation is recorded on the device and reported by the
- * next lor_check (the call itself does not synchronise). */
+ * next lor_check (the call itself does not synchronise).  Errors: LOR_EINVAL
+ * for a NULL ctx or d_kappa, LOR_ENOMEM, LOR_ECUDA. */
 int lor_set_coefficient(lor_ctx* ctx, const double* d_kappa, void* stream);
 
 /* Reaction term of the definite Helmholtz (diffusion-reaction) operator
@@ -158,19 +163,24 @@ int lor_set_coefficient(lor_ctx* ctx, const double* d_kappa, void* stream);
  * of beta over the sub-hex like kappa_s) in the LOR matrix.  d_beta == NULL
  * switches the term off.  Re-assemble (lor_assemble, lor_precond_setup) after
  * changing it.  A bad beta is reported by the next lor_check.  Does not
- * synchronise. */
+ * synchronise.  Errors: LOR_EINVAL for a NULL ctx, LOR_ENOMEM, LOR_ECUDA. */
 int lor_set_reaction(lor_ctx* ctx, const double* d_beta, void* stream);
 
 /* Synchronise the stream and report any error recorded by earlier device
- * work of this context (LOR_EINVAL for a bad coefficient, LOR_ETIMEOUT when
- * an SpMV-type kernel gave up waiting for its bulk copy of matrix values;
- * lor_precond_setup and lor_pcg_solve check the latter themselves). */
+ * work of this context, then clear it.  Plumbing (no passage).  Errors:
+ * LOR_EINVAL for a NULL ctx, a bad coefficient or a coupling missing from
+ * the pattern given to lor_assemble_unstructured; LOR_EGEOM for a detJ <= 0
+ * met there; LOR_ETIMEOUT when an SpMV-type kernel gave up waiting for its
+ * bulk copy of matrix values (lor_precond_setup and the solvers check that
+ * themselves); LOR_ECUDA. */
 int lor_check(lor_ctx* ctx, void* stream);
 
 /* Step S1.2 / A2: build the CSR sparsity of the LOR matrix (27-point graph of
  * the LOR mesh, columns ascending, Dirichlet rows included) inside the
  * context.  If d_rowptr (int64[N+1]) and d_colidx (int32[nnz]) are non-NULL
- * the pattern is also written there.  Idempotent. */
+ * the pattern is also written there.  Idempotent.  Errors: LOR_EINVAL for a
+ * NULL ctx or when only one of the two arrays is given, LOR_ENOMEM,
+ * LOR_ECUDA. */
 int lor_build_pattern(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, void* stream);
 
 /* Step S1.2 / A1 + A4: assemble the values of the LOR matrix A_h for the
@@ -182,18 +192,23 @@ int lor_build_pattern(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, void* 
  * the block entries (LOR_F64 or LOR_F32).  d_values: nnz entries of dtype in
  * the order of lor_build_pattern, or NULL to assemble into the context's own
  * matrix of that dtype (the one lor_precond_setup uses).  Requires
- * lor_build_pattern and lor_set_coefficient. */
+ * lor_build_pattern and lor_set_coefficient.  Errors: LOR_EINVAL for a NULL
+ * ctx or a bad dtype, LOR_ESTATE before those two calls, LOR_ENOMEM,
+ * LOR_ECUDA. */
 int lor_assemble(lor_ctx* ctx, void* d_values, int dtype, void* stream);
 
-/* The LOR mesh as a general hex mesh (E-vectors), the input of the
- * unstructured assembly below: for every sub-hex s = a + p(b + p c) of every
+/* The LOR mesh as a general hex mesh (E-vectors: the input of the
+ * unstructured assembly of Section 4.2, below): for every sub-hex s = a + p(b + p c) of every
  * element e (index e p^3 + s), its 8 vertices T_e(GLL tensor points)
  * d_corners [nsub][8][3] f64 (local vertex r = r0 + 2 r1 + 4 r2), their global
  * DOF ids d_dofs [nsub][8] int64, kappa_s d_kappa_sub [nsub] f64 (the same
  * Gauss-weight binning the macro-element assembly uses) and, if d_beta_sub is
  * not NULL, beta_s [nsub] (requires lor_set_reaction).  d_ess (uint8[N], may
  * be NULL) receives 1 on essential (boundary) DOFs.  nsub = nel p^3.  All
- * arrays are caller-owned device memory.  Requires lor_set_coefficient. */
+ * arrays are caller-owned device memory.  Requires lor_set_coefficient.
+ * Errors: LOR_EINVAL for a NULL ctx or output array, LOR_ESTATE on a general
+ * mesh (lor_create_general), before lor_set_coefficient, or for d_beta_sub
+ * without lor_set_reaction; LOR_ECUDA. */
 int lor_lor_mesh(lor_ctx* ctx, double* d_corners, int64_t* d_dofs, double* d_kappa_sub, double* d_beta_sub,
                  uint8_t* d_ess, void* stream);
 
@@ -211,7 +226,9 @@ int lor_lor_mesh(lor_ctx* ctx, double* d_corners, int64_t* d_dofs, double* d_kap
  * Rows and columns with d_ess[i] != 0 (may be NULL) are eliminated, their
  * diagonal set to 1.  The context only carries the error state.  A coupling
  * missing from the pattern or a detJ <= 0 is reported by the next
- * lor_check.  Does not synchronise. */
+ * lor_check.  Does not synchronise.  Errors: LOR_EINVAL for a NULL ctx, a bad
+ * dtype, a negative size or a missing array (the mesh arrays may be NULL only
+ * when nsub = 0, d_values only when nnz = 0), LOR_ECUDA. */
 int lor_assemble_unstructured(lor_ctx* ctx, int64_t nsub, const double* d_corners, const int64_t* d_dofs,
                               const double* d_kappa_sub, const double* d_beta_sub, int64_t n, int64_t nnz,
                               const int64_t* d_rowptr, const int32_t* d_colidx, const uint8_t* d_ess, void* d_values,
@@ -230,13 +247,19 @@ int lor_assemble_unstructured(lor_ctx* ctx, int64_t nsub, const double* d_corner
  * topology and p only.  On a general mesh (lor_create_general) the edges are
  * the sub-hex edges through the element-to-DOF map, each oriented from its
  * lower to its higher global DOF and numbered by (tail, head) ascending; the
- * first call enumerates them (synchronises) and keeps them in the context. */
+ * first call enumerates them (synchronises) and keeps them in the context.
+ * Errors: LOR_EINVAL for a NULL ctx, when only some of the three arrays are
+ * given, for misaligned arrays or 2^31 or more vertices; LOR_ENOMEM,
+ * LOR_ECUDA. */
 int lor_discrete_gradient(lor_ctx* ctx, int64_t* d_rowptr, int32_t* d_colidx, double* d_values, int64_t* nedge,
                           void* stream);
 
-/* Coordinates of the LOR vertices without duplicates (the vector AMS takes
- * besides the discrete gradient): d_xyz f64[N][3], DOF d (structured: vertex
- * I + nx(J + ny K)) at T_e(GLL node) of the lowest-index element holding it. */
+/* Coordinates of the LOR vertices without duplicates (the vector the
+ * H(curl) solver of Section 3 takes besides the discrete gradient of
+ * Algorithm 1): d_xyz f64[N][3], DOF d (structured: vertex I + nx(J + ny K))
+ * at T_e(GLL node) of the lowest-index element holding it, i.e. the vertices
+ * of the LOR mesh of Section 2.1.  Errors: LOR_EINVAL for a NULL ctx or
+ * d_xyz, LOR_ECUDA. */
 int lor_vertex_coordinates(lor_ctx* ctx, double* d_xyz, void* stream);
 
 /* Step S2.1: y = A_p x, the high-order operator applied matrix-free by sum
@@ -244,7 +267,8 @@ int lor_vertex_coordinates(lor_ctx* ctx, double* d_xyz, void* stream);
  * interpolation/derivative matrices, D from lor_set_coefficient), in FP64.
  * Dirichlet rows: y_ess = x_ess; x_ess is ignored in the free rows.  With
  * lor_set_reaction the mass term is included.  d_x, d_y: f64[N], must not
- * alias. */
+ * alias.  Errors: LOR_EINVAL for a NULL ctx, NULL or aliased arrays,
+ * LOR_ESTATE before lor_set_coefficient, LOR_ECUDA. */
 int lor_apply(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
 
 /* y = A_p x as lor_apply computes it, but with FP32 arithmetic inside the
@@ -254,7 +278,9 @@ int lor_apply(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
  * FP64.  Relative error about 1e-6 of |A_p| |x|.  It is the operator of the
  * inner solves of lor_pcg_solve_ir; the FP64 lor_apply stays the operator of
  * every residual that decides convergence.  d_x, d_y: f64[N], must not alias.
- * The paper has no counterpart (it runs the operator in FP64 only). */
+ * The operator is that of Step S2.1; the paper has no FP32 counterpart (it
+ * runs the operator in FP64 only).  Errors: as lor_apply, and LOR_ENOMEM
+ * for the FP32 factors. */
 int lor_apply_f32(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
 
 /* Backward of y = A_p(kappa) x for the cotangent d_gy (FP64):
@@ -262,18 +288,29 @@ int lor_apply_f32(lor_ctx* ctx, const double* d_x, double* d_y, void* stream);
  *   d_gkappa = d(gy^T A_p x)/d kappa = grad_ref(x)^T (D/kappa) grad_ref(gy)
  *              at every Gauss point, x and gy taken as 0 on essential DOFs
  *                                                          (f64[nel q^3], may be NULL).
- * This is the gradient used by the adjoint method for dJ/dkappa. */
+ * This is the gradient used by the adjoint method for dJ/dkappa.  The
+ * operator is that of Step S2.1 (Eq. (4) with D = kappa w detJ J^-1 J^-T);
+ * the paper does not differentiate it.  Errors: LOR_EINVAL for a NULL ctx or
+ * d_gy, d_gkappa without d_x, or d_gx aliasing d_gy; LOR_ESTATE before
+ * lor_set_coefficient; LOR_ECUDA. */
 int lor_apply_backward(lor_ctx* ctx, const double* d_x, const double* d_gy, double* d_gx, double* d_gkappa,
                        void* stream);
 
 /* Load vector b_i = sum_e sum_g w_g detJ_g f_g phi_i(x_g) for f given at the
- * Gauss points (d_f [nel][q^3] f64) or f = 1 (d_f == NULL); b_ess = 0. */
+ * Gauss points (d_f [nel][q^3] f64) or f = 1 (d_f == NULL); b_ess = 0: the
+ * right-hand side of the problem of Section 4.1, computed with the
+ * quadrature of Step S2.1.  Needs only the mesh.  Errors: LOR_EINVAL for a
+ * NULL ctx or d_b, LOR_ECUDA. */
 int lor_load_vector(lor_ctx* ctx, const double* d_f, double* d_b, void* stream);
 
 /* y = A_h x with the context's assembled LOR matrix of `dtype` (x, y f64;
  * in LOR_F32 mode x is rounded to f32 and the product accumulated in f32).
  * The kernel reads the CSR values only; the columns of the 27-point pattern
- * that lor_build_pattern writes are recomputed from the grid. */
+ * that lor_build_pattern writes are recomputed from the grid.  The SpMV is
+ * the building block of Step S2.2 (the solve phase reduces to SpMVs and
+ * vector updates).  Errors: LOR_EINVAL for a NULL ctx, NULL or aliased
+ * arrays; LOR_ESTATE when no matrix of that dtype is assembled in the
+ * context; LOR_ECUDA. */
 int lor_spmv(lor_ctx* ctx, int dtype, const double* d_x, double* d_y, void* stream);
 
 /* Preconditioner B_h on the context's assembled LOR matrix of `dtype`
@@ -286,17 +323,22 @@ int lor_spmv(lor_ctx* ctx, int dtype, const double* d_x, double* d_y, void* stre
  * iteration w = D_h^-1 A_h v, lambda = |w|/|v|, v = w/|w| from d_v0 (f64[N],
  * device; NULL means all ones).  Returns lmax in *lambda_out (host, may be
  * NULL); synchronises the stream when it estimates lmax.  The smoother
- * computes in `dtype`. */
+ * computes in `dtype`.  Errors: LOR_EINVAL for a NULL ctx, a bad kind or
+ * dtype, degree < 1, not 0 < lo_ratio < hi_ratio, or power_iters < 1 when
+ * lmax is estimated; LOR_ESTATE before the context matrix of that dtype is
+ * assembled; LOR_ENOMEM; LOR_ETIMEOUT; LOR_ECUDA. */
 int lor_precond_setup(lor_ctx* ctx, int kind, int dtype, int degree, double lo_ratio, double hi_ratio,
                       double lambda_max, int power_iters, const double* d_v0, double* lambda_out, void* stream);
 
-/* z = B_h r with the preconditioner from lor_precond_setup (r, z f64[N]). */
+/* Step S2.2: z = B_h r with the preconditioner from lor_precond_setup
+ * (r, z f64[N]; z = r when none is set).  Errors: LOR_EINVAL for a NULL ctx,
+ * NULL or aliased arrays, LOR_ECUDA. */
 int lor_precond_apply(lor_ctx* ctx, const double* d_r, double* d_z, void* stream);
 
 /* Size in bytes of the device array used by lor_precond_apply_noalloc. */
 #define LOR_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* z = B_h r exactly as lor_precond_apply computes it, for callers that must
+/* z = B_h r (Step S2.2) exactly as lor_precond_apply computes it, for callers that must
  * not allocate device memory when they apply the preconditioner (for example
  * a solver loop whose device memory is reserved up front by another
  * allocator, or host code where CUDA allocation calls are not allowed).  The
@@ -322,7 +364,10 @@ int lor_precond_apply_noalloc(lor_ctx* ctx, const double* d_r, double* d_z, void
  * b - A_p x confirms it (otherwise continues from the true residual).
  * Returns the iteration count and final relative residual through host
  * pointers (may be NULL), LOR_ENOCONV after maxit iterations.  Synchronises
- * the stream (it reads the residual norm on the host). */
+ * the stream (it reads the residual norm on the host).  Other errors:
+ * LOR_EINVAL for a NULL ctx, NULL or aliased b and x, rtol <= 0 or
+ * maxit < 0; LOR_ESTATE before lor_set_coefficient; LOR_ETIMEOUT;
+ * LOR_ECUDA. */
 int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int maxit, int* iters,
                   double* final_rel_residual, void* stream);
 
@@ -351,7 +396,11 @@ int lor_pcg_solve(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, int
  * receive the counts and the final FP64 relative residual.  LOR_ENOCONV when
  * maxit or the outer limit is reached first, or when an outer step does not
  * lower the FP64 residual.  Synchronises the stream.
- * The paper has no counterpart: it solves with PCG in FP64. */
+ * The paper has no counterpart: it solves with PCG in FP64 (Section 3,
+ * step S2).  Other errors: LOR_EINVAL for a NULL ctx, NULL or aliased b and
+ * x, rtol <= 0, inner_rtol outside (0, 1), maxit < 0 or an unknown scheme;
+ * LOR_ESTATE before lor_set_coefficient; LOR_ENOMEM; LOR_ETIMEOUT;
+ * LOR_ECUDA. */
 int lor_pcg_solve_ir(lor_ctx* ctx, const double* d_b, double* d_x, double rtol, double inner_rtol, int maxit,
                      int scheme, int* outer_iters, int* inner_iters, double* final_rel_residual, void* stream);
 

@@ -31,6 +31,20 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_documents_every_entry_point():
+    """Each declaration's comment cites the passage that defines the call (or
+    says it is plumbing with no passage) and states its error behaviour."""
+    src = open(os.path.join(ROOT, "include", "lor.h")).read()
+    decl = re.compile(r"/\*((?:(?!\*/).)*?)\*/\s*(?:int|const char\*)\s+(lor_[a-z_0-9]+)\s*\(", re.S)
+    documented = {}
+    for com, name in decl.findall(src):
+        cites = re.search(r"Section|Step|Eq\.|Algorithm|[Pp]lumbing|no passage", com)
+        errors = re.search(r"LOR_E|Never fails|Always LOR_OK", com)
+        documented[name] = bool(cites and errors)
+    assert sorted(documented) == declared_entry_points()
+    assert all(documented.values()), [n for n, ok in documented.items() if not ok]
+
+
 def test_library_exports_every_declared_symbol(libpath):
     L = ctypes.CDLL(libpath)
     missing = [n for n in declared_entry_points() if not hasattr(L, n)]
