@@ -64,7 +64,8 @@
 /* ------------------------------------------------------------------------- */
 
 /* Legendre polynomial P_n(x) by the three-term recurrence
- * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}; also returns P_{n-1}(x). */
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}; also returns P_{n-1}(x).  Both
+ * 1D rules of Section 2.1 are built on it. */
 static void legendre_pair(int n, double x, double* Pn, double* Pnm1) {
   double pm1 = 1.0, p = x;
   if (n == 0) { *Pn = 1.0; *Pnm1 = 0.0; return; }
@@ -136,7 +137,9 @@ int orc_gauss_lobatto(int p, double* x) {
 
 /* Lagrange basis on the n nodes, evaluated at t by the product formula
  *   l_j(t)  = prod_{m != j} (t - x_m) / (x_j - x_m)
- *   l_j'(t) = sum_{l != j} 1/(x_j - x_l) prod_{m != j,l} (t - x_m)/(x_j - x_m). */
+ *   l_j'(t) = sum_{l != j} 1/(x_j - x_l) prod_{m != j,l} (t - x_m)/(x_j - x_m).
+ * On the Gauss-Lobatto nodes this is the nodal basis of the order-p space of
+ * Section 2.1. */
 void orc_lagrange(int n, const double* nodes, double t, double* phi, double* dphi) {
   for (int j = 0; j < n; ++j) {
     double v = 1.0;
@@ -188,7 +191,7 @@ static void element_corners(const double* V, int nex, int ney, int ex, int ey, i
 
 /* Trilinear map through corners X at reference point xi in [-1,1]^3:
  * x(xi) = sum_c X_c prod_k l_{c_k}(xi_k), l_0 = (1-t)/2, l_1 = (1+t)/2,
- * J[i][j] = d x_i / d xi_j. */
+ * J[i][j] = d x_i / d xi_j: the element map T_e of Section 2.1 with p_g = 1. */
 static void trilinear_map(const double X[8][3], const double xi[3], double x[3], double J[3][3]) {
   for (int i = 0; i < 3; ++i) {
     if (x) x[i] = 0.0;
@@ -210,7 +213,8 @@ static void trilinear_map(const double X[8][3], const double xi[3], double x[3],
   }
 }
 
-/* Inverse of a 3x3 matrix by the cofactor formula; returns det. */
+/* Inverse of a 3x3 matrix by the cofactor formula; returns det (the J^-1
+ * and detJ of Step S1.1). */
 static double inverse3(const double A[3][3], double Ai[3][3]) {
   double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
   double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
@@ -228,7 +232,8 @@ static double inverse3(const double A[3][3], double Ai[3][3]) {
   return det;
 }
 
-/* G = w detJ J^-1 J^-T, stored as (00,01,02,11,12,22). */
+/* G = w detJ J^-1 J^-T, stored as (00,01,02,11,12,22): the geometric part of
+ * the quadrature-point factor D = kappa G of Step S1.1. */
 static void diffusion_factor(const double J[3][3], double w, double* detJ, double G[6]) {
   double Ji[3][3];
   double det = inverse3(J, Ji);
@@ -273,7 +278,8 @@ int orc_geometry(int nex, int ney, int nez, const double* V, int q, double* detJ
   return bad ? ORC_EGEOM : ORC_OK;
 }
 
-/* Physical coordinates of every global GLL DOF: x = T_e(GLL tensor point). */
+/* Physical coordinates of every global GLL DOF: x = T_e(GLL tensor point),
+ * i.e. the vertices of the LOR mesh of Section 2.1. */
 int orc_dof_coordinates(int nex, int ney, int nez, const double* V, int p, double* xyz) {
   double gll[ORC_MAXN];
   int rc = orc_gauss_lobatto(p, gll);
@@ -311,7 +317,8 @@ static int is_essential(int64_t I, int64_t J, int64_t K, int64_t nx, int64_t ny,
 /* ------------------------------------------------------------------------- */
 
 /* Reference gradient of the element field u[k][j][i] at every Gauss point,
- * gr[g][3] (d/dxi0, d/dxi1, d/dxi2), by the three tensor stages of B. */
+ * gr[g][3] (d/dxi0, d/dxi1, d/dxi2), by the three tensor stages of B
+ * (Step S2.1). */
 static void element_reference_gradient(int n, int q, const double* B, const double* D, const double* u, double* gr) {
   /* stage along xi0 */
   double* Bu = (double*)malloc(sizeof(double) * n * n * q);
@@ -363,7 +370,7 @@ static void element_reference_gradient(int n, int q, const double* B, const doub
 }
 
 /* Transpose of element_reference_gradient: v[g][3] at Gauss points ->
- * element vector y[k][j][i] = sum_g (B^T v). */
+ * element vector y[k][j][i] = sum_g (B^T v), the B^T of Eq. (4). */
 static void element_reference_gradient_transpose(int n, int q, const double* B, const double* D, const double* v, double* y) {
   double* T0 = (double*)malloc(sizeof(double) * n * q * q);
   double* T1 = (double*)malloc(sizeof(double) * n * q * q);
@@ -436,7 +443,8 @@ static void element_values(int n, int q, const double* B, const double* u, doubl
   free(T1); free(T2);
 }
 
-/* Transpose of element_values, accumulated: y[k][j][i] += ((B (x) B (x) B)^T v)_{ijk}. */
+/* Transpose of element_values, accumulated: y[k][j][i] += ((B (x) B (x) B)^T v)_{ijk}
+ * (the B_m^T of the reaction term of Section 4.1's problem). */
 static void element_values_transpose_add(int n, int q, const double* B, const double* v, double* y) {
   double* T2 = (double*)malloc(sizeof(double) * n * q * q);
   double* T1 = (double*)malloc(sizeof(double) * n * n * q);
@@ -464,6 +472,8 @@ static void element_values_transpose_add(int n, int q, const double* B, const do
   free(T1); free(T2);
 }
 
+/* Element restriction G of Eq. (4): the element's (p+1)^3 values from the
+ * global vector, zero on essential DOFs when dirichlet != 0. */
 static void gather_element(int64_t nx, int64_t ny, int64_t nz, int p, int ex, int ey, int ez, const double* x, int dirichlet, double* xe) {
   int n = p + 1;
   for (int k = 0; k < n; ++k)
@@ -476,6 +486,9 @@ static void gather_element(int64_t nx, int64_t ny, int64_t nz, int p, int ex, in
       }
 }
 
+/* y = A_p x (Step S2.1, Eq. (4)): restriction, reference gradient, the
+ * factor D (Step S1.1), transposed stages, accumulation; see the banner
+ * above for the reaction term and the Dirichlet treatment. */
 int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
                  const double* x, double* y, int dirichlet) {
   if (p < 1 || q < 1 || p + 1 > ORC_MAXN || q > ORC_MAXN) return ORC_EINVAL;
@@ -545,7 +558,9 @@ int orc_ho_apply(int nex, int ney, int nez, const double* V, int p, int q, const
  *                  x and gy taken as zero on essential DOFs,
  * i.e. the derivative of gy^T A_p(kappa) x with respect to kappa[e][g].
  * Either output may be NULL; beta (may be NULL) is the reaction coefficient
- * of the operator, which enters gx only. */
+ * of the operator, which enters gx only.  The operator is that of Step S2.1
+ * (Eq. (4)); the paper does not differentiate it, so this is its plain
+ * derivative written out. */
 int orc_ho_apply_backward(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta,
                           const double* x, const double* gy, double* gx, double* gkappa) {
   if (gx) {
@@ -588,7 +603,8 @@ int orc_ho_apply_backward(int nex, int ney, int nez, const double* V, int p, int
 }
 
 /* Load vector b_i = sum_e sum_g w_g detJ_g f_g phi_i(x_g) for a right-hand
- * side given at Gauss points f[e][g] (f == NULL means f = 1); b_ess = 0. */
+ * side given at Gauss points f[e][g] (f == NULL means f = 1); b_ess = 0: the
+ * right-hand side of the problem of Section 2.2 (f = 1 in Section 4.1). */
 int orc_load_vector(int nex, int ney, int nez, const double* V, int p, int q, const double* f, double* b) {
   int n = p + 1, nq3 = q * q * q;
   int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
@@ -905,7 +921,8 @@ void orc_csr_free(void* h) {
  * sub-hexes that contain the row's vertex (no global assembly): for every
  * sub-hex s touching DOF r, add row r of K_s.  Entries are returned sorted
  * by column, at most cap per row: cols/vals are [nrows][cap], counts[nrows].
- * Same Dirichlet treatment as orc_lor_assemble. */
+ * Same Dirichlet treatment as orc_lor_assemble (Step S1.2, A4); the rows of
+ * the LOR matrix at full size, computed one by one. */
 int orc_lor_rows(int nex, int ney, int nez, const double* V, int p, int q, const double* kappa, const double* beta, int dirichlet,
                  int64_t nrows, const int64_t* rows, int cap, int32_t* counts, int64_t* cols, double* vals) {
   int64_t nx = (int64_t)nex * p + 1, ny = (int64_t)ney * p + 1, nz = (int64_t)nez * p + 1;
@@ -986,7 +1003,8 @@ int64_t orc_lor_edge_count(int nex, int ney, int nez, int p) {
   return (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1);
 }
 
-/* rowptr[nedge+1], colidx[2 nedge], values[2 nedge] */
+/* The matrix of Algorithm 1 in the numbering above:
+ * rowptr[nedge+1], colidx[2 nedge], values[2 nedge]. */
 int orc_discrete_gradient(int nex, int ney, int nez, int p, int64_t* rowptr, int64_t* colidx, double* values) {
   int64_t n[3] = {(int64_t)nex * p + 1, (int64_t)ney * p + 1, (int64_t)nez * p + 1};
   int64_t stride[3] = {1, n[0], n[0] * n[1]};
@@ -1015,6 +1033,7 @@ int orc_discrete_gradient(int nex, int ney, int nez, int p, int64_t* rowptr, int
 /* phase reduces to spmv and vector updates).                                  */
 /* ------------------------------------------------------------------------- */
 
+/* y = A x (Step S2.2's SpMV). */
 void orc_csr_spmv(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* values, const double* x, double* y) {
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
@@ -1023,6 +1042,7 @@ void orc_csr_spmv(int64_t n, const int64_t* rowptr, const int64_t* colidx, const
   }
 }
 
+/* d = diag(A), the Jacobi scaling of the smoother (Step S2.2, reading R6). */
 void orc_csr_diagonal(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* values, double* d) {
   for (int64_t i = 0; i < n; ++i) {
     d[i] = 0.0;
