@@ -88,3 +88,18 @@ def test_reference_arm_line(monkeypatch):
     assert "2x2x2 elements" in out["config"]["workload"]
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
+
+
+def test_clock_log_summary():
+    import bench
+    lines = ["0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, 1980, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+             "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n",
+             "truncated line, 2070\n"]
+    out = bench.parse_clock_log(lines)
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+    hot = lines[:1] + ["0, 1500, 2070, 700.0, 0x48, Active, Not Active, Active, Not Active\n"]
+    assert bench.parse_clock_log(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.parse_clock_log([]) is None
