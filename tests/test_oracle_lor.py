@@ -21,33 +21,50 @@ def lor_dense(mesh, p, q, kappa, dirichlet):
 
 
 # ------------------------------------------------------------ kappa binning (R1)
-def kappa_sub_bruteforce(p, q, kappa):
-    g = gll_nodes(p)
-    xg, wg = npleg.leggauss(q)
-    out = np.zeros((kappa.shape[0], p ** 3))
-    for e in range(kappa.shape[0]):
-        for s in range(p ** 3):
-            a, b, c = s % p, (s // p) % p, s // (p * p)
-            num = den = 0.0
-            for g2 in range(q):
-                for g1 in range(q):
-                    for g0 in range(q):
-                        if all(g[t] < xg[gg] <= g[t + 1] or (t == 0 and xg[gg] == g[0])
-                               for t, gg in ((a, g0), (b, g1), (c, g2))):
-                            w = wg[g0] * wg[g1] * wg[g2]
-                            num += w * kappa[e, g0 + q * (g1 + q * g2)]
-                            den += w
-            out[e, s] = num / den
-    return out
+def bin_of(p, q):
+    """Sub-interval of each Gauss-Legendre point along one axis: the GLL
+    interval [x_a, x_{a+1}] that contains it (from numpy's nodes alone)."""
+    xg, _ = npleg.leggauss(q)
+    return np.clip(np.searchsorted(gll_nodes(p), xg, side="left") - 1, 0, p - 1)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
-def test_kappa_sub_binning(p):
+@pytest.mark.parametrize("p", range(1, 11))
+def test_kappa_sub_of_a_coefficient_constant_on_each_sub_hex(p):
+    """kappa constant on each sub-hex's set of Gauss points (the value c_s
+    drawn per sub-hex) gives kappa_s = c_s exactly, whatever the weights:
+    this fixes which high-order points belong to which sub-hex."""
     q = p + 2
-    rng = np.random.default_rng(p)
-    kap = np.exp(rng.standard_normal((3, q ** 3)))
-    np.testing.assert_allclose(oracle.lor_kappa_sub(p, q, kap), kappa_sub_bruteforce(p, q, kap), rtol=1e-14)
-    np.testing.assert_allclose(oracle.lor_kappa_sub(p, q, np.full((2, q ** 3), 2.5)), 2.5, rtol=1e-15)
+    rng = np.random.default_rng(100 + p)
+    c = np.exp(rng.standard_normal((2, p ** 3)))
+    b = bin_of(p, q)
+    g0, g1, g2 = np.meshgrid(np.arange(q), np.arange(q), np.arange(q), indexing="ij")
+    sub = (b[g0] + p * (b[g1] + p * b[g2]))          # [g0, g1, g2] -> sub-hex index
+    kap = np.zeros((2, q ** 3))
+    kap[:, (g0 + q * (g1 + q * g2)).ravel()] = c[:, sub.ravel()]
+    np.testing.assert_allclose(oracle.lor_kappa_sub(p, q, kap), c, rtol=1e-15, atol=0)
+
+
+def test_kappa_sub_of_a_linear_coefficient_p2():
+    """p = 2 (GLL nodes -1, 0, 1), q = 4 Gauss points
+    +-x1 = +-sqrt(3/7 - (2/7) sqrt(6/5)), weight (18 + sqrt 30)/36, and
+    +-x2 = +-sqrt(3/7 + (2/7) sqrt(6/5)), weight (18 - sqrt 30)/36.
+    For kappa = 2 + xi_d the weighted bin average is 2 -+ (w1 x1 + w2 x2) / (w1 + w2)
+    on the lower / upper half of axis d (the other axes' weights cancel),
+    with w1 + w2 = 1."""
+    x1 = np.sqrt(3 / 7 - 2 / 7 * np.sqrt(6 / 5))
+    x2 = np.sqrt(3 / 7 + 2 / 7 * np.sqrt(6 / 5))
+    w1, w2 = (18 + np.sqrt(30)) / 36, (18 - np.sqrt(30)) / 36
+    S = (w1 * x1 + w2 * x2) / (w1 + w2)
+    xs = np.array([-x2, -x1, x1, x2])                 # ascending Gauss points
+    p, q = 2, 4
+    for d in range(3):
+        g = np.stack(np.meshgrid(np.arange(q), np.arange(q), np.arange(q), indexing="ij"), 0)
+        kap = np.zeros(q ** 3)
+        kap[(g[0] + q * (g[1] + q * g[2])).ravel()] = (2.0 + xs[g[d]]).ravel()
+        ks = oracle.lor_kappa_sub(p, q, kap[None])[0]
+        for s in range(p ** 3):
+            a = (s, s // p, s // (p * p))[d] % p
+            assert abs(ks[s] - (2.0 - S if a == 0 else 2.0 + S)) < 2e-15  # a few ulps of 2.5
 
 
 # ------------------------------------------------------------ closed forms
@@ -227,7 +244,7 @@ def test_one_d_equivalence_constants_bounded(p):
     assert 0.5 <= lm.min() and lm.max() <= 3.0
 
 
-@pytest.mark.parametrize("p", range(1, 8))
+@pytest.mark.parametrize("p", range(1, 9))
 def test_spectral_equivalence_within_tensor_bounds(p):
     """Generalised eigenvalues of (A_p, A_h) on the free DOFs of an
     undistorted mesh lie in [lk_min lm_min^2, lk_max lm_max^2], the products
@@ -251,3 +268,41 @@ def test_spectral_equivalence_within_tensor_bounds(p):
     if p == 1:
         np.testing.assert_allclose(lam, 1.0, atol=1e-12)
     assert hi <= (np.pi ** 2 / 4) * 9.0
+
+
+def element_bounds(X, p):
+    """Extreme generalised eigenvalues of one element's high-order and LOR
+    stiffness matrices (kappa = 1, no boundary conditions) on the complement
+    of the constants, the common kernel of both."""
+    q = p + 2
+    n = (p + 1) ** 3
+    k1 = np.ones((1, q ** 3))
+    Ah, _ = lor_dense(oracle.Mesh(1, 1, 1, X.copy()), p, q, k1, dirichlet=False)
+    Ap = oracle.dense_general(X[None], element_dofs(1, 1, 1, p), k1, p, q, n)
+    Z = scipy.linalg.null_space(np.ones((1, n)))
+    lam = scipy.linalg.eigh(Z.T @ Ap @ Z, Z.T @ Ah @ Z, eigvals_only=True)
+    return lam.min(), lam.max()
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_spectral_equivalence_jittered_mesh_lognormal_kappa(p):
+    """Jittered mesh, kappa lognormal and constant on each element: both
+    operators are sums of kappa_e times element matrices (kappa_s = kappa_e by
+    R1), so the generalised eigenvalues of (A_p, A_h) on the free DOFs lie in
+    [min_e mu_lo(e), max_e mu_hi(e)] of the elements' own kappa = 1 bounds,
+    independent of the coefficient's contrast; and those bounds stay within
+    the undistorted tensor-product range (1D stiffness at most pi^2/4, 1D mass
+    in [1/2, 3]) as p grows."""
+    dims = (2, 2, 2) if p <= 5 else (2, 1, 1)
+    mesh = jittered(*dims, seed=p, jitter=0.2)
+    q = p + 2
+    kap = np.repeat(np.exp(np.random.default_rng(20 + p).standard_normal((mesh.nel, 1))), q ** 3, axis=1)
+    Ah, _ = lor_dense(mesh, p, q, kap, dirichlet=False)
+    C = element_corners(mesh.V, *dims)
+    Ap = oracle.dense_general(C, element_dofs(*dims, p), kap, p, q, mesh.ndof(p))
+    free = ~essential_mask(*dims, p)
+    lam = scipy.linalg.eigh(Ap[np.ix_(free, free)], Ah[np.ix_(free, free)], eigvals_only=True)
+    b = [element_bounds(C[e], p) for e in range(mesh.nel)]
+    lo, hi = min(x[0] for x in b), max(x[1] for x in b)
+    assert lam.min() >= lo * (1 - 1e-10) and lam.max() <= hi * (1 + 1e-10)
+    assert lo >= 0.25 and hi <= 9.0 * np.pi ** 2 / 4
