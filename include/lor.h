@@ -175,6 +175,24 @@ int lor_set_reaction(lor_ctx* ctx, const double* d_beta, void* stream);
  * themselves); LOR_ECUDA. */
 int lor_check(lor_ctx* ctx, void* stream);
 
+/* Bit of lor_set_test_hooks. */
+#define LOR_TEST_EXPIRE_WAITS 1u
+
+/* Test hooks (no passage: the paper has no counterpart; a way for tests to exercise the
+ * error paths of device-side waits without a fault).  flags is a bit mask:
+ *   LOR_TEST_EXPIRE_WAITS  every CTA of the TMA-staged SpMV/smoother kernels
+ *                          (structured meshes) treats its first bounded wait
+ *                          for a bulk copy as expired: it records
+ *                          LOR_FLAG_TIMEOUT in the context's status word, lets
+ *                          every copy it issued land (waits at the normal
+ *                          bound) and exits without writing its rows, exactly
+ *                          as after a real expiry.  lor_check, lor_precond_setup
+ *                          and the solvers then return LOR_ETIMEOUT.
+ * 0 clears the hooks; a cleared context computes as before (clear the status
+ * word with lor_check first).  Host only, does not synchronise.  Errors:
+ * LOR_EINVAL for a NULL ctx or an unknown flag. */
+int lor_set_test_hooks(lor_ctx* ctx, unsigned flags);
+
 /* Step S1.2 / A2: build the CSR sparsity of the LOR matrix (27-point graph of
  * the LOR mesh, columns ascending, Dirichlet rows included) inside the
  * context.  If d_rowptr (int64[N+1]) and d_colidx (int32[nnz]) are non-NULL
@@ -338,7 +356,7 @@ int lor_precond_apply(lor_ctx* ctx, const double* d_r, double* d_z, void* stream
 /* Size in bytes of the device array used by lor_precond_apply_noalloc. */
 #define LOR_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* z = B_h r (Step S2.2) exactly as lor_precond_apply computes it, for callers that must
+/* z = B_h r exactly as lor_precond_apply computes it, for callers that must
  * not allocate device memory when they apply the preconditioner (for example
  * a solver loop whose device memory is reserved up front by another
  * allocator, or host code where CUDA allocation calls are not allowed).  The
@@ -348,12 +366,14 @@ int lor_precond_apply(lor_ctx* ctx, const double* d_r, double* d_z, void* stream
  * It needs 3 N values of the smoother's precision (N = DOFs): up to 699,050
  * DOFs for an FP64 smoother and 1,398,101 for FP32 (Jacobi and degree 1 need
  * none); larger sizes are rejected with LOR_EINVAL.  The first call on each
- * device looks up the array's device address (with that device current);
- * make that first call before any stream capture.  All calls share the
+ * device looks up the array's device address (with that device current)
+ * and keeps it for the life of the process, which assumes one primary CUDA
+ * context per device (a cudaDeviceReset invalidates it); make that first
+ * call before any stream capture.  All calls share the
  * array, which keeps the last call's contents (each call writes every element
  * it reads, so nothing needs clearing); calls that overlap on the GPU race
  * and must be ordered by the caller.  r, z: f64[N], distinct.
- * The paper has no counterpart: this is an interface for allocation-free
+ * The paper has no counterpart (no passage): this is an interface for allocation-free
  * callers of this library. */
 int lor_precond_apply_noalloc(lor_ctx* ctx, const double* d_r, double* d_z, void* stream);
 

@@ -53,6 +53,7 @@ def _declare(L):
         "orc_dense_general": (i, [i64, i, i, _dp, _i64p, _dp, vp, i64, _dp]),
         "orc_lor_kappa_sub": (i, [i, i, i64, _dp, _dp]),
         "orc_lor_assemble": (vp, [i, i, i, _dp, i, i, _dp, vp, i, C.POINTER(i)]),
+        "orc_lor_assemble_general": (vp, [i64, i, i, _dp, _i64p, i64, vp, _dp, vp, i, C.POINTER(i)]),
         "orc_csr_nnz": (i64, [vp]),
         "orc_csr_n": (i64, [vp]),
         "orc_csr_copy": (None, [vp, _i64p, _i64p, _dp]),
@@ -228,6 +229,33 @@ def lor_assemble(mesh, p, q, kappa, dirichlet=True, beta=None):
     finally:
         lib().orc_csr_free(h)
     return rowptr, colidx, values
+
+
+def _csr_from_handle(h, st, what):
+    if not h:
+        raise OracleError(st.value, what)
+    try:
+        _check(st.value, what)
+        n, nnz = lib().orc_csr_n(h), lib().orc_csr_nnz(h)
+        rowptr, colidx, values = np.zeros(n + 1, np.int64), np.zeros(nnz, np.int64), np.zeros(nnz)
+        lib().orc_csr_copy(h, rowptr, colidx, values)
+    finally:
+        lib().orc_csr_free(h)
+    return rowptr, colidx, values
+
+
+def lor_assemble_general(corners, dofs, N, p, q, kappa, ess=None, dirichlet=True, beta=None):
+    """Full LOR CSR of a general conforming hex mesh (corners [nel][8][3],
+    element-to-DOF map [nel][(p+1)^3], essential mask uint8[N] or None)."""
+    corners = _f64(corners).reshape(-1, 8, 3)
+    nel = corners.shape[0]
+    dofs = np.ascontiguousarray(dofs, dtype=np.int64).reshape(nel, (p + 1) ** 3)
+    e = None if ess is None else np.ascontiguousarray(ess, dtype=np.uint8).reshape(N)
+    b = _opt(beta, nel * q ** 3)
+    st = C.c_int(0)
+    h = lib().orc_lor_assemble_general(nel, p, q, corners, dofs, N, None if e is None else e.ctypes.data_as(C.c_void_p),
+                                       _f64(kappa).ravel(), _ptr(b), int(dirichlet), C.byref(st))
+    return _csr_from_handle(h, st, "lor_assemble_general")
 
 
 def lor_rows(mesh, p, q, kappa, rows, dirichlet=True, cap=64, beta=None):

@@ -917,6 +917,92 @@ void orc_csr_free(void* h) {
   free(A->rowptr); free(A->colidx); free(A->values); free(A);
 }
 
+/* ------------------------------------------------------------------------- */
+/* LOR matrix of a general conforming hex mesh given in element-restriction    */
+/* form (Step S1.1's maps G: corners [nel][8][3] and element-to-DOF map        */
+/* [nel][(p+1)^3], local node i + n(j + n k)): the same sub-hex blocks as      */
+/* orc_lor_assemble (readings R1, R2), their 8 DOFs looked up through the map, */
+/* triplets sorted by (row, col) and merged; then (dirichlet != 0) the rows    */
+/* and columns of the DOFs with ess[i] != 0 eliminated, pattern kept,          */
+/* diagonal 1 (A4, reading R4).  ess may be NULL (no essential DOFs).          */
+/* ------------------------------------------------------------------------- */
+void* orc_lor_assemble_general(int64_t nel, int p, int q, const double* corners, const int64_t* dofs, int64_t N,
+                               const uint8_t* ess, const double* kappa, const double* beta, int dirichlet, int* status) {
+  *status = ORC_OK;
+  int n = p + 1, n3 = n * n * n, p3 = p * p * p;
+  double gll[ORC_MAXN];
+  if (orc_gauss_lobatto(p, gll)) { *status = ORC_EINVAL; return NULL; }
+  double* ksub = (double*)malloc(sizeof(double) * nel * p3);
+  double* bsub = (double*)calloc((size_t)(nel * p3), sizeof(double));
+  if (orc_lor_kappa_sub(p, q, nel, kappa, ksub) || (beta && orc_lor_kappa_sub(p, q, nel, beta, bsub))) {
+    free(ksub); free(bsub); *status = ORC_EINVAL; return NULL;
+  }
+  int64_t ntrip = nel * p3 * 64;
+  orc_triplet* T = (orc_triplet*)malloc(sizeof(orc_triplet) * ntrip);
+  if (!T) { free(ksub); free(bsub); *status = ORC_ENOMEM; return NULL; }
+  int64_t t = 0;
+  int bad = 0;
+  for (int64_t e = 0; e < nel; ++e) {
+    double X[8][3];
+    for (int cc = 0; cc < 8; ++cc)
+      for (int d = 0; d < 3; ++d) X[cc][d] = corners[(e * 8 + cc) * 3 + d];
+    for (int c = 0; c < p; ++c)
+      for (int b = 0; b < p; ++b)
+        for (int a = 0; a < p; ++a) {
+          double K[8][8];
+          int s = a + p * (b + p * c);
+          bad |= lor_subhex_matrix(X, gll, a, b, c, ksub[e * p3 + s], bsub[e * p3 + s], K);
+          int64_t dof[8];
+          for (int r = 0; r < 8; ++r) {
+            int i = a + (r & 1), j = b + ((r >> 1) & 1), k = c + ((r >> 2) & 1);
+            dof[r] = dofs[e * n3 + i + n * (j + n * k)];
+            if (dof[r] < 0 || dof[r] >= N) bad = 2;
+          }
+          for (int r = 0; r < 8; ++r)
+            for (int s2 = 0; s2 < 8; ++s2) {
+              T[t].row = dof[r];
+              T[t].col = dof[s2];
+              T[t].val = K[r][s2];
+              ++t;
+            }
+        }
+  }
+  free(ksub);
+  free(bsub);
+  if (bad == 2) { free(T); *status = ORC_EINVAL; return NULL; }
+  qsort(T, (size_t)ntrip, sizeof(orc_triplet), triplet_cmp);
+  orc_csr* A = (orc_csr*)calloc(1, sizeof(orc_csr));
+  A->n = N;
+  A->rowptr = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < ntrip; ++i)
+    if (i == 0 || T[i].row != T[i - 1].row || T[i].col != T[i - 1].col) ++nnz;
+  A->nnz = nnz;
+  A->colidx = (int64_t*)malloc(sizeof(int64_t) * (nnz > 0 ? nnz : 1));
+  A->values = (double*)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+  int64_t k = -1;
+  for (int64_t i = 0; i < ntrip; ++i) {
+    if (i == 0 || T[i].row != T[i - 1].row || T[i].col != T[i - 1].col) {
+      ++k;
+      A->colidx[k] = T[i].col;
+      A->values[k] = 0.0;
+      A->rowptr[T[i].row + 1]++;
+    }
+    A->values[k] += T[i].val;
+  }
+  free(T);
+  for (int64_t i = 0; i < N; ++i) A->rowptr[i + 1] += A->rowptr[i];
+  if (dirichlet && ess) {
+    for (int64_t r = 0; r < N; ++r)
+      for (int64_t j = A->rowptr[r]; j < A->rowptr[r + 1]; ++j) {
+        int64_t cc = A->colidx[j];
+        if (ess[r] || ess[cc]) A->values[j] = (cc == r) ? 1.0 : 0.0;
+      }
+  }
+  if (bad) *status = ORC_EGEOM;
+  return A;
+}
+
 /* Selected rows of the LOR matrix, each computed on its own from the
  * sub-hexes that contain the row's vertex (no global assembly): for every
  * sub-hex s touching DOF r, add row r of K_s.  Entries are returned sorted

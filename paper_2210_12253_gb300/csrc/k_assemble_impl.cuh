@@ -22,7 +22,15 @@
 // Geometry: the sub-hex map is the element's trilinear map restricted to the
 // sub-box, so J_sub(tau) = J_e(xi(tau)) diag(r_a, r_b, r_c) with r the half
 // widths of the GLL intervals; only the element Jacobian columns (bilinear in
-// the two other coordinates) are evaluated, in FP64.
+// the two other coordinates) are evaluated, in FP64.  In FP64 the metric is
+// formed from M = J_e^T J_e: with V = r_a r_b r_c,
+//   detJ_sub J_sub^-1 J_sub^-T = adj(J_sub^T J_sub) / detJ_sub
+//                             = V / (r_a r_b) adj(M)_ab / detJ_e,
+// detJ_e = sqrt(det M).  M's diagonal |c_d|^2 depends on the two coordinates
+// its column is tabulated on, so it is tabulated per element too; per Gauss
+// point remain the three off-diagonal products, the cofactors, det M and one
+// reciprocal square root (fewer FP64 instructions than the adjugate rows of
+// J_e, their products and a determinant with its reciprocal).
 #pragma once
 
 #include "lor_internal.cuh"
@@ -65,6 +73,24 @@ __device__ __forceinline__ constexpr double inv_sqrt3_pow(int p) {  // 3^(-p/2),
                 : 0.03703703703703703704;
 }
 __device__ __forceinline__ constexpr int sym(int i, int j) { return i <= j ? i * 8 + j : j * 8 + i; }
+
+// 1/sqrt(x) in FP64 for x > 0 in the FP32 normal range (1.2e-38 .. 3.4e38):
+// an FP32 seed (x's leading 20 mantissa bits, the hardware rsqrt
+// approximation: about 20 correct bits) refined by one Newton step with its
+// second-order term, y (1 + e/2 + 3 e^2/8) with e = 1 - x y^2 (the error
+// left is O(e^3), below FP64 rounding; within 1.3 ulp in a CPU emulation over
+// 1e-30 .. 1e30).  The FP64 <-> FP32 moves are integer bit operations, since
+// the conversion instructions issue on the FP64 pipe.  Five FP64 operations.
+__device__ __forceinline__ double lor_rsqrt(double x) {
+  const int hi = __double2hiint(x);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float((hi - (896 << 20)) << 3)));
+  const int yb = __float_as_int(yf);
+  const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
 
 // v(w) = sum_g v(g) prod_k eps_k^{w_k}; the three butterfly stages commute,
 // stage FIRST runs first.  For a diagonal metric entry G^{aa} only the
@@ -142,6 +168,7 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
   constexpr bool F32 = sizeof(VT) == sizeof(float);
   __shared__ double Ehalf[EPB][36];
   __shared__ double tab[EPB][TAB];
+  __shared__ double mdiag[F32 ? 1 : EPB][F32 ? 1 : 3 * L * L];  // |c_d|^2 on each column's table (FP64)
   __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
   __shared__ double sl0[L], sl1[L];
   if (threadIdx.x < L) {
@@ -159,6 +186,13 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
   }
   if constexpr (F32) {
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
+    __syncthreads();
+  } else {
+    constexpr int ND = 3 * L * L;
+    for (int i = threadIdx.x; i < EPB * ND; i += blockDim.x) {
+      const double* cc = &tab[i / ND][3 * (i % ND)];
+      mdiag[i / ND][i % ND] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+    }
     __syncthreads();
   }
   const int nwork = EPB * P3;
@@ -181,40 +215,52 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
         }
       }
 
-    // G_sub^{ab}(g) = F_ab (A_a . A_b) / det_e with A the adjugate rows of the
-    // element Jacobian, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64 (the 1/64
-    // of the modal-to-nodal transform folded in).
+    // G_sub^{ab}(g) = F_ab adj(M)_ab / det_e, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64
+    // (the 1/64 of the modal-to-nodal transform folded in).  In FP64, G holds
+    // adj(M)_ab / det_e and F_ab multiplies in the modal block; in FP32 (G
+    // from the adjugate rows A_a of J_e: A_a . A_b = adj(M)_ab) G includes F_ab.
     VT G[6][8];
     VT W[MASS ? 8 : 1];  // reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
     const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
+    double FF[6];  // F_ab in pair order (00, 01, 02, 11, 12, 22) (FP64 only)
     if constexpr (!F32) {
       const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
       const double k64 = ks * (1.0 / 64.0);
-      const double F00 = k64 * rb * rc * T.sub_rinv[a], F01 = k64 * rc, F02 = k64 * rb;
-      const double F11 = k64 * ra * rc * T.sub_rinv[b], F12 = k64 * ra, F22 = k64 * ra * rb * T.sub_rinv[c];
+      FF[0] = k64 * rb * rc * T.sub_rinv[a];
+      FF[1] = k64 * rc;
+      FF[2] = k64 * rb;
+      FF[3] = k64 * ra * rc * T.sub_rinv[b];
+      FF[4] = k64 * ra;
+      FF[5] = k64 * ra * rb * T.sub_rinv[c];
       const double bR = MASS ? bs * (1.0 / 64.0) * ra * rb * rc : 0.0;
       const double* t0 = tab[le];
       const double* t1 = tab[le] + L * L * 3;
       const double* t2 = tab[le] + 2 * L * L * 3;
+      const double* q0 = mdiag[le];
+      const double* q1 = mdiag[le] + L * L;
+      const double* q2 = mdiag[le] + 2 * L * L;
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
         const double* c0 = t0 + 3 * (u1 + L * u2);
         const double* c1 = t1 + 3 * (u0 + L * u2);
         const double* c2 = t2 + 3 * (u0 + L * u1);
-        double A[3][3];
-        lor_cross(c1, c2, A[0]);
-        lor_cross(c2, c0, A[1]);
-        lor_cross(c0, c1, A[2]);
-        const double det = c0[0] * A[0][0] + c0[1] * A[0][1] + c0[2] * A[0][2];
-        const double r = lor_rcp(det);
-        if constexpr (MASS) W[g] = (VT)(bR * det);
-#pragma unroll
-        for (int ab = 0; ab < 6; ++ab) {
-          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
-          const double Fab = ab == 0 ? F00 : ab == 1 ? F01 : ab == 2 ? F02 : ab == 3 ? F11 : ab == 4 ? F12 : F22;
-          G[ab][g] = (VT)((Fab * r) * (A[pa][0] * A[pb][0] + A[pa][1] * A[pb][1] + A[pa][2] * A[pb][2]));
-        }
+        const double M00 = q0[u1 + L * u2], M11 = q1[u0 + L * u2], M22 = q2[u0 + L * u1];
+        const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
+        const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
+        const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
+        const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
+        const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
+        const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
+        const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
+        const double r = lor_rsqrt(detM);  // 1 / det J_e
+        if constexpr (MASS) W[g] = (VT)(bR * (detM * r));
+        G[0][g] = (VT)(r * A00);
+        G[1][g] = (VT)(r * A01);
+        G[2][g] = (VT)(r * A02);
+        G[3][g] = (VT)(r * A11);
+        G[4][g] = (VT)(r * A12);
+        G[5][g] = (VT)(r * A22);
       }
     } else {
       // FP64: the first adjugate row and the determinant; FP32: the rest.
@@ -283,8 +329,14 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
           if ((mm >> aa) & 1)
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb)
-              if ((nn >> bb) & 1)
-                acc += (VT)inv_sqrt3_pow(popc3(mm) + popc3(nn) - 2) * G[pair_index(aa, bb)][walsh_index(mm, nn, aa, bb)];
+              if ((nn >> bb) & 1) {
+                if constexpr (F32)
+                  acc += (VT)inv_sqrt3_pow(popc3(mm) + popc3(nn) - 2) * G[pair_index(aa, bb)][walsh_index(mm, nn, aa, bb)];
+                else  // F_ab here, the common factor 3^(-(|m|+|n|-2)/2) once below
+                  acc = fma(FF[pair_index(aa, bb)], G[pair_index(aa, bb)][walsh_index(mm, nn, aa, bb)], acc);
+              }
+        if constexpr (!F32)
+          if (popc3(mm) + popc3(nn) > 2) acc *= inv_sqrt3_pow(popc3(mm) + popc3(nn) - 2);
         K[sym(mm, nn)] = acc;
       }
     if constexpr (MASS) {
@@ -300,7 +352,9 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
 
     // Scatter into the CSR values (closed-form positions on the structured
     // grid, binary search in the row on a general mesh), skipping essential
-    // rows and columns (their diagonal was pre-set to 1).
+    // rows and columns; an essential row's diagonal is set to 1 here (every
+    // DOF is a corner of some sub-hex; no atomic ever targets that row, and
+    // several sub-hexes may store the same 1).
     if constexpr (GEN) {
       constexpr int N = P + 1;
       const int64_t* dm = m.edofs + e * (N * N * N);
@@ -309,8 +363,12 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
       for (int r = 0; r < 8; ++r) dv[r] = dm[(a + (r & 1)) + N * ((b + ((r >> 1) & 1)) + N * (c + (r >> 2)))];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        if (m.ess[dv[r]]) continue;
         const int64_t rb = m.rowptr[dv[r]], re = m.rowptr[dv[r] + 1];
+        if (m.ess[dv[r]]) {
+          const int64_t pos = lor_find_col(m.colidx, rb, re, dv[r]);
+          if (pos >= 0) vals[pos] = (VT)1;
+          continue;
+        }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           if (m.ess[dv[t]]) continue;
@@ -324,8 +382,11 @@ __global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTable
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int64_t I = I0 + (r & 1), J = J0 + ((r >> 1) & 1), Kk = K0 + (r >> 2);
-        if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) continue;
         const int64_t base = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
+        if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) {
+          vals[base] = (VT)1;
+          continue;
+        }
         const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {

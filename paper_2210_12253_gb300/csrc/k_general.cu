@@ -281,104 +281,115 @@ __global__ void k_general_vertices(LorMesh m, LorTables T, const unsigned long l
 
 }  // namespace
 
-cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr_out, int32_t** colidx_out, int64_t* nnz_out,
-                                int* d_status, cudaStream_t s) {
+// A block allocated through the context's allocator, released on scope exit
+// unless kept.
+template <typename T>
+struct DevBuf {
+  const LorDeviceAlloc& A;
+  T* p = nullptr;
+  size_t bytes = 0;
+  explicit DevBuf(const LorDeviceAlloc& a) : A(a) {}
+  cudaError_t get(int64_t count) {
+    bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    return A.alloc(A.ctx, (void**)&p, bytes);
+  }
+  T* keep() {
+    T* q = p;
+    p = nullptr;
+    return q;
+  }
+  ~DevBuf() {
+    if (p) A.release(A.ctx, p, bytes);
+  }
+};
+
+cudaError_t lor_general_pattern(const LorMesh& m, const LorDeviceAlloc& A, int64_t** rowptr_out, int32_t** colidx_out,
+                                int64_t* nnz_out, int* d_status, cudaStream_t s) {
   const int64_t n = m.ndof;
   const int64_t nb = (n + kChunk - 1) / kChunk + 1;
-  int64_t *off = nullptr, *cur = nullptr, *scratch = nullptr, *rowptr = nullptr;
-  int32_t *list = nullptr, *colidx = nullptr;
+  DevBuf<int64_t> off(A), cur(A), scratch(A), rowptr(A);
+  DevBuf<int32_t> list(A), colidx(A);
   int64_t total = 0, nnz = 0;
-  cudaError_t err = cudaMalloc(&off, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMalloc(&cur, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMalloc(&scratch, sizeof(int64_t) * nb);
-  if (err == cudaSuccess) err = cudaMemsetAsync(off, 0, sizeof(int64_t) * (n + 1), s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(cur, 0, sizeof(int64_t) * (n + 1), s);
+  cudaError_t err = off.get(n + 1);
+  if (err == cudaSuccess) err = cur.get(n + 1);
+  if (err == cudaSuccess) err = scratch.get(nb);
+  if (err == cudaSuccess) err = cudaMemsetAsync(off.p, 0, sizeof(int64_t) * (n + 1), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(cur.p, 0, sizeof(int64_t) * (n + 1), s);
   if (err == cudaSuccess) {
-    k_incidence_count<<<grid_for(m.nel * (int64_t)m.p * m.p * m.p * 8), kT, 0, s>>>(m, off, d_status);
+    k_incidence_count<<<grid_for(m.nel * (int64_t)m.p * m.p * m.p * 8), kT, 0, s>>>(m, off.p, d_status);
     lor_count_launch();
-    err = exclusive_scan(off, n, scratch, s);
+    err = exclusive_scan(off.p, n, scratch.p, s);
   }
-  if (err == cudaSuccess) err = cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&total, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  if (err == cudaSuccess) err = cudaMalloc(&list, sizeof(int32_t) * (total > 0 ? total : 1));
+  if (err == cudaSuccess) err = list.get(total);
   if (err == cudaSuccess) {
-    k_incidence_fill<<<grid_for(m.nel * (int64_t)m.p * m.p * m.p * 8), kT, 0, s>>>(m, off, cur, list);
+    k_incidence_fill<<<grid_for(m.nel * (int64_t)m.p * m.p * m.p * 8), kT, 0, s>>>(m, off.p, cur.p, list.p);
     lor_count_launch();
-    k_row_sort_count<<<grid_for(n), kT, 0, s>>>(n, off, list, cur, d_status); lor_count_launch();
+    k_row_sort_count<<<grid_for(n), kT, 0, s>>>(n, off.p, list.p, cur.p, d_status); lor_count_launch();
     err = cudaGetLastError();
   }
-  if (err == cudaSuccess) err = cudaMalloc(&rowptr, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMemcpyAsync(rowptr, cur, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
-  if (err == cudaSuccess) err = exclusive_scan(rowptr, n, scratch, s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = rowptr.get(n + 1);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(rowptr.p, cur.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
+  if (err == cudaSuccess) err = exclusive_scan(rowptr.p, n, scratch.p, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&nnz, rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  if (err == cudaSuccess) err = cudaMalloc(&colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  if (err == cudaSuccess) err = colidx.get(nnz);
   if (err == cudaSuccess) {
-    k_row_write<<<grid_for(n), kT, 0, s>>>(n, off, list, rowptr, colidx); lor_count_launch();
+    k_row_write<<<grid_for(n), kT, 0, s>>>(n, off.p, list.p, rowptr.p, colidx.p); lor_count_launch();
     err = cudaGetLastError();
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  cudaFree(off);
-  cudaFree(cur);
-  cudaFree(scratch);
-  cudaFree(list);
   if (err != cudaSuccess) {
-    cudaFree(rowptr);
-    cudaFree(colidx);
+    cudaStreamSynchronize(s);  // nothing queued may still use a block freed on the way out
     return err;
   }
-  *rowptr_out = rowptr;
-  *colidx_out = colidx;
+  *rowptr_out = rowptr.keep();
+  *colidx_out = colidx.keep();
   *nnz_out = nnz;
   return cudaSuccess;
 }
 
-cudaError_t lor_general_edges(const LorMesh& m, int32_t** tail_out, int32_t** head_out, int64_t* nedge_out,
-                              int* d_status, cudaStream_t s) {
+cudaError_t lor_general_edges(const LorMesh& m, const LorDeviceAlloc& A, int32_t** tail_out, int32_t** head_out,
+                              int64_t* nedge_out, int* d_status, cudaStream_t s) {
   const int64_t n = m.ndof;
   const int64_t nb = (n + kChunk - 1) / kChunk + 1;
   const int64_t nw = m.nel * (int64_t)m.p * m.p * m.p * 12;
-  int64_t *off = nullptr, *cur = nullptr, *scratch = nullptr, *estart = nullptr;
-  int32_t *list = nullptr, *tail = nullptr, *head = nullptr;
+  DevBuf<int64_t> off(A), cur(A), scratch(A), estart(A);
+  DevBuf<int32_t> list(A), tail(A), head(A);
   int64_t nedge = 0;
-  cudaError_t err = cudaMalloc(&off, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMalloc(&cur, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMalloc(&estart, sizeof(int64_t) * (n + 1));
-  if (err == cudaSuccess) err = cudaMalloc(&scratch, sizeof(int64_t) * nb);
-  if (err == cudaSuccess) err = cudaMalloc(&list, sizeof(int32_t) * (nw > 0 ? nw : 1));
-  if (err == cudaSuccess) err = cudaMemsetAsync(off, 0, sizeof(int64_t) * (n + 1), s);
-  if (err == cudaSuccess) err = cudaMemsetAsync(cur, 0, sizeof(int64_t) * (n + 1), s);
+  cudaError_t err = off.get(n + 1);
+  if (err == cudaSuccess) err = cur.get(n + 1);
+  if (err == cudaSuccess) err = estart.get(n + 1);
+  if (err == cudaSuccess) err = scratch.get(nb);
+  if (err == cudaSuccess) err = list.get(nw);
+  if (err == cudaSuccess) err = cudaMemsetAsync(off.p, 0, sizeof(int64_t) * (n + 1), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(cur.p, 0, sizeof(int64_t) * (n + 1), s);
   if (err == cudaSuccess) {
-    k_edge_count<<<grid_for(nw), kT, 0, s>>>(m, off); lor_count_launch();
-    err = exclusive_scan(off, n, scratch, s);
+    k_edge_count<<<grid_for(nw), kT, 0, s>>>(m, off.p); lor_count_launch();
+    err = exclusive_scan(off.p, n, scratch.p, s);
   }
   if (err == cudaSuccess) {
-    k_edge_fill<<<grid_for(nw), kT, 0, s>>>(m, off, cur, list); lor_count_launch();
-    k_row_sort_count<<<grid_for(n), kT, 0, s>>>(n, off, list, cur, d_status); lor_count_launch();
-    err = cudaMemcpyAsync(estart, cur, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
+    k_edge_fill<<<grid_for(nw), kT, 0, s>>>(m, off.p, cur.p, list.p); lor_count_launch();
+    k_row_sort_count<<<grid_for(n), kT, 0, s>>>(n, off.p, list.p, cur.p, d_status); lor_count_launch();
+    err = cudaMemcpyAsync(estart.p, cur.p, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
   }
-  if (err == cudaSuccess) err = exclusive_scan(estart, n, scratch, s);
-  if (err == cudaSuccess) err = cudaMemcpyAsync(&nedge, estart + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = exclusive_scan(estart.p, n, scratch.p, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&nedge, estart.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  if (err == cudaSuccess) err = cudaMalloc(&tail, sizeof(int32_t) * (nedge > 0 ? nedge : 1));
-  if (err == cudaSuccess) err = cudaMalloc(&head, sizeof(int32_t) * (nedge > 0 ? nedge : 1));
+  if (err == cudaSuccess) err = tail.get(nedge);
+  if (err == cudaSuccess) err = head.get(nedge);
   if (err == cudaSuccess) {
-    k_edge_write<<<grid_for(n), kT, 0, s>>>(n, off, list, estart, tail, head); lor_count_launch();
+    k_edge_write<<<grid_for(n), kT, 0, s>>>(n, off.p, list.p, estart.p, tail.p, head.p); lor_count_launch();
     err = cudaGetLastError();
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  cudaFree(off);
-  cudaFree(cur);
-  cudaFree(estart);
-  cudaFree(scratch);
-  cudaFree(list);
   if (err != cudaSuccess) {
-    cudaFree(tail);
-    cudaFree(head);
+    cudaStreamSynchronize(s);
     return err;
   }
-  *tail_out = tail;
-  *head_out = head;
+  *tail_out = tail.keep();
+  *head_out = head.keep();
   *nedge_out = nedge;
   return cudaSuccess;
 }

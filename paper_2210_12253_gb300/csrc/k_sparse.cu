@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce_final(const double* __restr
 // Each dot product finishes in the last CTA to arrive (arrival counted with
 // an atomic after a fence; that CTA sums the per-CTA partials in index order,
 // so the result does not depend on which CTA finishes last, and resets the
-// counter).  No CTA waits for another.
-__device__ __forceinline__ void finish_sums(double s0, double s1, int nsum, double* __restrict__ partial,
+// counter).  No CTA waits for another.  Returns true in the last CTA.
+__device__ __forceinline__ bool finish_sums(double s0, double s1, int nsum, double* __restrict__ partial,
                                             unsigned* __restrict__ counter, double* __restrict__ out0,
                                             double* __restrict__ out1) {
   __shared__ bool last;
@@ -115,7 +115,7 @@ __device__ __forceinline__ void finish_sums(double s0, double s1, int nsum, doub
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   const volatile double* vp = partial;
   double t0 = 0.0, t1 = 0.0;
@@ -130,6 +130,7 @@ __device__ __forceinline__ void finish_sums(double s0, double s1, int nsum, doub
     if (nsum > 1) *out1 = t1;
     *counter = 0;
   }
+  return true;
 }
 
 
@@ -359,7 +360,10 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     // the barrier that ended the previous iteration)
     if (threadIdx.x == 0 && t + stride < ntiles)
       base[b ^ 1] = issue_tile<VT>(m, vals, t + stride, b ? buf0 : buf1, &bar[b ^ 1]);
-    if (!mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u)) abort_flag = 1;
+    // (a test hook makes the wait count as expired: the copy still lands and
+    // is waited for below)
+    const bool landed = !(m.test_flags & LOR_TEST_EXPIRE_WAITS) && mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
+    if (!landed) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
     const VT* sv = b ? buf1 : buf0;
@@ -373,8 +377,12 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
   }
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, LOR_FLAG_TIMEOUT);
-    // let a prefetch that is still in flight land before the CTA exits
+    // Let every copy this CTA issued land before it exits, each wait again
+    // bounded: the tile whose wait gave up (after a real expiry this wait
+    // gives up too, and the CTA can only exit with that copy pending if the
+    // copy never completes) and the next tile's prefetch if one is in flight.
     const int b = it & 1;
+    mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
     if (blockIdx.x + (int64_t)(it + 1) * stride < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
   }
   if constexpr (MODE == ST_CHEB_DOT) finish_sums((double)acc, 0.0, 1, partial, counter, out, nullptr);
@@ -416,7 +424,9 @@ __global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restric
 
 // Persistent grid: every SM filled to the kernel's occupancy (at most one CTA
 // per tile; the reducing mode at most LOR_PCG_MAX_BLOCKS CTAs).  The shared
-// memory limit is raised once per device.
+// memory limit is raised once per device and the grid size cached for the
+// life of the process (one primary context per device: a cudaDeviceReset
+// would drop the attribute).
 template <typename VT, typename XT, int MODE, typename V>
 cudaError_t stencil_grid(const LorMesh& m, int* grid) {
   static int per_device[64] = {};
@@ -661,6 +671,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dot(int64_t n, const V* __rest
 //   mode 2 (Chebyshev, degree 1): z = D^-1 r / theta;
 //   mode 3 (Chebyshev, degree >= 2): zA = d = D^-1 r / theta (smoother precision).
 // Modes 0-2 also form r.z (z is final there).
+//
+// Convergence record rec (device): rec[0] = r.r, rec[1] = 1 when
+// r.r <= stop_rr (the stopping test of this iteration), rec[2] = the status
+// word; written by the last CTA, copied to the host in one read.  The host
+// queues the next iteration before it reads this one's record, so the next
+// iteration's update and direction kernels start by testing rec[1]: behind a
+// converged iteration they change nothing (x, r, p, q and the scalars keep
+// the converged iteration's values).
 template <typename VT, typename V = double>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double* __restrict__ S, int rz_slot,
                                                          const V* __restrict__ p, const V* __restrict__ q,
@@ -669,7 +687,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double
                                                          V* __restrict__ z, VT* __restrict__ zA,
                                                          VT* __restrict__ d, double* __restrict__ partial,
                                                          unsigned* __restrict__ counter, double* __restrict__ out_rr,
-                                                         double* __restrict__ out_rz) {
+                                                         double* __restrict__ out_rz, double stop_rr,
+                                                         double* __restrict__ rec, const int* __restrict__ status) {
+  if (*(volatile double*)(rec + 1) != 0.0) return;  // behind a converged iteration
   const double alpha = S[rz_slot] / S[S_PQ];
   const V av = (V)alpha;
   Acc<V> srr = 0, srz = 0;
@@ -691,14 +711,24 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n, const double
       d[i] = zi;
     }
   }
-  finish_sums((double)srr, (double)srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz);
+  if (finish_sums((double)srr, (double)srz, mode <= 2 ? 2 : 1, partial, counter, out_rr, out_rz) &&
+      threadIdx.x == 0) {
+    const double rr = *out_rr;
+    rec[0] = rr;
+    rec[2] = (double)*(const volatile int*)status;
+    __threadfence();
+    rec[1] = rr <= stop_rr ? 1.0 : 0.0;
+  }
 }
 
 // p = z + beta p (beta = rz_new / rz_old; first: p = z) and the output of
-// the next apply initialised: q = p on essential DOFs, 0 elsewhere.
+// the next apply initialised: q = p on essential DOFs, 0 elsewhere.  Does
+// nothing behind a converged iteration (rec[1] set, see k_pcg_update).
 template <typename V = double>
 __global__ void k_pcg_direction(LorMesh m, const double* __restrict__ S, int new_slot, int old_slot, int first,
-                                const V* __restrict__ z, V* __restrict__ p, V* __restrict__ q) {
+                                const V* __restrict__ z, V* __restrict__ p, V* __restrict__ q,
+                                const double* __restrict__ rec) {
+  if (*(const volatile double*)(rec + 1) != 0.0) return;
   const V beta = (V)(first ? 0.0 : S[new_slot] / S[old_slot]);
   LOR_GRID_STRIDE(i, m.ndof) {
     const V pi = first ? z[i] : z[i] + beta * p[i];
@@ -773,15 +803,32 @@ cudaError_t pcg_precond_rest(lor_ctx* c, const VT* vals, const VT* dinv, const V
 
 template <typename VT, typename V = double>
 cudaError_t pcg_update(lor_ctx* c, const VT* dinv, double* S, int cur, const V* p, const V* q, double* x, V* r,
-                       V* z, int mode, double* out_rz, int grid, cudaStream_t s) {
+                       V* z, int mode, double* out_rz, double stop_rr, double* rec, int grid, cudaStream_t s) {
   const double theta = 0.5 * (c->pc_hi + c->pc_lo);
   VT* zA = (VT*)c->pc_work;
   VT* d = zA ? zA + 2 * c->m.ndof : nullptr;
   k_pcg_update<VT, V><<<grid, kThreads, 0, s>>>(c->m.ndof, S, cur, p, q, x, r, mode, dinv,
                                                    (VT)(theta > 0 ? 1.0 / theta : 1.0), z, zA, d, pcg_partials(c),
-                                                   c->red_count, S + S_RR, out_rz); lor_count_launch();
+                                                   c->red_count, S + S_RR, out_rz, stop_rr, rec, c->d_status);
+  lor_count_launch();
   return cudaGetLastError();
 }
+
+// The two events of the iteration records (below), destroyed on every exit.
+struct EventPair {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t create() {
+    for (auto& e : ev) {
+      const cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+  }
+  ~EventPair() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
 
 __global__ void k_add(int64_t n, double* __restrict__ x, const double* __restrict__ d) {
   LOR_GRID_STRIDE(i, n) x[i] += d[i];
@@ -811,7 +858,12 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   V* q = p + n;
   double* ax64 = c->pcg_work + 2 * n;
   double* S = c->red + LOR_RED_BLOCKS;  // S[0] = p.q, S[1] = r.r, S[2] = b.b, S[3], S[4] = r.z (alternating)
+  double* rec = S + 8;                  // the latest update's record: r.r, converged flag, status word
   double* hs = c->h_scalar;
+  // Host copies of the records of two consecutive iterations (pinned), each
+  // complete when its event has passed.
+  auto hrec = [&](int k) { return hs + 8 + 3 * (k & 1); };
+  EventPair evs;
   const int g = grid_rows(n);
   const bool f64 = c->pc_dtype == LOR_F64;
   // preconditioner mode of the fused update (see k_pcg_update)
@@ -822,7 +874,9 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   auto dot = [&](const V* a, const V* bb, double* out) {
     k_pcg_dot<V><<<g_dot, kThreads, 0, s>>>(n, a, bb, pcg_partials(c), c->red_count, out); lor_count_launch();
   };
-  cudaError_t err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
+  auto other = [](int slot) { return slot == S_RZ0 ? S_RZ1 : S_RZ0; };
+  cudaError_t err = evs.create();
+  if (err == cudaSuccess) err = cudaMemsetAsync(x, 0, sizeof(double) * n, s);
   if (err == cudaSuccess) {
     if constexpr (VF) err = lor_launch_to_f32(b, r, n, s);
     else err = cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
@@ -839,87 +893,132 @@ int pcg_core(lor_ctx* c, const double* b, double* x, double rtol, int maxit, boo
   double rel = 0.0, last_true = 1.0;
   int status = LOR_ENOCONV;
   const char* why = "pcg: no convergence within maxit";
+  // One iteration: q += A p, p.q, then the fused update, which also tests
+  // |r|^2 <= (trigger |b|)^2 and records the result; the record is read on
+  // the host one iteration late (the next iteration is already queued).
+  auto queue_iteration = [&](int k, int cur, double trigger) -> cudaError_t {
+    cudaError_t e;
+    if constexpr (VF) {
+      e = lor_launch_apply_f32v_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s);
+    } else {
+      e = f32_apply ? lor_launch_apply_f32_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s)
+                    : lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
+    }
+    if (e != cudaSuccess) return e;
+    dot(p, q, S + S_PQ);
+    const double stop = trigger * nb;
+    e = f64 ? pcg_update<double, V>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + other(cur), stop * stop, rec,
+                                    g_upd, s)
+            : pcg_update<float, V>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + other(cur), stop * stop, rec,
+                                   g_upd, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hrec(k), rec, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(evs.ev[k & 1], s);
+    return e;
+  };
+  // The rest of the preconditioner on the updated r (Chebyshev degree >= 2)
+  // and the next search direction (a no-op behind a converged iteration).
+  auto queue_tail = [&](int cur) -> cudaError_t {
+    const int nxt = other(cur);
+    if (mode == 3) {
+      const cudaError_t e = f64 ? pcg_precond_rest<double, V>(c, c->vals64, c->dinv64, r, z, S + nxt, s)
+                                : pcg_precond_rest<float, V>(c, c->vals32, c->dinv32, r, z, S + nxt, s);
+      if (e != cudaSuccess) return e;
+    }
+    k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q, rec); lor_count_launch();
+    return cudaGetLastError();
+  };
+  auto trigger_now = [&]() { return replace > 0.0 ? fmax(rtol, replace * last_true) : rtol; };
   if (nb == 0.0) {
     status = LOR_OK;
-  } else {
+  } else if (maxit > 0) {
     int rc = precond_apply_v<V>(c, r, z, s);
     if (rc) return rc;
     int cur = S_RZ0;
     dot(r, z, S + cur);
-    k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q); lor_count_launch();
-    while (it < maxit) {
-      if constexpr (VF) {
-        err = lor_launch_apply_f32v_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s);
-      } else {
-        err = f32_apply
-                  ? lor_launch_apply_f32_accumulate(c->m, c->T, c->Dq32, c->have_beta ? c->Mq32 : nullptr, p, q, s)
-                  : lor_launch_apply_accumulate(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, p, q, s);
+    err = cudaMemsetAsync(rec, 0, 3 * sizeof(double), s);
+    if (err != cudaSuccess) return fail(c, err, "pcg");
+    k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, cur, cur, 1, z, p, q, rec); lor_count_launch();
+    double trigger = trigger_now();
+    err = queue_iteration(0, cur, trigger);
+    if (err != cudaSuccess) return fail(c, err, "pcg");
+    // Loop invariant: iteration `it` (0-based) is queued and its record not yet read.
+    while (true) {
+      const int nxt = other(cur);
+      const bool ahead = it + 1 < maxit;
+      if (ahead) {  // queue the next iteration before waiting for this one's record
+        err = queue_tail(cur);
+        if (err == cudaSuccess) err = queue_iteration(it + 1, nxt, trigger);
+        if (err != cudaSuccess) return fail(c, err, "pcg");
       }
-      if (err != cudaSuccess) return fail(c, err, "pcg apply");
-      dot(p, q, S + S_PQ);
-      const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
-      err = f64 ? pcg_update<double, V>(c, c->dinv64, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s)
-                : pcg_update<float, V>(c, c->dinv32, S, cur, p, q, x, r, z, mode, S + nxt, g_upd, s);
-      if (err == cudaSuccess) err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
-      if (err == cudaSuccess) err = queue_status_read(c, s);
-      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      err = cudaEventSynchronize(evs.ev[it & 1]);
       if (err != cudaSuccess) return fail(c, err, "pcg");
-      if (int trc = timed_out(c, "pcg")) return trc;
+      const double* hr = hrec(it);
+      const int flags = (int)hr[2];
+      if (flags & LOR_FLAG_TIMEOUT) {
+        c->err = "pcg: a bounded device wait expired (a bulk copy into shared memory never completed)";
+        return LOR_ETIMEOUT;
+      }
       ++it;
-      rel = sqrt(hs[0]) / nb;
-      bool restarted = false;
-      const double trigger = replace > 0.0 ? fmax(rtol, replace * last_true) : rtol;
-      if (rel <= trigger && !confirm) {
+      rel = sqrt(hr[0]) / nb;
+      if (hr[1] == 0.0) {  // not converged: the next iteration is already queued
+        if (!ahead) break;
+        cur = nxt;
+        continue;
+      }
+      // Converged on the recurrence residual; the iteration queued behind it
+      // changed nothing.
+      if (!confirm) {
         status = LOR_OK;
         break;
       }
-      if (rel <= trigger) {
-        // confirm on the true residual b - A x (FP64 operator)
-        if constexpr (VF) {
-          err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, ax64, s);
-          if (err == cudaSuccess) {
-            k_residual_norm<V><<<g_dot64, kThreads, 0, s>>>(n, b, ax64, r, pcg_partials(c), c->red_count, S + S_RR);
-            lor_count_launch();
-            err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
-          }
-        } else {
-          err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
-          if (err == cudaSuccess) {
-            k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
-            dot(r, r, S + S_RR);
-            err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
-          }
+      // confirm on the true residual b - A x (FP64 operator)
+      if constexpr (VF) {
+        err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, ax64, s);
+        if (err == cudaSuccess) {
+          k_residual_norm<V><<<g_dot64, kThreads, 0, s>>>(n, b, ax64, r, pcg_partials(c), c->red_count, S + S_RR);
+          lor_count_launch();
+          err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
-        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-        if (err != cudaSuccess) return fail(c, err, "pcg");
-        rel = sqrt(hs[0]) / nb;
-        if (rel <= rtol) {
-          status = LOR_OK;
+      } else {
+        err = lor_launch_apply(c->m, c->T, c->Dq, c->have_beta ? c->Mq : nullptr, x, q, s);
+        if (err == cudaSuccess) {
+          k_residual<<<g, kThreads, 0, s>>>(n, b, q, r); lor_count_launch();
+          dot(r, r, S + S_RR);
+          err = cudaMemcpyAsync(hs, S + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+        }
+      }
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err != cudaSuccess) return fail(c, err, "pcg");
+      rel = sqrt(hs[0]) / nb;
+      if (rel <= rtol) {
+        status = LOR_OK;
+        break;
+      }
+      if (replace > 0.0) {
+        if (!(rel < last_true)) {
+          why = "pcg: a residual replacement did not lower the true residual";
           break;
         }
-        if (replace > 0.0) {
-          if (!(rel < last_true)) {
-            why = "pcg: a residual replacement did not lower the true residual";
-            break;
-          }
-          last_true = rel;
-          ++nrep;
-        }
-        // continue from the true residual: precondition it afresh
-        rc = precond_apply_v<V>(c, r, z, s);
-        if (rc) return rc;
-        dot(r, z, S + nxt);
-        restarted = true;
+        last_true = rel;
+        ++nrep;
       }
-      if (!restarted && mode == 3) {
-        err = f64 ? pcg_precond_rest<double, V>(c, c->vals64, c->dinv64, r, z, S + nxt, s)
-                  : pcg_precond_rest<float, V>(c, c->vals32, c->dinv32, r, z, S + nxt, s);
-        if (err != cudaSuccess) return fail(c, err, "pcg precond");
-      }
-      k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q); lor_count_launch();
+      // continue from the true residual (keeping the search direction):
+      // precondition it afresh and clear the converged flag
+      err = cudaMemsetAsync(rec, 0, 3 * sizeof(double), s);
+      if (err != cudaSuccess) return fail(c, err, "pcg");
+      rc = precond_apply_v<V>(c, r, z, s);
+      if (rc) return rc;
+      dot(r, z, S + nxt);
+      k_pcg_direction<V><<<g, kThreads, 0, s>>>(c->m, S, nxt, cur, 0, z, p, q, rec); lor_count_launch();
       cur = nxt;
+      trigger = trigger_now();
+      if (it >= maxit) break;
+      err = queue_iteration(it, cur, trigger);
+      if (err != cudaSuccess) return fail(c, err, "pcg");
     }
-    err = cudaGetLastError();
+    // drain what was queued behind the last record read
+    err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess) err = cudaGetLastError();
     if (err != cudaSuccess) return fail(c, err, "pcg");
   }
   if (iters) *iters = it;
@@ -1048,7 +1147,8 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of lor_noalloc_scratch on the current device (looked up once
 // per device, with that device current; the host-side symbol itself is not a
-// device address).
+// device address).  Cached for the life of the process: this assumes one
+// primary context per device (after a cudaDeviceReset it would be stale).
 cudaError_t noalloc_scratch(void** out) {
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);

@@ -199,6 +199,39 @@ int alloc(lor_ctx* c, T** p, size_t count, const char* what) {
 
 cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
+// The same budget for blocks allocated by the general-mesh builders.
+cudaError_t ctx_device_alloc(void* cv, void** p, size_t bytes) {
+  lor_ctx* c = (lor_ctx*)cv;
+  const size_t limit = device_alloc_limit();
+  if (c->device_bytes > limit || bytes > limit - c->device_bytes) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e;
+  }
+  c->device_bytes += bytes;
+  return cudaSuccess;
+}
+
+void ctx_device_release(void* cv, void* p, size_t bytes) {
+  lor_ctx* c = (lor_ctx*)cv;
+  cudaFree(p);
+  c->device_bytes -= bytes;
+}
+
+LorDeviceAlloc device_allocator(lor_ctx* c) { return LorDeviceAlloc{c, ctx_device_alloc, ctx_device_release}; }
+
+// A failed allocation through the budget is LOR_ENOMEM, anything else LOR_ECUDA.
+int builder_err(lor_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_err(c, LOR_ENOMEM, std::string("device allocation failed: ") + what);
+  return cuda_err(c, e, what);
+}
+
 void free_all(lor_ctx* c) {
   cudaFree(c->verts);
   cudaFree(c->Dq);
@@ -382,8 +415,11 @@ int lor_create_general(lor_ctx** out, int p, int64_t nel, int64_t ndof, const do
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), S(stream));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->red_count, 0, 8 * sizeof(unsigned), S(stream));
     if (e == cudaSuccess) e = lor_launch_geometry_check(m, c->T, c->d_status, S(stream));
-    if (e == cudaSuccess) e = lor_general_pattern(m, &c->rowptr, &c->colidx, &m.nnz, c->d_status, S(stream));
     if (e != cudaSuccess) rc = cuda_err(c, e, "lor_create_general");
+  }
+  if (!rc) {
+    e = lor_general_pattern(m, device_allocator(c), &c->rowptr, &c->colidx, &m.nnz, c->d_status, S(stream));
+    if (e != cudaSuccess) rc = builder_err(c, e, "lor_create_general: LOR pattern");
   }
   int flags = 0;
   if (!rc) rc = read_status(c, S(stream), &flags);
@@ -488,8 +524,9 @@ int lor_discrete_gradient(lor_ctx* c, int64_t* d_rowptr, int32_t* d_colidx, doub
                           void* stream) {
   if (!c) return LOR_EINVAL;
   if (c->general && c->nedge < 0) {  // enumerate the LOR edges once
-    cudaError_t e = lor_general_edges(c->m, &c->etail, &c->ehead, &c->nedge, c->d_status, S(stream));
-    if (e != cudaSuccess) return cuda_err(c, e, "lor_discrete_gradient: edges");
+    cudaError_t e = lor_general_edges(c->m, device_allocator(c), &c->etail, &c->ehead, &c->nedge, c->d_status,
+                                      S(stream));
+    if (e != cudaSuccess) return builder_err(c, e, "lor_discrete_gradient: LOR edges");
   }
   const int64_t ne = c->general ? c->nedge : lor_edge_count(c->m);
   if (nedge) *nedge = ne;
@@ -528,6 +565,13 @@ int lor_check(lor_ctx* c, void* stream) {
       return set_err(c, LOR_EINVAL, "lor_assemble_unstructured: a coupling is missing from the given CSR pattern");
     return set_err(c, LOR_EINVAL, "kappa (and beta) must be finite and > 0 at every Gauss point");
   }
+  return LOR_OK;
+}
+
+int lor_set_test_hooks(lor_ctx* c, unsigned flags) {
+  if (!c) return LOR_EINVAL;
+  if (flags & ~LOR_TEST_EXPIRE_WAITS) return set_err(c, LOR_EINVAL, "lor_set_test_hooks: unknown flag");
+  c->m.test_flags = flags;
   return LOR_OK;
 }
 

@@ -47,6 +47,7 @@ struct LorMesh {
   const uint8_t* ess = nullptr;
   const int64_t* rowptr = nullptr;
   const int32_t* colidx = nullptr;
+  unsigned test_flags = 0;  // lor_set_test_hooks (LOR_TEST_EXPIRE_WAITS)
 };
 
 struct lor_ctx {
@@ -288,15 +289,26 @@ cudaError_t lor_launch_assemble_unstructured(int64_t nsub, const double* corners
                                              const double* ksub, const double* bsub, int64_t n, int64_t nnz,
                                              const int64_t* rowptr, const int32_t* colidx, const uint8_t* ess,
                                              void* vals, int dtype, int* status, cudaStream_t s);
+// The context's device allocator, handed to the general-mesh builders so that
+// their temporaries and results count against the same budget as the
+// context's own buffers (LOR_DEVICE_ALLOC_LIMIT): alloc fails with
+// cudaErrorMemoryAllocation past the limit without calling the runtime;
+// release frees a block and uncounts its bytes.
+struct LorDeviceAlloc {
+  void* ctx;
+  cudaError_t (*alloc)(void* ctx, void** p, size_t bytes);
+  void (*release)(void* ctx, void* p, size_t bytes);
+};
 // general meshes (k_general.cu): LOR pattern from the element-to-DOF map
-// (allocates *rowptr and *colidx, sets *nnz; synchronises), map validation
-cudaError_t lor_general_pattern(const LorMesh& m, int64_t** rowptr, int32_t** colidx, int64_t* nnz, int* d_status,
-                                cudaStream_t s);
+// (allocates *rowptr and *colidx through A, sets *nnz; synchronises), map
+// validation
+cudaError_t lor_general_pattern(const LorMesh& m, const LorDeviceAlloc& A, int64_t** rowptr, int32_t** colidx,
+                                int64_t* nnz, int* d_status, cudaStream_t s);
 // the LOR edges of a general mesh (tail < head, ordered by tail then head;
-// allocates *tail and *head, synchronises), the discrete gradient from them,
-// and the vertex coordinates through the map
-cudaError_t lor_general_edges(const LorMesh& m, int32_t** tail, int32_t** head, int64_t* nedge, int* d_status,
-                              cudaStream_t s);
+// allocates *tail and *head through A, synchronises), the discrete gradient
+// from them, and the vertex coordinates through the map
+cudaError_t lor_general_edges(const LorMesh& m, const LorDeviceAlloc& A, int32_t** tail, int32_t** head,
+                              int64_t* nedge, int* d_status, cudaStream_t s);
 cudaError_t lor_launch_general_gradient(int64_t nedge, const int32_t* tail, const int32_t* head, int64_t* rowptr,
                                         int32_t* colidx, double* values, cudaStream_t s);
 cudaError_t lor_launch_general_vertices(const LorMesh& m, const LorTables& T, double* xyz, cudaStream_t s);

@@ -17,6 +17,7 @@ LOR_F64, LOR_F32 = 0, 1
 LOR_PRECOND_NONE, LOR_PRECOND_JACOBI, LOR_PRECOND_CHEB = 0, 1, 2
 LOR_IR_RESTART, LOR_IR_REPLACE = 0, 1
 LOR_MAX_P = 10
+LOR_TEST_EXPIRE_WAITS = 1
 
 EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
@@ -24,7 +25,7 @@ EXPORTED = [
     "lor_precond_setup", "lor_precond_apply", "lor_pcg_solve", "lor_launch_count",
     "lor_precond_apply_noalloc", "lor_set_reaction", "lor_lor_mesh", "lor_assemble_unstructured",
     "lor_discrete_gradient", "lor_vertex_coordinates", "lor_create_general", "lor_apply_f32",
-    "lor_pcg_solve_ir",
+    "lor_pcg_solve_ir", "lor_set_test_hooks",
 ]
 
 
@@ -75,6 +76,8 @@ def load_library(path=LIB):
     L.lor_assemble_unstructured.argtypes = [vp, i64, vp, vp, vp, vp, i64, i64, vp, vp, vp, vp, i, vp]
     L.lor_check.restype = i
     L.lor_check.argtypes = [vp, vp]
+    L.lor_set_test_hooks.restype = i
+    L.lor_set_test_hooks.argtypes = [vp, C.c_uint]
     L.lor_build_pattern.restype = i
     L.lor_build_pattern.argtypes = [vp, vp, vp, vp]
     L.lor_assemble.restype = i
@@ -238,6 +241,11 @@ class LOR:
 
     def check(self):
         self._call("lor_check")
+
+    def set_test_hooks(self, flags):
+        """Test hooks (LOR_TEST_EXPIRE_WAITS: the TMA-staged kernels treat
+        their first bounded wait as expired); 0 clears them."""
+        self._call("lor_set_test_hooks", C.c_uint(flags), stream=False)
 
     def build_pattern(self, rowptr=None, colidx=None):
         """Step S1.2 A2: CSR pattern (rowptr int64[N+1], colidx int32[nnz])."""

@@ -123,7 +123,7 @@ def test_every_entry_point_rejects_a_null_context(libpath):
         fn = getattr(L, name)
         args = []
         for t in fn.argtypes:
-            if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+            if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint):
                 args.append(0)
             elif t is ctypes.c_double:
                 args.append(0.0)

@@ -1,9 +1,10 @@
 """Parity at the measured sizes, in the launch configuration bench.py times.
 
-* 16^3 elements, p = 4 (274,625 DOFs; the benchmark step): sparsity and LOR
-  values on sampled rows (the oracle computes each row alone), the full
-  high-order apply and backward, SpMV and the Chebyshev-Jacobi smoother
-  against the oracle's own assembled CSR.
+* 16^3 elements, p = 4 (274,625 DOFs; the benchmark step): the whole LOR
+  CSR (pattern bit-exact, all 7,189,057 values in FP64 and FP32) against the
+  oracle's assembled CSR, sampled rows against the oracle's rows computed
+  alone, the full high-order apply and backward, SpMV and the
+  Chebyshev-Jacobi smoother.
 * 32^3 elements, p = 6 (7,189,057 DOFs; the PCG workload): sampled LOR rows,
   the full apply (FP64 and FP32 arithmetic), and PCG to 1e-8 in FP64, mixed
   precision and the mixed-precision refinement (both schemes), whose true
@@ -67,12 +68,26 @@ def check_rows(prob, mesh, op, rows, tol, dtype):
         assert np.abs(v[a:b] - ref).max() <= tol * np.abs(ref).max()
 
 
+def rowwise_max_rel_err(rp, v, ref):
+    """max over rows of max|v - ref| / max|ref| on the row (every row non-empty)."""
+    err = np.maximum.reduceat(np.abs(v - ref), rp[:-1])
+    scale = np.maximum.reduceat(np.abs(ref), rp[:-1])
+    return (err / scale).max()
+
+
 def test_step_workload_16x16x16_p4():
     prob, mesh, op = setup("c2_16x16x16_p4")
     p, q = prob.p, prob.q
-    rows = sample_rows(prob, 3000, 1)
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
+    rp, ci = op.build_pattern()
+    np.testing.assert_array_equal(rp.cpu().numpy(), csr[0])
+    np.testing.assert_array_equal(ci.cpu().numpy().astype(np.int64), csr[1])
+    assert csr[2].size == 7189057
+    for dtype, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        v = op.assemble(dtype).cpu().numpy().astype(np.float64)
+        assert rowwise_max_rel_err(csr[0], v, csr[2]) <= tol, dtype
+    rows = sample_rows(prob, 300, 1)
     check_rows(prob, mesh, op, rows, 1e-12, torch.float64)
-    check_rows(prob, mesh, op, rows, 1e-5, torch.float32)
     rng = np.random.default_rng(2)
     x, gy = rng.standard_normal(op.ndof), rng.standard_normal(op.ndof)
     y = op.apply(t(x)).cpu().numpy()
@@ -83,7 +98,6 @@ def test_step_workload_16x16x16_p4():
     assert np.abs(gx.cpu().numpy() - rgx).max() <= 1e-12 * np.abs(rgx).max()
     assert np.abs(gk.cpu().numpy() - rgk.ravel()).max() <= 1e-12 * np.abs(rgk).max()
     # smoother and SpMV against the oracle's own CSR
-    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
     op.build_pattern_internal()
     op.assemble_internal(torch.float64)
     v0 = power_start_vector(op.ndof)

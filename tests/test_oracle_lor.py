@@ -306,3 +306,63 @@ def test_spectral_equivalence_jittered_mesh_lognormal_kappa(p):
     lo, hi = min(x[0] for x in b), max(x[1] for x in b)
     assert lam.min() >= lo * (1 - 1e-10) and lam.max() <= hi * (1 + 1e-10)
     assert lo >= 0.25 and hi <= 9.0 * np.pi ** 2 / 4
+
+
+# ------------------------------------------------------------ general (element-restriction) meshes
+def cube_in_cube(m, p, seed=1):
+    from meshutil import cube_in_cube_corners, general_dofs, jitter_interior_vertices
+    C = jitter_interior_vertices(cube_in_cube_corners(m), 0.1 * 0.3 / m, np.random.default_rng(seed))
+    dofs, N, xyz, ess = general_dofs(C, p)
+    return C, dofs, N, xyz, ess
+
+
+@pytest.mark.parametrize("p,dims", [(1, (2, 3, 2)), (2, (2, 2, 3)), (4, (2, 2, 2))])
+def test_general_lor_on_a_lattice_is_the_structured_lor(p, dims):
+    """A structured mesh handed over in element-restriction form (natural
+    numbering) gives the structured routine's matrix (same sub-hex blocks;
+    only the summation order of the merged triplets may differ)."""
+    mesh = jittered(*dims, seed=p)
+    q = p + 2
+    kap = np.exp(np.random.default_rng(p).standard_normal((mesh.nel, q ** 3)))
+    ess = essential_mask(*dims, p).astype(np.uint8)
+    for dirichlet in (False, True):
+        rp, ci, v = oracle.lor_assemble(mesh, p, q, kap, dirichlet)
+        g = oracle.lor_assemble_general(element_corners(mesh.V, *dims), element_dofs(*dims, p), mesh.ndof(p), p, q,
+                                        kap, ess, dirichlet)
+        np.testing.assert_array_equal(g[0], rp)
+        np.testing.assert_array_equal(g[1], ci)
+        np.testing.assert_allclose(g[2], v, rtol=0, atol=1e-14 * np.abs(v).max())
+
+
+@pytest.mark.parametrize("m,p", [(1, 1), (1, 2), (1, 3), (2, 2)])
+def test_general_lor_on_cube_in_cube_is_q1_matrix_of_its_lor_mesh(m, p):
+    """On the non-lattice cube-in-cube mesh (vertex valences 3 and 4 at the
+    special corners), A_h equals the brute-force p = 1 stiffness matrix of the
+    LOR mesh (sub-hexes T_e(GLL boxes), 2x2x2 Gauss, kappa_s per sub-hex);
+    the pattern is the union of the sub-hexes' 8 x 8 couplings; zero row
+    sums and symmetry hold; with the boundary mask the essential rows and
+    columns become the identity and the free block is unchanged."""
+    from meshutil import general_lor_mesh
+    C, dofs, N, xyz, ess = cube_in_cube(m, p)
+    q = p + 2
+    kap = np.exp(np.random.default_rng(3).standard_normal((C.shape[0], q ** 3)))
+    ks = oracle.lor_kappa_sub(p, q, kap).ravel()
+    sc, sd = general_lor_mesh(C, dofs, p)
+    ref = oracle.dense_general(sc, sd, np.repeat(ks[:, None], 8, axis=1), 1, 2, N)
+    rp, ci, v = oracle.lor_assemble_general(C, dofs, N, p, q, kap, ess, dirichlet=False)
+    A = csr_to_dense(rp, ci, v, N)
+    np.testing.assert_allclose(A, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    pattern = np.zeros((N, N), bool)
+    for s in range(sd.shape[0]):
+        pattern[np.ix_(sd[s], sd[s])] = True
+    assert rp[-1] == pattern.sum()
+    for r in range(N):
+        assert ci[rp[r]:rp[r + 1]].tolist() == np.nonzero(pattern[r])[0].tolist()
+    lengths = set(np.diff(rp).tolist())
+    assert lengths - {8, 12, 18, 27}, lengths  # row lengths a lattice never has
+    assert np.abs(A.sum(axis=1)).max() < 1e-13 * np.abs(A).max()
+    np.testing.assert_allclose(A, A.T, atol=1e-15 * np.abs(A).max())
+    rp2, ci2, v2 = oracle.lor_assemble_general(C, dofs, N, p, q, kap, ess, dirichlet=True)
+    np.testing.assert_array_equal(rp2, rp)
+    np.testing.assert_array_equal(ci2, ci)
+    np.testing.assert_allclose(csr_to_dense(rp2, ci2, v2, N), eliminate(A, ess.astype(bool)), rtol=0, atol=0)

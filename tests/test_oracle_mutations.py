@@ -94,6 +94,9 @@ MUTATIONS = [
     ("SpMV reads x at the row instead of the column",
      "    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) s += values[j] * x[colidx[j]];",
      "    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) s += values[j] * x[i];"),
+    ("general-mesh LOR looks up the element map with j and k swapped",
+     "            dof[r] = dofs[e * n3 + i + n * (j + n * k)];",
+     "            dof[r] = dofs[e * n3 + i + n * (k + n * j)];"),
     ("LOR Dirichlet diagonal left at zero",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = (cc == r) ? 1.0 : 0.0;",
      "        if (er || is_essential(cI, cJ, cK, nx, ny, nz)) A->values[j] = 0.0;"),
