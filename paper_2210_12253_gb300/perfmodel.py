@@ -55,19 +55,38 @@ def setup_flops_per_element(p):
 
 
 def assemble_flops_per_element(p):
-    """Jacobian columns at the 2p x 2p sub-hex Gauss pairs; per sub-hex, one
-    8x8 block by 2x2x2 Gauss in the modal (Walsh-Hadamard) form, as the kernel
-    evaluates it: per Gauss point adjugate (27), det (5), 1/det (1), the six
-    scaled metric entries (42) = 75 x 8; six 8-point Walsh transforms, 24
-    additions each less the 12 whose outputs the diagonal entries never use
-    (108); the 84-term modal block (168); the modal-to-nodal transform per
-    axis, 8 additions for each of the 6 off-diagonal 2x2 blocks and 6 flops
-    for each of the 4 diagonal ones (3 x 72 = 216); the six scales F_ab (13).
-    Per element the kappa_s averages: 3 per high-order Gauss point and one
-    weight product per (y, z) point pair of each sub-hex column (p q^2).
-    (Evaluated directly, G grad(phi_j) and 36 dot products at each Gauss
-    point, the block costs 8 x (144 + 216) = 2,880 flops instead of the 492 of
-    the transforms, the modal block and the sandwich.)"""
+    """FP64 LOR assembly as the kernel evaluates it: per element the Jacobian
+    columns at the 2p x 2p sub-hex Gauss pairs and the squared column norms
+    |c_d|^2 on the same tables (the diagonal of M = J^T J: 5 each, 3 (2p)^2);
+    per sub-hex, one 8x8 block by 2x2x2 Gauss in the modal (Walsh-Hadamard)
+    form: per Gauss point the off-diagonal entries of M (15), its cofactors
+    (18), det M (5), 1/sqrt(det M) (1), the six metric entries F_ab / sqrt(det
+    M) adj(M)_ab (12) = 51 x 8; six 8-point Walsh transforms, 24 additions
+    each less the 12 whose outputs the diagonal entries never use (108); the
+    modal block, 28 sums of the |m||n| transformed entries (56 additions) and
+    their 22 factors 3^(-(|m|+|n|-2)/2) other than 1 (78); the
+    modal-to-nodal transform per axis, 8 additions for each of the 6
+    off-diagonal 2x2 blocks and 6 flops for each of the 4 diagonal ones
+    (3 x 72 = 216); the six scales F_ab (13).  Per element the kappa_s
+    averages: 3 per high-order Gauss point and one weight product per (y, z)
+    point pair of each sub-hex column (p q^2).  (The kernel executes the
+    additions of the transforms, the modal sums and the sandwich as exact
+    64-bit integer additions; they are counted here as the flops they are.)"""
+    q, L = p + 2, 2 * p
+    return (jacobian_columns_flops(L) + 15 * L * L + p ** 3 * (8 * 51 + 108 + 78 + 216 + 13) + 3 * q ** 3
+            + p * q * q)
+
+
+def assemble_f32_flops_per_element(p):
+    """The FP32 LOR assembly (the values of the mixed-precision smoother) as
+    that kernel evaluates it: Jacobian columns at the sub-hex Gauss pairs;
+    per Gauss point adjugate rows (27), det (5), 1/det (1), the six scaled
+    metric entries (42) = 75 x 8; the Walsh transforms (108); the 84-term
+    modal block (168); the sandwich (216); the scales F_ab (13); per element
+    the kappa_s averages.  (Evaluated directly, G grad(phi_j) and 36 dot
+    products at each Gauss point, the block costs 8 x (144 + 216) = 2,880
+    flops instead of the 492 of the transforms, the modal block and the
+    sandwich.)"""
     q = p + 2
     return jacobian_columns_flops(2 * p) + p ** 3 * (8 * 75 + 108 + 168 + 216 + 13) + 3 * q ** 3 + p * q * q
 
@@ -93,10 +112,19 @@ def reaction_extra_apply_flops_per_element(p):
 
 
 def reaction_extra_assemble_flops_per_element(p):
-    """Per sub-hex: the scale beta_s r_a r_b r_c / 64 (4), W(g) (8), its Walsh
-    transform (24), 36 modal mass terms (72); per element the beta_s averages
-    (2 per high-order Gauss point, sharing the kappa_s weights)."""
-    return p ** 3 * (4 + 8 + 24 + 72) + 2 * (p + 2) ** 3
+    """FP64, per sub-hex: the scale beta_s r_a r_b r_c / 64 (4), W(g) = that
+    scale times det J_e = det M / sqrt(det M) (16), its Walsh transform (24),
+    the 36 modal mass terms 3^(-(|m|+|n|)/2) What(m xor n) added to the block
+    (35 products, 36 additions); per element the beta_s averages (2 per
+    high-order Gauss point, sharing the kappa_s weights)."""
+    return p ** 3 * (4 + 16 + 24 + 71) + 2 * (p + 2) ** 3
+
+
+def reaction_extra_assemble_f32_flops_per_element(p):
+    """FP32: the scale (4), W(g) (8), its Walsh transform (24), the 36 modal
+    mass terms added to the block (35 products, 36 additions); per element
+    the beta_s averages."""
+    return p ** 3 * (4 + 8 + 24 + 71) + 2 * (p + 2) ** 3
 
 
 def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
@@ -107,7 +135,8 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
     if kind == "setup":
         return setup_flops_per_element(p) * nel, 64 * nq  # kappa in, D (48) + kappa copy out
     if kind == "assemble":
-        return assemble_flops_per_element(p) * nel, vbytes * nnz + 8 * nq
+        f = assemble_flops_per_element(p) if vbytes == 8 else assemble_f32_flops_per_element(p)
+        return f * nel, vbytes * nnz + 8 * nq
     if kind == "apply":
         return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
     if kind == "apply_f32":
@@ -120,7 +149,9 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
         return 8 * nq, 24 * nq
     if kind == "assemble_helmholtz":
         f, b = kernel_work("assemble", p, ndof, nel, nnz, vbytes)
-        return f + reaction_extra_assemble_flops_per_element(p) * nel, b + 8 * nq
+        extra = reaction_extra_assemble_flops_per_element(p) if vbytes == 8 else \
+            reaction_extra_assemble_f32_flops_per_element(p)
+        return f + extra * nel, b + 8 * nq
     if kind == "apply_helmholtz":
         f, b = kernel_work("apply", p, ndof, nel, nnz, vbytes)
         return f + reaction_extra_apply_flops_per_element(p) * nel, b + 8 * nq

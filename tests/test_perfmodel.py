@@ -46,6 +46,11 @@ class Flop:
     def __rtruediv__(self, o): return self._op(o, operator.truediv, True)
 
 
+def rsqrt(x):
+    """1/sqrt(x) as one operation (like a division)."""
+    return Flop(1.0 / math.sqrt(x.v), (x,))
+
+
 def leaves(a):
     return [Flop(float(v)) for v in np.asarray(a, dtype=float).ravel()]
 
@@ -336,10 +341,13 @@ def hadamard_axis(K, k):
     return out
 
 
-def modal_block(G, W=None):
+def modal_block(G, W=None, sums=False):
     """Nodal 8x8 block (36 symmetric entries) from the scaled metric G[ab][g]
     (1/64 folded in) and, for the reaction term, W(g) = beta_s detJ_sub / 64:
-    Walsh transforms, modal block, Hadamard sandwich on each axis."""
+    Walsh transforms, modal block, Hadamard sandwich on each axis.  sums:
+    each modal entry as the FP64 kernel forms it, the plain sum of its
+    transformed terms times its factor 3^(-(|m|+|n|-2)/2) (when not 1);
+    otherwise as the FP32 kernel does, one FMA per term with the factor."""
     for ab, first in enumerate([0, 0, 0, 1, 0, 2]):
         walsh8(G[ab], first)
     K = {(0, n): Flop(0.0) for n in range(8)}  # psi_0 has no gradient
@@ -349,12 +357,20 @@ def modal_block(G, W=None):
             ws = [(m & ~(1 << x)) ^ (n & ~(1 << y)) for x in range(3) if (m >> x) & 1 for y in range(3)
                   if (n >> y) & 1]
             cf = 3.0 ** (-(popc(m) + popc(n) - 2) / 2)
-            K[m, n] = acc([cf] * len(terms), [G[t][w] for t, w in zip(terms, ws)])
+            if sums:
+                t = [G[t][w] for t, w in zip(terms, ws)]
+                s = t[0]
+                for x in t[1:]:
+                    s = s + x
+                K[m, n] = s * cf if popc(m) + popc(n) > 2 else s
+            else:
+                K[m, n] = acc([cf] * len(terms), [G[t][w] for t, w in zip(terms, ws)])
     if W is not None:
         walsh8(W, 0)
         for m in range(8):
             for n in range(m, 8):
-                K[m, n] = K[m, n] + 3.0 ** (-(popc(m) + popc(n)) / 2) * W[m ^ n]
+                cw = 3.0 ** (-(popc(m) + popc(n)) / 2)
+                K[m, n] = K[m, n] + (cw * W[m ^ n] if popc(m) + popc(n) > 0 else W[m ^ n])
     for k in range(3):
         K = hadamard_axis(K, k)
     return K
@@ -399,10 +415,13 @@ def test_modal_block_equals_the_direct_nodal_block_and_costs_less():
     assert all(abs(sum(Kn[sym(i, j)].v for j in range(8))) <= 1e-12 * abs(Kn[i, i].v) for i in range(8))
 
 
-def lor_element_modal(p, corners, kappa, beta=None):
+def lor_element_modal(p, corners, kappa, beta=None, fp64=True):
     """The LOR blocks of one element, each sub-hex's 8x8 block by 2x2x2 Gauss
     in the modal form: metric at the 8 points, its Walsh transforms, the modal
-    block, the Hadamard sandwich.  Returns (blocks {(a, b, c): {(i, j): K_ij}}, all outputs)."""
+    block, the Hadamard sandwich.  fp64: the metric as the FP64 kernel forms
+    it, adj(M) / sqrt(det M) from M = J^T J with M's diagonal tabulated per
+    element; otherwise from the adjugate rows of J and 1/det (the FP32
+    kernel).  Returns (blocks {(a, b, c): {(i, j): K_ij}}, all outputs)."""
     q, L = p + 2, 2 * p
     gll = oracle.gauss_lobatto(p)
     xg, wg = oracle.gauss_legendre(q)
@@ -410,6 +429,7 @@ def lor_element_modal(p, corners, kappa, beta=None):
     mid = (gll[1:] + gll[:-1]) / 2
     xi = np.array([mid[a] + s * r[a] / math.sqrt(3.0) for a in range(p) for s in (-1, 1)])
     col = jacobian_columns(corner_leaves(corners), (1 - xi) / 2, (1 + xi) / 2)
+    mdiag = [{key: dot3(c, c) for key, c in col[d].items()} for d in range(3)] if fp64 else None
     binof = np.array([int(np.sum(gll[1:-1] < x)) for x in xg])
     wn = np.array([wg[g] / wg[binof == binof[g]].sum() for g in range(q)])
     bw = leaves(wn)  # normalised Gauss weights per axis bin, read from a table
@@ -440,14 +460,26 @@ def lor_element_modal(p, corners, kappa, beta=None):
                 for g in range(8):
                     u0, u1, u2 = 2 * a + (g & 1), 2 * b + ((g >> 1) & 1), 2 * c + (g >> 2)
                     c0, c1, c2 = col[0][u1, u2], col[1][u0, u2], col[2][u0, u1]
-                    A = [cross(c1, c2), cross(c2, c0), cross(c0, c1)]
-                    det = dot3(c0, A[0])
-                    rr = 1.0 / det
-                    if bR is not None:
-                        W[g] = bR * det
-                    for ab, (i, j) in enumerate(PAIRS):
-                        G[ab][g] = (F[ab] * rr) * dot3(A[i], A[j])
-                K = modal_block(G, W if bR is not None else None)
+                    if fp64:
+                        M00, M11, M22 = mdiag[0][u1, u2], mdiag[1][u0, u2], mdiag[2][u0, u1]
+                        M01, M02, M12 = dot3(c0, c1), dot3(c0, c2), dot3(c1, c2)
+                        adj = [M11 * M22 - M12 * M12, M02 * M12 - M01 * M22, M01 * M12 - M02 * M11,
+                               M00 * M22 - M02 * M02, M01 * M02 - M00 * M12, M00 * M11 - M01 * M01]
+                        detM = M00 * adj[0] + M01 * adj[1] + M02 * adj[2]
+                        rr = rsqrt(detM)
+                        if bR is not None:
+                            W[g] = bR * (detM * rr)
+                        for ab in range(6):
+                            G[ab][g] = (F[ab] * rr) * adj[ab]
+                    else:
+                        A = [cross(c1, c2), cross(c2, c0), cross(c0, c1)]
+                        det = dot3(c0, A[0])
+                        rr = 1.0 / det
+                        if bR is not None:
+                            W[g] = bR * det
+                        for ab, (i, j) in enumerate(PAIRS):
+                            G[ab][g] = (F[ab] * rr) * dot3(A[i], A[j])
+                K = modal_block(G, W if bR is not None else None, sums=fp64)
                 blocks[a, b, c] = K
                 outs.extend(K.values())
     return blocks, outs
@@ -472,23 +504,30 @@ def dense(csr, n):
     return A
 
 
+@pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("p", [1, 2, 4])
-def test_assemble_flops_evaluate_the_oracle_lor_matrix(p):
+def test_assemble_flops_evaluate_the_oracle_lor_matrix(p, fp64):
     q, n = p + 2, p + 1
     mesh, corners, kappa, _ = one_element(p, 50 + p)
-    blocks, outs = lor_element_modal(p, corners, kappa)
-    assert count(outs) == pm.assemble_flops_per_element(p)
+    blocks, outs = lor_element_modal(p, corners, kappa, fp64=fp64)
+    want = pm.assemble_flops_per_element(p) if fp64 else pm.assemble_f32_flops_per_element(p)
+    assert count(outs) == want
     ref = dense(oracle.lor_assemble(mesh, p, q, kappa, dirichlet=False), n ** 3)
     np.testing.assert_allclose(scatter(p, blocks), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("p", [2, 3])
-def test_assemble_reaction_flops_evaluate_the_oracle_lor_matrix(p):
+def test_assemble_reaction_flops_evaluate_the_oracle_lor_matrix(p, fp64):
     q, n = p + 2, p + 1
     mesh, corners, kappa, rng = one_element(p, 60 + p)
     beta = np.exp(rng.standard_normal(q ** 3))
-    blocks, outs = lor_element_modal(p, corners, kappa, beta)
-    assert count(outs) == pm.assemble_flops_per_element(p) + pm.reaction_extra_assemble_flops_per_element(p)
+    blocks, outs = lor_element_modal(p, corners, kappa, beta, fp64=fp64)
+    if fp64:
+        want = pm.assemble_flops_per_element(p) + pm.reaction_extra_assemble_flops_per_element(p)
+    else:
+        want = pm.assemble_f32_flops_per_element(p) + pm.reaction_extra_assemble_f32_flops_per_element(p)
+    assert count(outs) == want
     ref = dense(oracle.lor_assemble(mesh, p, q, kappa, dirichlet=False, beta=beta), n ** 3)
     np.testing.assert_allclose(scatter(p, blocks), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
@@ -502,4 +541,5 @@ def test_kernel_work_uses_the_per_element_counts():
                                                            16 * ndof + 48 * nel * q ** 3)
     assert pm.kernel_work("backward", p, ndof, nel, nnz)[0] == nel * pm.backward_flops_per_element(p)
     # bytes: values once per nonzero and kappa once per Gauss point
-    assert pm.kernel_work("assemble", p, ndof, nel, nnz, vbytes=4)[1] == 4 * nnz + 8 * nel * q ** 3
+    assert pm.kernel_work("assemble", p, ndof, nel, nnz, vbytes=4) == (nel * pm.assemble_f32_flops_per_element(p),
+                                                                       4 * nnz + 8 * nel * q ** 3)
