@@ -125,6 +125,75 @@ class ClockSampler:
         return out
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries of
+    libnvidia-ml, no settings changed) every `period` seconds on a background
+    thread, so a timed region of a few milliseconds still gets samples.
+    start() returns False where NVML cannot be loaded."""
+    SM_CLOCK = 1  # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, gpu_index, period=0.001, uuid=None):
+        self.gpu, self.period, self.uuid = gpu_index, period, uuid
+        self.samples, self.thread, self.lib = [], None, None
+
+    def start(self):
+        import ctypes
+        import threading
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            # the CUDA device by its UUID (NVML numbers every GPU of the machine), else by index
+            found = self.uuid is not None and lib.nvmlDeviceGetHandleByUUID(
+                ("GPU-" + str(self.uuid)).encode(), ctypes.byref(h)) == 0
+            if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                lib.nvmlShutdown()
+                return False
+            reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return False
+        self.lib, self.h, self.reasons_fn = lib, h, reasons_fn
+        mx = ctypes.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, self.SM_CLOCK, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.stop_flag = threading.Event()
+
+        def run():
+            clk, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+            while not self.stop_flag.is_set():
+                if lib.nvmlDeviceGetClockInfo(h, self.SM_CLOCK, ctypes.byref(clk)) == 0 and \
+                        reasons_fn(h, ctypes.byref(rs)) == 0:
+                    self.samples.append((float(clk.value), int(rs.value)))
+                time.sleep(self.period)
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        return True
+
+    def stop(self):
+        if self.thread is None:
+            return None
+        self.stop_flag.set()
+        self.thread.join()
+        self.lib.nvmlShutdown()
+        out = summarize_clock_samples(self.samples, self.max_mhz, self.REASONS)
+        if out is not None:
+            out["source"] = "NVML every %g ms during the timed region" % (self.period * 1e3)
+        return out
+
+
+def summarize_clock_samples(samples, max_mhz, names):
+    """Median SM clock, the maximum clock and the clock-event reasons seen in
+    any sample, from (sm_mhz, reason bit mask) samples (None without one)."""
+    if not samples:
+        return None
+    reasons = sorted({n for _, mask in samples for bit, n in names.items() if mask & bit})
+    return {"sm_mhz": statistics.median(c for c, _ in samples), "sm_max_mhz": max_mhz, "reasons": reasons,
+            "samples": len(samples)}
+
+
 def parse_clock_log(lines):
     """Summary of `nvidia-smi --query-gpu=ClockSampler.FIELDS --format=csv,noheader,nounits`
     lines: median SM clock, maximum SM clock, and the throttle reasons seen
@@ -239,8 +308,10 @@ def run_gpu(args, rank, world, local_rank):
         flush.zero_()
         step([torch.cuda.Event(enable_timing=True) for _ in range(6)])
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    clocks = NvmlSampler(local_rank, uuid=getattr(torch.cuda.get_device_properties(dev), "uuid", None))
+    if not clocks.start():
+        clocks = ClockSampler(local_rank)
+        clocks.start()
     launches0 = launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -252,6 +323,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier(world)
     wall = time.perf_counter() - t0
     launches = launch_count() - launches0
+    clk = clocks.stop()
     per_kernel = {n: [] for n in names}
     step_ms = []
     for ev in evs:
@@ -266,7 +338,7 @@ def run_gpu(args, rank, world, local_rank):
     # and every result read back, inside the timed region.  Copies run on a second stream with
     # double-buffered device inputs/outputs, so step k+1's inputs and step k's results move
     # while step k computes; the compute stream waits for each step's inputs by event.
-    e2e_steps = max(3, args.steps // 4)
+    e2e_steps = max(10, args.steps // 2)
     comp_s = torch.cuda.current_stream()
     copy_s = torch.cuda.Stream()
     ins = [(kappa, x, gy, r)] + [tuple(torch.empty_like(t) for t in (kappa, x, gy, r))]
@@ -337,7 +409,6 @@ def run_gpu(args, rank, world, local_rank):
                 "fp64_pipe_active": read_traffic("k_" + dominant, "fp64_pipe_active_fraction"),
                 "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
                         "frac": dk["frac_hbm"]}}
-    clk = clocks.stop()
 
     pcg = None
     if not args.no_pcg:
@@ -360,6 +431,9 @@ def run_gpu(args, rank, world, local_rank):
     precision = None
     if not args.no_precision:
         precision = run_precision(args, dev)
+    sweep_c5 = None
+    if not args.no_c5:
+        sweep_c5 = run_sweep_compact(args, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -379,11 +453,40 @@ def run_gpu(args, rank, world, local_rank):
                              "inputs and step k's results move while step k computes"},
            "gpu_launches": int(launches), "clocks": clk, "pcg": pcg, "gradient": grad,
            "helmholtz": helm, "assembly_comparator": comparator, "hcurl_topology": hcurl,
-           "general_mesh": general, "mixed_precision_errors": precision}
+           "general_mesh": general, "mixed_precision_errors": precision, "sweep_c5": sweep_c5}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    out["summary"] = summary(out)
     op.close()
     return out
+
+
+def summary(out):
+    """The line's key results in a few hundred characters, last on the line:
+    the dominant kernel's roofline, the PCG times to 1e-8 (32^3 p = 6), the
+    gradient solves, the p-sweep's GDOF/s and the oracle's rates."""
+    r = out["roofline"]
+    s = {"step_gdofs": round(out["value"], 4),
+         "roofline": "%s %.3f of %s %s" % (r["kernel"], r["frac"], r["peak"], r["unit"])}
+    pc = out.get("pcg")
+    if pc:
+        s["pcg_c3_to_1e-8"] = {"fp64_s": round(pc["fp64"]["solve_s"], 3), "fp64_it": pc["fp64"]["iterations"],
+                               "mixed_s": round(pc["mixed"]["solve_s"], 3), "mixed_it": pc["mixed"]["iterations"],
+                               "mixed_speedup": round(pc["mixed_speedup"], 3)}
+        if pc.get("mixed_ir"):
+            s["pcg_c3_to_1e-8"]["refinement_s"] = round(pc["mixed_ir"]["solve_s"], 3)
+    g = out.get("gradient")
+    if g:
+        s["gradient_c4_s"] = {k: round(v, 4) for k, v in g.items() if k.endswith("_s") and isinstance(v, float)}
+    c5 = out.get("sweep_c5")
+    if c5:
+        s["sweep_c5_gdofs"] = {"p": c5["p"]}
+        for k in ("assemble_f64", "apply", "backward", "precond_f32"):
+            s["sweep_c5_gdofs"][k] = [round(v, 3) for v in c5[k + "_gdofs"]]
+    cb = out.get("cpu_baseline")
+    if cb:
+        s["oracle_gdofs"] = {"cores": cb["cores"], "all_cores": cb["value"], "one_core": cb["one_core"]["value"]}
+    return s
 
 
 def run_pcg(args, dev, rank):
@@ -930,15 +1033,15 @@ def run_precision(args, dev):
     return out
 
 
-def run_sweep(args, dev):
-    """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
-    JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
-    (the kappa-gradient kernel), one FP32 Chebyshev-Jacobi degree-3
-    application), CUDA-event timed, median of `--sweep-reps` after one
-    warm-up, L2 flushed before each launch, and the FP32-arithmetic apply;
-    then the time per PCG iteration (30 iterations, the faster of two runs)
-    in mixed precision, in FP64 and in the refinement solver's inner
-    iterations (FP32 operator)."""
+SWEEP_KERNELS = ("setup", "assemble_f64", "assemble_f32", "apply", "apply_f32", "backward", "precond_f32")
+
+
+def sweep_degree(name, dev, reps, flush, kernels=SWEEP_KERNELS, pcg=True):
+    """Per-kernel timings on one p-sweep workload (about 20M DOFs): each kernel
+    CUDA-event timed, median of `reps` after one warm-up, L2 flushed before
+    each launch; with pcg, the time per PCG iteration (30 iterations, the
+    faster of two runs) in mixed precision, in FP64 and in the refinement
+    solver's inner iterations (FP32 operator)."""
     import numpy as np
     import torch
 
@@ -947,53 +1050,51 @@ def run_sweep(args, dev):
     from paper_2210_12253_gb300.perfmodel import FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
 
     hbm_peak, _ = hbm_peak_gbs()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    out = []
-    names = args.sweep_workloads or ["c5_p%d" % p for p in args.sweep_p]
-    for name in names:
-        prob = workload(name)
-        p = prob.p
-        op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
-        kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
-        prob.kappa = None
-        x = torch.tensor(np.random.default_rng(5).standard_normal(op.ndof), device=dev)
-        y, z, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
-        gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
-        op.set_coefficient(kappa, check=True)
-        op.build_pattern_internal()
-        op.assemble_internal(torch.float32)
-        lam = op.precond_setup("cheb", torch.float32, degree=3, power_iters=20)
-        calls = {
-            "setup": lambda: op.set_coefficient(kappa),
-            "assemble_f64": lambda: op.assemble_internal(torch.float64),
-            "assemble_f32": lambda: op.assemble_internal(torch.float32),
-            "apply": lambda: op.apply(x, out=y),
-            "apply_f32": lambda: op.apply_f32(x, out=y),
-            "backward": lambda: op.apply_backward(x, x, gx_out=gx, gk_out=gk),
-            "precond_f32": lambda: op.precond_apply(x, out=z),
-        }
-        res = {"p": p, "elements": op.nel, "ndof": op.ndof, "nnz": op.nnz, "lambda_max": lam}
-        for name, fn in calls.items():
+    prob = workload(name)
+    p = prob.p
+    op = LOR(p, prob.nex, prob.ney, prob.nez, torch.tensor(prob.vertices, device=dev))
+    kappa = torch.tensor(prob.kappa.reshape(-1), device=dev)
+    prob.kappa = None
+    x = torch.tensor(np.random.default_rng(5).standard_normal(op.ndof), device=dev)
+    y, z, gx = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    gk = torch.empty(op.nqpt, dtype=torch.float64, device=dev)
+    op.set_coefficient(kappa, check=True)
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float32)
+    lam = op.precond_setup("cheb", torch.float32, degree=3, power_iters=20)
+    calls = {
+        "setup": lambda: op.set_coefficient(kappa),
+        "assemble_f64": lambda: op.assemble_internal(torch.float64),
+        "assemble_f32": lambda: op.assemble_internal(torch.float32),
+        "apply": lambda: op.apply(x, out=y),
+        "apply_f32": lambda: op.apply_f32(x, out=y),
+        "backward": lambda: op.apply_backward(x, x, gx_out=gx, gk_out=gk),
+        "precond_f32": lambda: op.precond_apply(x, out=z),
+    }
+    res = {"p": p, "elements": op.nel, "ndof": op.ndof, "nnz": op.nnz, "lambda_max": lam}
+    for kname in kernels:
+        fn = calls[kname]
+        fn()
+        times = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             fn()
-            times = []
-            for _ in range(args.sweep_reps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn()
-                e1.record()
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1))
-            ms = statistics.median(times)
-            kind = {"assemble_f64": "assemble", "assemble_f32": "assemble", "precond_f32": "precond"}.get(name, name)
-            vb = 4 if name.endswith("f32") else 8
-            flops, nbytes = kernel_work(kind, p, op.ndof, op.nel, op.nnz, vbytes=vb, degree=3)
-            res[name] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
-                         "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                         "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
-            if name == "apply_f32":  # FP32 flops against the FP32 peak
-                del res[name]["frac_fp64"]
-                res[name]["frac_fp32"] = flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        kind = {"assemble_f64": "assemble", "assemble_f32": "assemble", "precond_f32": "precond"}.get(kname, kname)
+        vb = 4 if kname.endswith("f32") else 8
+        flops, nbytes = kernel_work(kind, p, op.ndof, op.nel, op.nnz, vbytes=vb, degree=3)
+        res[kname] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
+                      "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                      "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        if kname.endswith("f32") and kname != "precond_f32":  # FP32 flops against the FP32 peak
+            del res[kname]["frac_fp64"]
+            res[kname]["frac_fp32"] = flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS
+    if pcg:
         # PCG per iteration (30 iterations from x0 = 0, fixed count), mixed
         # precision and FP64, with the same lambda_max
         b = torch.tensor(prob.rhs, device=dev)
@@ -1017,11 +1118,51 @@ def run_sweep(args, dev):
                 torch.cuda.synchronize()
                 ms_it = min(ms_it, e0.elapsed_time(e1) / its)
             res[tag] = {"ms_per_iteration": ms_it, "gdofs_iterations": op.ndof / (ms_it * 1e-3) / 1e9}
-        op.close()
-        del op, kappa, x, y, z, gx, gk, b
-        torch.cuda.empty_cache()
+        del b
+    op.close()
+    del op, kappa, x, y, z, gx, gk
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_sweep(args, dev):
+    """Per-kernel GDOF/s versus p at about 20M DOFs (p = 2..10, seed 4): one
+    JSON object per degree (setup, FP64 and FP32 assembly, apply, backward
+    (the kappa-gradient kernel), one FP32 Chebyshev-Jacobi degree-3
+    application), CUDA-event timed, median of `--sweep-reps` after one
+    warm-up, L2 flushed before each launch, and the FP32-arithmetic apply;
+    then the time per PCG iteration (30 iterations, the faster of two runs)
+    in mixed precision, in FP64 and in the refinement solver's inner
+    iterations (FP32 operator)."""
+    import torch
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = []
+    for name in args.sweep_workloads or ["c5_p%d" % p for p in args.sweep_p]:
+        res = sweep_degree(name, dev, args.sweep_reps, flush)
         print(json.dumps(res), flush=True)
         out.append(res)
+    return out
+
+
+def run_sweep_compact(args, dev):
+    """The p-sweep's kernels (no PCG) at p = --c5-p (default 2, 4, 6, 8, 10),
+    each about 20M DOFs, 3 timed launches per kernel: GDOF/s per kernel and
+    degree, and the FP64 kernels' fraction of the FP64 peak."""
+    import torch
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rows = [sweep_degree("c5_p%d" % p, dev, 3, flush, pcg=False) for p in args.c5_p]
+    del flush
+    torch.cuda.empty_cache()
+    out = {"workloads": "c5 p-sweep: unit cube, n_e = round(20e6^(1/3)/p) per axis (19.9-20.6M DOFs), "
+                        "+-10% h jitter (seed 4), kappa lognormal(0,1); median of 3 launches, L2 flushed",
+           "p": [r["p"] for r in rows], "ndof": [r["ndof"] for r in rows]}
+    for k in SWEEP_KERNELS:
+        out[k + "_gdofs"] = [round(r[k]["gdofs"], 4) for r in rows]
+    for k in ("assemble_f64", "apply", "backward"):
+        out[k + "_frac_fp64"] = [round(r[k]["frac_fp64"], 3) for r in rows]
+    out["precond_f32_frac_hbm"] = [round(r["precond_f32"]["frac_hbm"], 3) for r in rows]
     return out
 
 
@@ -1049,12 +1190,12 @@ def oracle_step(sample):
     return prob.ndof
 
 
-def make_sample(ne=8):
+def make_sample(ne=8, seed=1):
     import numpy as np
 
     import oracle
     from paper_2210_12253_gb300.inputs import make_problem
-    prob = make_problem("sample", ne, ne, ne, 4, seed=1, kappa="lognormal", rhs="normal")
+    prob = make_problem("sample", ne, ne, ne, 4, seed=seed, kappa="lognormal", rhs="normal")
     mesh = oracle.Mesh(ne, ne, ne, prob.vertices)
     rng = np.random.default_rng(100)
     x, gy = rng.standard_normal(prob.ndof), rng.standard_normal(prob.ndof)
@@ -1076,7 +1217,88 @@ def reference_box(steps, warmup, step_s, ne=8, budget_s=None):
     return ne
 
 
+_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(args):
+    """One process of the all-cores leg: its own sub-box of the recipe (seed
+    1 + w), the oracle's step repeated for `seconds` after all workers met."""
+    w, seconds = args
+    sample = make_sample(8, seed=1 + w)
+    _BARRIER.wait()
+    t0 = time.perf_counter()
+    dofs = n = 0
+    while True:
+        dofs += oracle_step(sample)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return dofs, time.perf_counter() - t0, n
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_kernel_rates(seconds_each=2.0):
+    """The oracle's rate per kernel on one core, on a 6^3-element sub-box of
+    the 32^3 p = 6 PCG workload's recipe (seed 2): LOR assembly, high-order
+    apply, and one PCG iteration (FP64 operator, Chebyshev-Jacobi degree 3);
+    each repeated for at least `seconds_each`.  The PCG rate is also given as
+    the implied seconds per iteration at 7,189,057 DOFs (scaled by the DOF
+    count from the sub-box, where the oracle's per-iteration work is linear)."""
+    import numpy as np
+
+    import oracle
+    from paper_2210_12253_gb300.inputs import make_problem
+    ne, p = 6, 6
+    prob = make_problem("sample_c3", ne, ne, ne, p, seed=2, kappa="lognormal", rhs="normal")
+    mesh = oracle.Mesh(ne, ne, ne, prob.vertices)
+    q = p + 2
+    x = np.random.default_rng(101).standard_normal(prob.ndof)
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
+    lam = oracle.power_lambda_max(*csr, np.ones(prob.ndof), 20)
+
+    def rate(fn):
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            units = fn()
+            n += units
+            if time.perf_counter() - t0 >= seconds_each:
+                break
+        return n / (time.perf_counter() - t0)
+
+    def pcg_iters():
+        _, it, _, _ = oracle.pcg(mesh, p, q, prob.kappa, csr, prob.rhs, 1e-30, 3, oracle.PRECOND_CHEB, 3,
+                                 lam / 30, 1.1 * lam, raise_on_noconv=False)
+        return it
+    asm = rate(lambda: (oracle.lor_assemble(mesh, p, q, prob.kappa, True), prob.ndof)[1])
+    app = rate(lambda: (oracle.ho_apply(mesh, p, q, prob.kappa, x), prob.ndof)[1])
+    its = rate(pcg_iters)
+    return {"sample": "%d^3 elements, p=%d (%s DOFs), the 32^3 p=6 recipe (seed 2); one core" %
+                      (ne, p, format(prob.ndof, ",")),
+            "lor_assemble_gdofs": asm / 1e9, "ho_apply_gdofs": app / 1e9,
+            "pcg_iteration_gdofs": its * prob.ndof / 1e9,
+            "pcg_s_per_iteration_at_7189057_dofs": 7189057 / (its * prob.ndof)}
+
+
 def cpu_baseline(seconds):
+    """The oracle timed on the host: its step (LOR assembly, apply,
+    Chebyshev-Jacobi, backward) on an 8^3-element sub-box of the step
+    workload's recipe, on one core and then on every core the process may
+    use (one independent sub-box per core in a spawned process pool, started
+    together; value = all DOFs / the slowest worker's time), plus the
+    per-kernel rates of oracle_kernel_rates."""
+    import multiprocessing as mp
     sample = make_sample()
     t0 = time.perf_counter()
     dofs = 0
@@ -1087,8 +1309,19 @@ def cpu_baseline(seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": dofs / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample_desc(8) + "; %d oracle steps in %.1f s, single-threaded FP64 C" % (n, dt)}
+    one = {"value": dofs / dt / 1e9, "cores": 1, "steps": n, "seconds": dt}
+    cores = host_cores()
+    ctx = mp.get_context("spawn")  # after GPU work: never fork this process
+    barrier = ctx.Barrier(cores)
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(barrier,)) as pool:
+        res = pool.map(_oracle_worker, [(w, seconds) for w in range(cores)])
+    all_dofs = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return {"value": all_dofs / slowest / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample_desc(8) + "; on %d cores: one independent sub-box per core (spawned process pool, "
+                      "seeds 1..%d), %d oracle steps in %.1f s (slowest worker), single-threaded FP64 C per "
+                      "process" % (cores, cores, sum(r[2] for r in res), slowest),
+            "one_core": one, "kernels": oracle_kernel_rates()}
 
 
 def run_reference(args, rank, world):
@@ -1139,7 +1372,11 @@ def main(argv=None):
                     help="skip the macro-element vs unstructured LOR assembly comparison")
     ap.add_argument("--no-helmholtz", action="store_true",
                     help="skip the definite Helmholtz (reaction term) step on the 16^3 p=4 workload")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="seconds of each oracle leg (one core, then all cores)")
+    ap.add_argument("--no-c5", action="store_true", help="skip the compact p-sweep (kernels only) at ~20M DOFs")
+    ap.add_argument("--c5-p", type=int, nargs="*", default=[2, 4, 6, 8, 10],
+                    help="degrees of the compact p-sweep in the default line")
     ap.add_argument("--pcg-maxit", type=int, default=20000,
                     help="iteration cap of the PCG comparison (a small cap is for profiling only)")
     ap.add_argument("--pcg-only", action="store_true", help="run only the PCG comparison (profiling)")

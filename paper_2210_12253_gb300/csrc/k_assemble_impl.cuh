@@ -285,11 +285,16 @@ template <int P>
 constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
                                             : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
 
+// FP64: at most 128 registers per thread (65,536 / (128 x threads) CTAs per
+// SM), for the warps that hide the integer block algebra's latencies.
+template <int P, typename VT>
+constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (512 / kAsmThreads<P> > 1 ? 512 / kAsmThreads<P> : 1) : 1;
+
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
 
 template <int P, typename VT, bool MASS, bool GEN>
-__global__ void __launch_bounds__(kAsmThreads<P>) k_assemble(LorMesh m, LorTables T,
+__global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemble(LorMesh m, LorTables T,
                                                              const double* __restrict__ kappa,
                                                              const double* __restrict__ beta,
                                                              VT* __restrict__ vals) {

@@ -103,3 +103,41 @@ def test_clock_log_summary():
     hot = lines[:1] + ["0, 1500, 2070, 700.0, 0x48, Active, Not Active, Active, Not Active\n"]
     assert bench.parse_clock_log(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.parse_clock_log([]) is None
+
+
+def test_nvml_clock_sample_summary():
+    """Median SM clock, the maximum, and every clock-event reason seen in any
+    sample (bit masks of NVML's reasons)."""
+    import bench
+    names = bench.NvmlSampler.REASONS
+    out = bench.summarize_clock_samples([(2070.0, 0), (2055.0, 0x4), (2070.0, 0), (1980.0, 0x4 | 0x8)], 2070.0,
+                                        names)
+    assert out == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"],
+                   "samples": 4}
+    assert bench.summarize_clock_samples([], 2070.0, names) is None
+
+
+def test_summary_of_the_line():
+    """The compact summary at the end of the JSON line carries the PCG times
+    and counts, the sweep's GDOF/s and the oracle's rates."""
+    import bench
+    out = {"value": 0.3, "roofline": {"kernel": "assemble", "frac": 0.7, "peak": 1.2586, "unit": "TFLOP/s"},
+           "pcg": {"fp64": {"solve_s": 5.2, "iterations": 1440}, "mixed": {"solve_s": 4.6, "iterations": 1530},
+                   "mixed_speedup": 1.13, "mixed_ir": {"solve_s": 1.07}},
+           "gradient": {"workload": "c4", "forward_s": 0.39, "adjoint_s": 0.45, "total_s": 0.85,
+                        "forward_iterations": 379},
+           "sweep_c5": {"p": [2, 4], "assemble_f64_gdofs": [1.0, 1.2], "apply_gdofs": [1.5, 2.5],
+                        "backward_gdofs": [0.9, 1.5], "precond_f32_gdofs": [18.0, 18.0]},
+           "cpu_baseline": {"value": 2e-3, "cores": 16, "one_core": {"value": 1.8e-4}}}
+    s = bench.summary(out)
+    assert s["pcg_c3_to_1e-8"] == {"fp64_s": 5.2, "fp64_it": 1440, "mixed_s": 4.6, "mixed_it": 1530,
+                                   "mixed_speedup": 1.13, "refinement_s": 1.07}
+    assert s["gradient_c4_s"] == {"forward_s": 0.39, "adjoint_s": 0.45, "total_s": 0.85}
+    assert s["sweep_c5_gdofs"]["p"] == [2, 4] and s["sweep_c5_gdofs"]["apply"] == [1.5, 2.5]
+    assert s["oracle_gdofs"] == {"cores": 16, "all_cores": 2e-3, "one_core": 1.8e-4}
+    assert s["roofline"].startswith("assemble 0.700")
+
+
+def test_host_cores_is_positive():
+    import bench
+    assert bench.host_cores() >= 1
