@@ -278,9 +278,13 @@ template <typename VT>
 constexpr uint32_t tile_bytes() {
   return (uint32_t)(sizeof(VT) * 27 * kThreads + 16);
 }
+// Buffers per CTA: 2 overlaps a CTA's next copy with its rows; 1 halves the
+// shared memory, so twice as many CTAs share an SM and overlap each other.
+template <typename VT>
+constexpr int kStencilBuffers = 2;
 template <typename VT>
 constexpr size_t stencil_smem() {
-  return 2 * (size_t)tile_bytes<VT>();
+  return kStencilBuffers<VT> * (size_t)tile_bytes<VT>();
 }
 
 // Start the copy of tile t's values into buf; returns the CSR position of buf[0].
@@ -340,8 +344,9 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t base[2];  // CSR position of each buffer's first element
   __shared__ int abort_flag;
+  constexpr int NB = kStencilBuffers<VT>;
   VT* buf0 = reinterpret_cast<VT*>(smem_raw);
-  VT* buf1 = reinterpret_cast<VT*>(smem_raw + tile_bytes<VT>());
+  VT* buf1 = reinterpret_cast<VT*>(smem_raw + (NB - 1) * tile_bytes<VT>());
   const int64_t ntiles = (m.ndof + kThreads - 1) / kThreads;
   const int64_t stride = gridDim.x;
   if (threadIdx.x == 0) {
@@ -357,8 +362,9 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
   for (int64_t t = blockIdx.x; t < ntiles; t += stride, ++it) {
     const int b = it & 1;
     // prefetch the next tile into the other buffer (its readers finished at
-    // the barrier that ended the previous iteration)
-    if (threadIdx.x == 0 && t + stride < ntiles)
+    // the barrier that ended the previous iteration); with one buffer the
+    // next copy starts only after this tile's rows are done (below)
+    if (NB == 2 && threadIdx.x == 0 && t + stride < ntiles)
       base[b ^ 1] = issue_tile<VT>(m, vals, t + stride, b ? buf0 : buf1, &bar[b ^ 1]);
     // (a test hook makes the wait count as expired: the copy still lands and
     // is waited for below)
@@ -374,6 +380,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
       stencil_epilogue<VT, XT, MODE, V>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
     }
     __syncthreads();  // every read of this buffer is done before it is refilled
+    if (NB == 1 && threadIdx.x == 0 && t + stride < ntiles)
+      base[b ^ 1] = issue_tile<VT>(m, vals, t + stride, buf0, &bar[b ^ 1]);
   }
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, LOR_FLAG_TIMEOUT);
@@ -383,7 +391,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
     // copy never completes) and the next tile's prefetch if one is in flight.
     const int b = it & 1;
     mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
-    if (blockIdx.x + (int64_t)(it + 1) * stride < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+    if (NB == 2 && blockIdx.x + (int64_t)(it + 1) * stride < ntiles)
+      mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
   }
   if constexpr (MODE == ST_CHEB_DOT) finish_sums((double)acc, 0.0, 1, partial, counter, out, nullptr);
 }
