@@ -279,9 +279,11 @@ constexpr uint32_t tile_bytes() {
   return (uint32_t)(sizeof(VT) * 27 * kThreads + 16);
 }
 // Buffers per CTA: 2 overlaps a CTA's next copy with its rows; 1 halves the
-// shared memory, so twice as many CTAs share an SM and overlap each other.
+// shared memory, so twice as many CTAs share an SM and overlap each other's
+// copies.  Measured on the 32^3 p = 6 PCG: one buffer is 2% faster per FP64
+// and mixed iteration and 7% per refinement iteration (FP32 vectors).
 template <typename VT>
-constexpr int kStencilBuffers = 2;
+constexpr int kStencilBuffers = 1;
 template <typename VT>
 constexpr size_t stencil_smem() {
   return kStencilBuffers<VT> * (size_t)tile_bytes<VT>();
