@@ -74,24 +74,6 @@ __device__ __forceinline__ constexpr double inv_sqrt3_pow(int p) {  // 3^(-p/2),
 }
 __device__ __forceinline__ constexpr int sym(int i, int j) { return i <= j ? i * 8 + j : j * 8 + i; }
 
-// 1/sqrt(x) in FP64 for x > 0 in the FP32 normal range (1.2e-38 .. 3.4e38):
-// an FP32 seed (x's leading 20 mantissa bits, the hardware rsqrt
-// approximation: about 20 correct bits) refined by one Newton step with its
-// second-order term, y (1 + e/2 + 3 e^2/8) with e = 1 - x y^2 (the error
-// left is O(e^3), below FP64 rounding; within 1.3 ulp in a CPU emulation over
-// 1e-30 .. 1e30).  The FP64 <-> FP32 moves are integer bit operations, since
-// the conversion instructions issue on the FP64 pipe.  Five FP64 operations.
-__device__ __forceinline__ double lor_rsqrt(double x) {
-  const int hi = __double2hiint(x);
-  float yf;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float((hi - (896 << 20)) << 3)));
-  const int yb = __float_as_int(yf);
-  const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
-  const double t = x * y;
-  const double e = fma(-t, y, 1.0);
-  return fma(y * e, fma(0.375, e, 0.5), y);
-}
-
 // ---------------------------------------------------------------------------
 // FP64 block algebra in exact 64-bit integer arithmetic.
 //
@@ -109,7 +91,7 @@ __device__ __forceinline__ double lor_rsqrt(double x) {
 // largest scale that keeps them below 2^56 (a shift of 0 to 7 bits chosen
 // from their actual size, so the sandwich keeps 56 bits of the largest
 // entry), the sandwich is exact, and the 36 nodal entries return to FP64
-// correctly rounded (by integer operations too).  The roundings are those of the input conversion, the
+// correctly rounded.  The roundings are those of the input conversion, the
 // products, the one shift and the output conversion: in a CPU emulation on
 // random metrics the result is within 9e-16 of the exact block (relative to
 // the row maximum), against 1.7e-15 for the same steps in FP64.
@@ -124,23 +106,14 @@ __device__ __forceinline__ long long to_fix(double x, int emax) {
   const long long sgn = (long long)b >> 63;  // 0 or -1
   return e == 0 ? 0 : ((long long)X ^ sgn) - sgn;
 }
-// X 2^-scale in FP64 (|X| < 2^62; X 2^-scale a normal number here), rounded
-// to nearest even by integer operations: the conversion instruction issues on
-// the FP64 pipe, and at 36 per sub-hex it took a quarter of that pipe.  The
-// leading one of |X| is normalised to bit 63, the top 53 bits are the
-// significand, the 11 below decide the rounding; adding the rounded
-// significand (implicit bit included) onto the exponent field lets a carry
-// to 2^53 raise the exponent.
+// X 2^-scale in FP64, correctly rounded (X 2^-scale is a normal number
+// here).  The int64 conversion issues on the FP64 pipe (about a sixth of the
+// kernel's FP64 pipe time at p = 4); an integer-only conversion measured
+// slower: the kernel is latency-bound and the longer dependency chain cost
+// more than the pipe time it saved.
 __device__ __forceinline__ double from_fix(long long X, int scale) {
-  const unsigned long long sgn = (unsigned long long)X & 0x8000000000000000ull;
-  const unsigned long long a = X < 0 ? (unsigned long long)(-X) : (unsigned long long)X;
-  const int lz = __clzll((long long)a);
-  const unsigned long long n = a << (lz & 63);
-  const unsigned long long m = n >> 11, rem = n & 0x7FFull;
-  const unsigned long long up = (rem > 0x400ull) | ((rem == 0x400ull) & (m & 1ull));
-  const long long e = 1023 + (63 - lz) - scale;  // biased exponent of the result
-  const unsigned long long bits = ((unsigned long long)(e - 1) << 52) + m + up;
-  return a == 0 ? 0.0 : __longlong_as_double((long long)(bits | sgn));
+  const double d = __ll2double_rn(X);
+  return X == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) - ((long long)scale << 52));
 }
 // round(X C / 2^63) for a Q63 constant 0 <= C < 2^63
 __device__ __forceinline__ long long fix_mul(long long X, long long C) {

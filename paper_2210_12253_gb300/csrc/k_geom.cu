@@ -7,12 +7,20 @@
 // so these kernels are bound by FP64 issue, not by HBM.  The FP64 work per
 // point is kept minimal: a trilinear map has dx/dxi_0 independent of xi_0 (and
 // likewise for the other columns), so each Jacobian column is tabulated once
-// per element on a q x q grid in shared memory; per point only the adjugate
-// (three cross products), the determinant and six dot products remain.
+// per element on a q x q grid in shared memory, and so are the squared column
+// norms; per point the metric follows from the rest of M = J^T J.
 #include "lor_internal.cuh"
 
 namespace {
 
+// D = kappa w detJ J^-1 J^-T = kappa w adj(M) / sqrt(det M) with M = J^T J:
+// M's diagonal |c_d|^2 depends only on the two coordinates its column is
+// tabulated on, so it is tabulated per element next to the columns; per
+// Gauss point remain the three off-diagonal products, the six cofactors,
+// det M and one reciprocal square root (fewer FP64 instructions than the
+// adjugate rows of J, its determinant and reciprocal, and six dot products).
+// det M > 0 is checked here; the sign of det J was checked at context
+// creation (the mesh does not change afterwards).
 template <int P>
 __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
                                                double* __restrict__ kcopy, double* __restrict__ Dq,
@@ -20,6 +28,7 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ double Ehalf[36];
   __shared__ double col[3 * Q2 * 3];
+  __shared__ double mdg[3 * Q2];  // |c_d|^2 on each column's table
   __shared__ double sw[Q], s0[Q], s1[Q];
   if (threadIdx.x < Q) {
     sw[threadIdx.x] = T.gw[threadIdx.x];
@@ -30,27 +39,35 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   int bad = 0;
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
     lor_jacobian_columns(m, e, s0, s1, Q, Ehalf, col);
+    for (int i = threadIdx.x; i < 3 * Q2; i += blockDim.x) {
+      const double* cc = col + 3 * i;
+      mdg[i] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+    }
+    __syncthreads();
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
       const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
       const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
       const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
-      double a0[3], a1[3], a2[3];
-      lor_cross(c1, c2, a0);
-      lor_cross(c2, c0, a1);
-      lor_cross(c0, c1, a2);
-      const double det = c0[0] * a0[0] + c0[1] * a0[1] + c0[2] * a0[2];
+      const double M00 = mdg[g1 + Q * g2], M11 = mdg[Q2 + g0 + Q * g2], M22 = mdg[2 * Q2 + g0 + Q * g1];
+      const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
+      const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
+      const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
+      const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
+      const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
+      const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
+      const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
       const double k = kin[e * Q3 + pt];
       if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
-      if (!(det > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
-      const double s = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rcp(det);
+      if (!(detM > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
+      const double s = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(detM);
       double* D = Dq + e * 6 * Q3 + pt;
-      D[0 * Q3] = s * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
-      D[1 * Q3] = s * (a0[0] * a1[0] + a0[1] * a1[1] + a0[2] * a1[2]);
-      D[2 * Q3] = s * (a0[0] * a2[0] + a0[1] * a2[1] + a0[2] * a2[2]);
-      D[3 * Q3] = s * (a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
-      D[4 * Q3] = s * (a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2]);
-      D[5 * Q3] = s * (a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+      D[0 * Q3] = s * A00;
+      D[1 * Q3] = s * A01;
+      D[2 * Q3] = s * A02;
+      D[3 * Q3] = s * A11;
+      D[4 * Q3] = s * A12;
+      D[5 * Q3] = s * A22;
       kcopy[e * Q3 + pt] = k;
     }
     __syncthreads();

@@ -46,12 +46,13 @@ def jacobian_columns_flops(L):
 
 
 def setup_flops_per_element(p):
-    """Jacobian columns at the q x q Gauss pairs, then per Gauss point the
-    adjugate rows (3 cross products, 27), det (5), its reciprocal (1), the
-    weight product (2), kappa w / det (2) and the six scaled dot products
-    (36): 73."""
+    """Jacobian columns at the q x q Gauss pairs and their squared norms (the
+    diagonal of M = J^T J, 5 each, 3 q^2); per Gauss point the off-diagonal
+    entries of M (15), its cofactors (18), det M (5), 1/sqrt(det M) (1), the
+    weight product (2), kappa w / sqrt(det M) (2) and the six scaled
+    cofactors (6): 49."""
     q = p + 2
-    return jacobian_columns_flops(q) + 73 * q ** 3
+    return jacobian_columns_flops(q) + 15 * q * q + 49 * q ** 3
 
 
 def assemble_flops_per_element(p):

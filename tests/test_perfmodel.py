@@ -283,17 +283,21 @@ def test_setup_flops_evaluate_the_oracle_metric(p):
     xg, wg = oracle.gauss_legendre(q)
     w0, w1 = (1 - xg) / 2, (1 + xg) / 2
     col = jacobian_columns(corner_leaves(corners), w0, w1)
+    mdiag = [{key: dot3(c, c) for key, c in col[d].items()} for d in range(3)]  # |c_d|^2, tabulated
     sw = leaves(wg)  # weights are read from a table and multiplied at run time
     out = []
     for g2 in range(q):
         for g1 in range(q):
             for g0 in range(q):
                 c0, c1, c2 = col[0][g1, g2], col[1][g0, g2], col[2][g0, g1]
-                a = [cross(c1, c2), cross(c2, c0), cross(c0, c1)]
-                det = dot3(c0, a[0])
+                M00, M11, M22 = mdiag[0][g1, g2], mdiag[1][g0, g2], mdiag[2][g0, g1]
+                M01, M02, M12 = dot3(c0, c1), dot3(c0, c2), dot3(c1, c2)
+                adj = [M11 * M22 - M12 * M12, M02 * M12 - M01 * M22, M01 * M12 - M02 * M11,
+                       M00 * M22 - M02 * M02, M01 * M02 - M00 * M12, M00 * M11 - M01 * M01]
+                detM = M00 * adj[0] + M01 * adj[1] + M02 * adj[2]
                 k = Flop(kappa[g0 + q * (g1 + q * g2)])
-                s = k * (sw[g0] * sw[g1] * sw[g2]) * (1.0 / det)
-                out.append([s * dot3(a[i], a[j]) for i, j in PAIRS])
+                s = k * (sw[g0] * sw[g1] * sw[g2]) * rsqrt(detM)
+                out.append([s * a for a in adj])
     flat = [x for d in out for x in d]
     assert count(flat) == pm.setup_flops_per_element(p)
     _, G = oracle.geometry(mesh, q)
