@@ -175,19 +175,24 @@ int lor_set_reaction(lor_ctx* ctx, const double* d_beta, void* stream);
  * themselves); LOR_ECUDA. */
 int lor_check(lor_ctx* ctx, void* stream);
 
-/* Bit of lor_set_test_hooks. */
+/* Bits of lor_set_test_hooks. */
 #define LOR_TEST_EXPIRE_WAITS 1u
+#define LOR_TEST_UNSTAGED_CSR 2u
 
 /* Test hooks (no passage: the paper has no counterpart; a way for tests to exercise the
  * error paths of device-side waits without a fault).  flags is a bit mask:
  *   LOR_TEST_EXPIRE_WAITS  every CTA of the TMA-staged SpMV/smoother kernels
- *                          (structured meshes) treats its first bounded wait
- *                          for a bulk copy as expired: it records
+ *                          treats its first bounded wait for a bulk copy as
+ *                          expired: it records
  *                          LOR_FLAG_TIMEOUT in the context's status word, lets
  *                          every copy it issued land (waits at the normal
  *                          bound) and exits without writing its rows, exactly
  *                          as after a real expiry.  lor_check, lor_precond_setup
  *                          and the solvers then return LOR_ETIMEOUT.
+ *   LOR_TEST_UNSTAGED_CSR  the explicit-CSR SpMV/smoother kernel (general
+ *                          meshes) reads every tile from global memory, the
+ *                          path it otherwise takes only for tiles whose rows
+ *                          do not fit its shared-memory buffers (same result).
  * 0 clears the hooks; a cleared context computes as before (clear the status
  * word with lor_check first).  Host only, does not synchronise.  Errors:
  * LOR_EINVAL for a NULL ctx or an unknown flag. */

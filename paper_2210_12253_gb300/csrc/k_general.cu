@@ -334,7 +334,7 @@ cudaError_t lor_general_pattern(const LorMesh& m, const LorDeviceAlloc& A, int64
   if (err == cudaSuccess) err = exclusive_scan(rowptr.p, n, scratch.p, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(&nnz, rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  if (err == cudaSuccess) err = colidx.get(nnz);
+  if (err == cudaSuccess) err = colidx.get(nnz + 4);  // 16 bytes of padding for the smoother's rounded bulk copies
   if (err == cudaSuccess) {
     k_row_write<<<grid_for(n), kT, 0, s>>>(n, off.p, list.p, rowptr.p, colidx.p); lor_count_launch();
     err = cudaGetLastError();

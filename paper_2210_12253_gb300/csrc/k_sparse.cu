@@ -400,35 +400,117 @@ __global__ void __launch_bounds__(kThreads) k_stencil(LorMesh m, const VT* __res
 }
 
 // ---- the same modes on an explicit CSR pattern (general meshes, whose LOR
-// pattern has no closed form): kLanes lanes per row read consecutive entries
-// of the row and combine by shuffles; every warp runs the same number of row
-// rounds (the grid loops), so the shuffles stay uniform and the reducing mode
-// can finish in the last CTA.
-constexpr int kLanes = 4;
+// pattern has no closed form).  A CTA takes kCsrRows consecutive rows, one
+// thread per row; their values and column indices are contiguous in CSR, so
+// thread 0 stages both segments into shared memory with one bulk copy each
+// (both completing on one mbarrier) and each thread forms its row's product
+// from there, in column order.  A tile whose segments do not fit the buffers
+// (more than kCsrCap / kCsrRows entries per row on average) is read from
+// global memory instead, and its barrier phase is completed by a plain
+// arrive so that the phases stay in step.  The column array carries 16 bytes
+// of padding after nnz for the rounded last copy (the value arrays carry
+// theirs).
+constexpr int kCsrRows = 128;
+constexpr int kCsrCap = 28 * kCsrRows;  // entries each tile buffer holds
+
+template <typename VT>
+constexpr uint32_t csr_vbuf_bytes() {
+  return (uint32_t)(sizeof(VT) * kCsrCap + 16);
+}
+constexpr uint32_t csr_cbuf_bytes() { return (uint32_t)(4 * kCsrCap + 16); }
+template <typename VT>
+constexpr size_t csr_smem() {
+  return csr_vbuf_bytes<VT>() + csr_cbuf_bytes();
+}
+
+// Start the copies of tile t's value and column segments (both addresses
+// rounded down to 16 bytes, both lengths up); returns false, after a plain
+// arrive on bar, when they do not fit.
+template <typename VT>
+__device__ __forceinline__ bool issue_csr_tile(const LorMesh& m, const VT* __restrict__ vals, int64_t t, VT* vbuf,
+                                               int32_t* cbuf, uint64_t* bar, int64_t* vbase, int64_t* cbase) {
+  const int64_t r0 = t * kCsrRows;
+  const int64_t r1 = r0 + kCsrRows < m.ndof ? r0 + kCsrRows : m.ndof;
+  const int64_t e0 = m.rowptr[r0], e1 = m.rowptr[r1];
+  const int64_t av = e0 & ~(int64_t)(16 / sizeof(VT) - 1), ac = e0 & ~(int64_t)3;
+  const int64_t vb = ((e1 - av) * (int64_t)sizeof(VT) + 15) & ~(int64_t)15;
+  const int64_t cb = ((e1 - ac) * 4 + 15) & ~(int64_t)15;
+  if (vb > (int64_t)csr_vbuf_bytes<VT>() || cb > (int64_t)csr_cbuf_bytes() || (m.test_flags & LOR_TEST_UNSTAGED_CSR)) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    return false;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"((uint32_t)(vb + cb))
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(vbuf)),
+               "l"(vals + av), "r"((uint32_t)vb), "r"(smem_u32(bar))
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(cbuf)),
+               "l"(m.colidx + ac), "r"((uint32_t)cb), "r"(smem_u32(bar))
+               : "memory");
+  *vbase = av;
+  *cbase = ac;
+  return true;
+}
 
 template <typename VT, typename XT, int MODE, typename V = double>
-__global__ void __launch_bounds__(kThreads) k_csr(LorMesh m, const VT* __restrict__ vals, const VT* __restrict__ dinv,
+__global__ void __launch_bounds__(kCsrRows) k_csr(LorMesh m, const VT* __restrict__ vals, const VT* __restrict__ dinv,
                                                   const XT* __restrict__ x, const V* __restrict__ r,
                                                   VT* __restrict__ d, VT c1, VT c2, VT* __restrict__ zout,
                                                   V* __restrict__ y, double* __restrict__ partial,
-                                                  unsigned* __restrict__ counter, double* __restrict__ out) {
-  const int64_t n = m.ndof;
-  const int64_t rows_per_round = (int64_t)gridDim.x * blockDim.x / kLanes;
-  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kLanes;
-  const int group = (threadIdx.x & 31) / kLanes, lane = threadIdx.x & (kLanes - 1);
+                                                  unsigned* __restrict__ counter, double* __restrict__ out,
+                                                  int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int64_t vbase[2], cbase[2];  // CSR position of each buffer's first element
+  __shared__ int staged[2];
+  __shared__ int abort_flag;
+  VT* vbuf = reinterpret_cast<VT*>(smem_raw);
+  int32_t* cbuf = reinterpret_cast<int32_t*>(smem_raw + csr_vbuf_bytes<VT>());
+  const int64_t ntiles = (m.ndof + kCsrRows - 1) / kCsrRows;
+  const int64_t stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+    if ((int64_t)blockIdx.x < ntiles)
+      staged[0] = issue_csr_tile<VT>(m, vals, blockIdx.x, vbuf, cbuf, &bar[0], &vbase[0], &cbase[0]);
+  }
+  __syncthreads();
   Acc<V> acc = 0;
-  for (int64_t base = warp_first; base < n; base += rows_per_round) {
-    const int64_t i = base + group;
-    const bool valid = i < n;
-    VT s = 0;
-    if (valid) {
-      const int64_t b = m.rowptr[i], e = m.rowptr[i + 1];
-      for (int64_t j = b + lane; j < e; j += kLanes) s += vals[j] * (VT)x[m.colidx[j]];
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += stride, ++it) {
+    const int b = it & 1;
+    // (the test hook makes the wait count as expired; the copy still lands
+    // and is waited for below)
+    const bool landed = !(m.test_flags & LOR_TEST_EXPIRE_WAITS) && mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
+    if (!landed) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const int64_t i = t * kCsrRows + threadIdx.x;
+    if (i < m.ndof) {
+      const int64_t j0 = m.rowptr[i], j1 = m.rowptr[i + 1];
+      VT s = 0;
+      if (staged[b]) {
+        const int64_t ov = vbase[b], oc = cbase[b];
+        for (int64_t j = j0; j < j1; ++j) s += vbuf[j - ov] * (VT)x[cbuf[j - oc]];
+      } else {
+        for (int64_t j = j0; j < j1; ++j) s += vals[j] * (VT)x[m.colidx[j]];
+      }
+      stencil_epilogue<VT, XT, MODE, V>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
     }
-#pragma unroll
-    for (int o = kLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (!valid || lane != 0) continue;
-    stencil_epilogue<VT, XT, MODE, V>(i, s, dinv, x, r, d, c1, c2, zout, y, acc);
+    __syncthreads();  // every read of the buffers is done before they are refilled
+    if (threadIdx.x == 0 && t + stride < ntiles)
+      staged[b ^ 1] = issue_csr_tile<VT>(m, vals, t + stride, vbuf, cbuf, &bar[b ^ 1], &vbase[b ^ 1], &cbase[b ^ 1]);
+  }
+  if (abort_flag && threadIdx.x == 0) {
+    atomicOr(status, LOR_FLAG_TIMEOUT);
+    // let the copies whose wait gave up land before the CTA exits (bounded
+    // again; after a real expiry this gives up too)
+    mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u);
   }
   if constexpr (MODE == ST_CHEB_DOT) finish_sums((double)acc, 0.0, 1, partial, counter, out, nullptr);
 }
@@ -463,16 +545,41 @@ cudaError_t stencil_grid(const LorMesh& m, int* grid) {
   return cudaSuccess;
 }
 
+// The same for the explicit-CSR kernel.
+template <typename VT, typename XT, int MODE, typename V>
+cudaError_t csr_grid(const LorMesh& m, int* grid) {
+  static int per_device[64] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!per_device[dev]) {
+    err = cudaFuncSetAttribute(k_csr<VT, XT, MODE, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)csr_smem<VT>());
+    int sms = 0, occ = 0;
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_csr<VT, XT, MODE, V>, kCsrRows, csr_smem<VT>());
+    if (err != cudaSuccess) return err;
+    per_device[dev] = sms * (occ > 0 ? occ : 1);
+  }
+  const int64_t ntiles = (m.ndof + kCsrRows - 1) / kCsrRows;
+  int64_t g = per_device[dev] < ntiles ? per_device[dev] : ntiles;
+  if (MODE == ST_CHEB_DOT && g > LOR_PCG_MAX_BLOCKS) g = LOR_PCG_MAX_BLOCKS;
+  *grid = (int)(g > 0 ? g : 1);
+  return cudaSuccess;
+}
+
 template <typename VT, typename XT, int MODE, typename V = double>
 cudaError_t launch_stencil(const LorMesh& m, const VT* vals, const VT* dinv, const XT* x, const V* r, VT* d,
                            double c1, double c2, VT* zout, V* y, double* partial, unsigned* counter,
                            double* out, int* status, cudaStream_t s) {
   if (m.rowptr) {  // general mesh: explicit CSR pattern
-    const int64_t want = (m.ndof * kLanes + kThreads - 1) / kThreads;
-    const int64_t cap = MODE == ST_CHEB_DOT ? LOR_PCG_MAX_BLOCKS : 152 * 8;
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_csr<VT, XT, MODE, V><<<grid, kThreads, 0, s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y, partial, counter,
-                                                  out);
+    int grid = 0;
+    cudaError_t err = csr_grid<VT, XT, MODE, V>(m, &grid);
+    if (err != cudaSuccess) return err;
+    k_csr<VT, XT, MODE, V><<<grid, kCsrRows, csr_smem<VT>(), s>>>(m, vals, dinv, x, r, d, (VT)c1, (VT)c2, zout, y,
+                                                                  partial, counter, out, status);
     lor_count_launch();
     return cudaGetLastError();
   }

@@ -570,7 +570,8 @@ int lor_check(lor_ctx* c, void* stream) {
 
 int lor_set_test_hooks(lor_ctx* c, unsigned flags) {
   if (!c) return LOR_EINVAL;
-  if (flags & ~LOR_TEST_EXPIRE_WAITS) return set_err(c, LOR_EINVAL, "lor_set_test_hooks: unknown flag");
+  if (flags & ~(LOR_TEST_EXPIRE_WAITS | LOR_TEST_UNSTAGED_CSR))
+    return set_err(c, LOR_EINVAL, "lor_set_test_hooks: unknown flag");
   c->m.test_flags = flags;
   return LOR_OK;
 }

@@ -17,7 +17,7 @@ LOR_F64, LOR_F32 = 0, 1
 LOR_PRECOND_NONE, LOR_PRECOND_JACOBI, LOR_PRECOND_CHEB = 0, 1, 2
 LOR_IR_RESTART, LOR_IR_REPLACE = 0, 1
 LOR_MAX_P = 10
-LOR_TEST_EXPIRE_WAITS = 1
+LOR_TEST_EXPIRE_WAITS, LOR_TEST_UNSTAGED_CSR = 1, 2
 
 EXPORTED = [
     "lor_last_error", "lor_create", "lor_destroy", "lor_sizes", "lor_set_coefficient", "lor_check",
@@ -244,7 +244,9 @@ class LOR:
 
     def set_test_hooks(self, flags):
         """Test hooks (LOR_TEST_EXPIRE_WAITS: the TMA-staged kernels treat
-        their first bounded wait as expired); 0 clears them."""
+        their first bounded wait as expired; LOR_TEST_UNSTAGED_CSR: the
+        explicit-CSR kernel reads every tile from global memory); 0 clears
+        them."""
         self._call("lor_set_test_hooks", C.c_uint(flags), stream=False)
 
     def build_pattern(self, rowptr=None, colidx=None):
