@@ -67,8 +67,8 @@ __global__ void k_jacobi(int64_t n, const VT* __restrict__ dinv, const V* __rest
 }
 
 // ---------------------------------------------------------------- reductions
-// Block partial sums of a.b into partial[blockIdx.x] (fixed grid, fixed
-// order: the result is deterministic).
+// Sum of v over the CTA (blockDim.x a multiple of 32, at most kThreads),
+// returned in thread 0, in a fixed order: the result is deterministic.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double warp_part[kThreads / 32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -76,7 +76,7 @@ __device__ __forceinline__ double block_sum(double v) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int w = 0; w < kThreads / 32; ++w) s += warp_part[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += warp_part[w];
   __syncthreads();
   return s;
 }
