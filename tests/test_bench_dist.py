@@ -141,3 +141,25 @@ def test_summary_of_the_line():
 def test_host_cores_is_positive():
     import bench
     assert bench.host_cores() >= 1
+
+
+def test_profile_figures_are_read_only_while_the_sources_match(tmp_path, monkeypatch):
+    """bench.read_traffic takes a figure from a committed ncu summary only
+    while every source file listed there still has the recorded hash."""
+    import hashlib
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    digest = hashlib.sha256(b"kernel v1").hexdigest()
+    (prof / "k_demo_c2_case.md").write_text("traffic_bytes_per_launch: 123\nfp64_pipe_active_fraction: 0.5\n"
+                                            "source_sha256: %s k.cu\n" % digest)
+    (prof / "k_demo_backward_c2_case.md").write_text("fp64_pipe_active_fraction: 0.9\n"
+                                                     "source_sha256: %s k.cu\n" % digest)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic("k_demo_c2_") == 123.0
+    assert bench.read_traffic("k_demo_c2_", "fp64_pipe_active_fraction") == 0.5
+    assert bench.read_traffic("k_demo_backward_c2_", "fp64_pipe_active_fraction") == 0.9
+    src.write_text("kernel v2")
+    assert bench.read_traffic("k_demo_c2_") is None

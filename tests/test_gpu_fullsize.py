@@ -9,6 +9,9 @@
   the full apply (FP64 and FP32 arithmetic), and PCG to 1e-8 in FP64, mixed
   precision and the mixed-precision refinement (both schemes), whose true
   residual is re-checked with the oracle's operator.
+* the step workload with the reaction term (whole CSR, apply, backward), and
+  handed over as a renumbered, rotated general mesh (whole CSR, apply,
+  smoother).
 * 24^3 elements, p = 5 (1,771,561 DOFs; the gradient workload): dJ/dtheta by
   the adjoint against fourth-order central differences on 16 random
   directions, and the
@@ -186,4 +189,71 @@ def test_gradient_workload_24x24x24_p5():
         d2 = J_at(2 * h * v) - J_at(-2 * h * v)
         fd = (8 * d1 - d2) / (12 * h)
         assert abs(fd - float(g @ v)) <= 1e-6 * gnorm
+    op.close()
+
+
+def test_step_workload_with_reaction_16x16x16_p4():
+    """The definite Helmholtz variant of the step workload (beta = exp(N(0,1))
+    per Gauss point, seed 777): the whole LOR CSR (pattern bit-exact, values
+    FP64 1e-12 and FP32 1e-5 of the row maximum), the apply and the backward
+    in full against the oracle with the reaction term."""
+    prob, mesh, op = setup("c2_16x16x16_p4")
+    p, q = prob.p, prob.q
+    beta = np.exp(np.random.default_rng(777).standard_normal(prob.kappa.shape))
+    op.set_reaction(t(beta.reshape(-1)), check=True)
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True, beta=beta)
+    rp, ci = op.build_pattern()
+    np.testing.assert_array_equal(rp.cpu().numpy(), csr[0])
+    np.testing.assert_array_equal(ci.cpu().numpy().astype(np.int64), csr[1])
+    for dtype, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        v = op.assemble(dtype).cpu().numpy().astype(np.float64)
+        assert rowwise_max_rel_err(csr[0], v, csr[2]) <= tol, dtype
+    rng = np.random.default_rng(5)
+    x, gy = rng.standard_normal(op.ndof), rng.standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ry = oracle.ho_apply(mesh, p, q, prob.kappa, x, beta=beta)
+    assert np.abs(y - ry).max() <= 1e-12 * np.abs(ry).max()
+    gx, gk = op.apply_backward(t(x), t(gy))
+    rgx, rgk = oracle.ho_apply_backward(mesh, p, q, prob.kappa, x, gy, beta=beta)
+    assert np.abs(gx.cpu().numpy() - rgx).max() <= 1e-12 * np.abs(rgx).max()
+    assert np.abs(gk.cpu().numpy() - rgk.ravel()).max() <= 1e-12 * np.abs(rgk).max()
+    op.close()
+
+
+def test_step_workload_as_a_general_mesh_16x16x16_p4():
+    """The step workload handed over in element-restriction form with its
+    DOFs and elements randomly renumbered and every element's frame rotated:
+    the whole LOR CSR (renumbered) against the oracle's (pattern bit-exact,
+    FP64 1e-12, FP32 1e-5), the apply in full, and the Chebyshev-Jacobi
+    smoother (staged explicit-CSR kernel) against the oracle's."""
+    from paper_2210_12253_gb300 import LOR
+    from test_gpu_general import general_from_structured, permuted_csr
+    prob = workload("c2_16x16x16_p4")
+    p, q = prob.p, prob.q
+    mesh = oracle.Mesh(prob.nex, prob.ney, prob.nez, prob.vertices)
+    corners, edofs, perm, eperm, rot, kap, to_new, ess, qmaps = general_from_structured(prob, np.random.default_rng(3))
+    N = perm.size
+    op = LOR.general(p, t(corners), t(edofs), N, t(ess))
+    op.set_coefficient(t(kap).reshape(-1), check=True)
+    csr = oracle.lor_assemble(mesh, p, q, prob.kappa, True)
+    ref = permuted_csr(*csr, perm)
+    rp, ci = op.build_pattern()
+    np.testing.assert_array_equal(rp.cpu().numpy(), ref.indptr)
+    np.testing.assert_array_equal(ci.cpu().numpy().astype(np.int64), ref.indices)
+    for dtype, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        v = op.assemble(dtype).cpu().numpy().astype(np.float64)
+        assert rowwise_max_rel_err(ref.indptr, v, ref.data) <= tol, dtype
+    x = np.random.default_rng(6).standard_normal(N)
+    xn = np.empty(N)
+    xn[perm] = x
+    y = op.apply(t(xn)).cpu().numpy()[perm]
+    ry = oracle.ho_apply(mesh, p, q, prob.kappa, x)
+    assert np.abs(y - ry).max() <= 1e-12 * np.abs(ry).max()
+    op.build_pattern_internal()
+    op.assemble_internal(torch.float64)
+    lam = oracle.power_lambda_max(*csr, power_start_vector(N), 20)
+    op.precond_setup("cheb", torch.float64, degree=3, lambda_max=lam)
+    z = op.precond_apply(t(xn)).cpu().numpy()[perm]
+    zr = oracle.chebyshev(*csr, x, 3, lam / 30, 1.1 * lam)
+    assert np.abs(z - zr).max() <= 1e-12 * np.abs(zr).max()
     op.close()
