@@ -11,8 +11,8 @@
 // sub-hex), then adds the entries straight into the CSR values at positions
 // computed in closed form (no macro-element sparse block is stored), with
 // FP64/FP32 atomics for the entries shared between sub-hexes.  Rows and
-// columns of essential DOFs are skipped and their diagonal pre-set to 1 (A4),
-// so elimination costs no extra pass.
+// columns of essential DOFs are skipped and their diagonal set to 1 by the
+// same kernel (A4), so elimination costs no extra pass.
 //
 // Reaction term (definite Helmholtz, Section 4.1): the block gains beta_s
 // times the sub-hex's trilinear mass matrix by the same 2x2x2 Gauss rule; in
@@ -51,10 +51,11 @@ namespace {
 //         = sum_{a in m} sum_{b in n} 3^{-(|m|+|n|-2)/2} Ghat^ab(w(m,n,a,b)),
 // where Ghat^ab is the Walsh-Hadamard transform of G^ab over the 8 points,
 //   Ghat(w) = sum_g G(g) prod_k eps_k^{w_k},  w = (m without a) xor (n without b).
-// The nodal block is K = H Kt H^T / 64, applied axis by axis.  FP64 work per
-// sub-hex: 6 x 24 additions (transforms), 84 products (Kt), about 200
+// The nodal block is K = H Kt H^T / 64, applied axis by axis.  Work per
+// sub-hex: 6 x 24 additions (transforms), the 84 terms of Kt, about 200
 // additions (H . H^T on the 36 symmetric entries), instead of 8 x 180
-// operations for the nodal formula at each Gauss point.
+// operations for the nodal formula at each Gauss point; in the FP64 kernel
+// the additions run in exact 64-bit fixed point (below).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
 __device__ __forceinline__ constexpr int pair_index(int a, int b) {  // (00,01,02,11,12,22)
