@@ -272,14 +272,16 @@ template <int P>
 constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
                                             : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
 
-// FP64: 768 threads' worth of CTAs per SM (12 CTAs of 64 threads at p = 4,
-// about 80 registers per thread, the rest of the block's state spilled to
-// L1-resident local memory): the kernel is latency-bound, and the extra warps
-// hide the integer block algebra's and the conversions' latencies better than
-// the spills cost.  Measured at p = 4: 0.303 ms with 128 registers (8 CTAs),
-// 0.276 ms here; 16 CTAs (64 registers) 0.302 ms.
+// FP64: 640 threads' worth of CTAs per SM (10 CTAs of 64 threads at p = 4,
+// about 96 registers per thread, the rest of the block's state spilled to
+// local memory): the kernel is latency-bound, and the extra warps hide the
+// integer block algebra's and the conversions' latencies better than the
+// spills cost.  Measured at p = 4 (event-timed): 0.300 ms with 128 registers
+// (8 CTAs, no spills), 0.278 ms here; 12 CTAs (80 registers) the same time
+// with 2.6x the spill traffic to DRAM (126 against 48 MB per launch); 16 CTAs
+// (64 registers) 0.302 ms.
 template <int P, typename VT>
-constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (768 / kAsmThreads<P> > 1 ? 768 / kAsmThreads<P> : 1) : 1;
+constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (640 / kAsmThreads<P> > 1 ? 640 / kAsmThreads<P> : 1) : 1;
 
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
