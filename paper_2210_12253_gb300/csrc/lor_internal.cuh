@@ -244,22 +244,27 @@ __device__ __forceinline__ double lor_rcp(double x) {
   return fma(r, e, r);
 }
 
-// 1/sqrt(x) in FP64 for x > 0 in the FP32 normal range (1.2e-38 .. 3.4e38):
-// an FP32 seed (x's leading 20 mantissa bits, the hardware rsqrt
-// approximation: about 20 correct bits) refined by one Newton step with its
-// second-order term, y (1 + e/2 + 3 e^2/8) with e = 1 - x y^2 (the error
-// left is O(e^3), below FP64 rounding; within 1.3 ulp in a CPU emulation over
-// 1e-30 .. 1e30).  The FP64 <-> FP32 moves are integer bit operations, since
-// the conversion instructions issue on the FP64 pipe.  Five FP64 operations.
+// 1/sqrt(x) in FP64 for any normal x > 0.  x = 4^k m with m in [1, 4)
+// (exponent-field arithmetic, exact), an FP32 seed for 1/sqrt(m) (m's
+// leading 20 mantissa bits, the hardware rsqrt approximation: about 20
+// correct bits), one Newton step with its second-order term,
+// y (1 + e/2 + 3 e^2/8) with e = 1 - m y^2 (the error left is O(e^3), below
+// FP64 rounding), and the exact scaling by 2^-k.  Within 1.3 ulp in a CPU
+// emulation over 1e-300 .. 1e300.  The FP64 <-> FP32 moves and the scalings
+// are integer bit operations, since the conversion instructions issue on the
+// FP64 pipe.  Five FP64 operations.
 __device__ __forceinline__ double lor_rsqrt(double x) {
-  const int hi = __double2hiint(x);
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int k = (((hi >> 20) & 0x7FF) - 1023) >> 1;  // floor(unbiased exponent / 2)
+  const double m = __hiloint2double(hi - 2 * k * (1 << 20), lo);
   float yf;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float((hi - (896 << 20)) << 3)));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float((__double2hiint(m) - (896 << 20)) << 3)));
   const int yb = __float_as_int(yf);
   const double y = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
-  const double t = x * y;
+  const double t = m * y;
   const double e = fma(-t, y, 1.0);
-  return fma(y * e, fma(0.375, e, 0.5), y);
+  const double r = fma(y * e, fma(0.375, e, 0.5), y);  // 1/sqrt(m), in (1/2, 1]
+  return __hiloint2double(__double2hiint(r) - k * (1 << 20), __double2loint(r));
 }
 
 // -------------------------------------------------------------------------

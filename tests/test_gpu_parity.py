@@ -323,3 +323,28 @@ def test_bad_coefficient_and_call_order():
     with pytest.raises(LORError) as ei:
         op.precond_setup("jacobi", torch.float64)
     assert ei.value.code == 7
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1e-3, 1e4, 1e9])
+def test_fp64_path_at_extreme_mesh_scales(scale):
+    """The FP64 setup and assembly form the metric from M = J^T J, whose
+    determinant is det(J)^2, and take 1/sqrt(det M) by a range-reduced
+    seed: meshes of any size give the oracle's LOR matrix and apply (both
+    scale with the element size; det M spans 1e-60 .. 1e+54 here)."""
+    from paper_2210_12253_gb300 import LOR
+    dims, p = (3, 2, 2), 3
+    prob = make_problem("t", *dims, p, seed=1, jitter=0.1, kappa="lognormal", rhs="normal")
+    V = prob.vertices * scale
+    mesh = oracle.Mesh(*dims, V)
+    op = LOR(p, *dims, t(V))
+    op.set_coefficient(t(prob.kappa).reshape(-1), check=True)
+    rp, ci = op.build_pattern()
+    v = op.assemble(torch.float64).cpu().numpy()
+    orp, oci, ov = oracle.lor_assemble(mesh, p, p + 2, prob.kappa, True)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert rowwise_rel_err(orp, v, ov) <= 1e-12
+    x = np.random.default_rng(2).standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ref = oracle.ho_apply(mesh, p, p + 2, prob.kappa, x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()
