@@ -862,9 +862,18 @@ cudaError_t configure(K kernel, size_t bytes, unsigned* mask) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+#include "k_apply_fix.cuh"
+
+namespace {
+
+// The FP64 operator and its backward run the fixed-point kernels of
+// k_apply_fix.cuh; the FP32-arithmetic operator the kernels above.
 template <int P, bool MASS, bool GEN, typename R, typename XV>
 cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* Mq, const XV* x, XV* y,
                     cudaStream_t s) {
+  if constexpr (sizeof(R) == sizeof(double)) return apply_fx_p<P, MASS, GEN>(m, T, Dq, Mq, x, y, s);
   using Z = Sz<P>;
   using L = Lay<P, R>;
   const size_t bytes = sizeof(R) * (L::TABLES + (size_t)L::E * L::PER_ELEM);
@@ -879,6 +888,12 @@ cudaError_t apply_p(const LorMesh& m, const LorTables& T, const R* Dq, const R* 
 template <int P, bool MASS, bool GEN>
 cudaError_t backward_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq, const double* kappa,
                        const double* x, const double* gy, double* gx, double* gk, cudaStream_t s) {
+  return backward_fx_p<P, MASS, GEN>(m, T, Dq, Mq, kappa, x, gy, gx, gk, s);
+}
+template <int P, bool MASS, bool GEN>
+cudaError_t backward_fp64_p(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
+                            const double* kappa, const double* x, const double* gy, double* gx, double* gk,
+                            cudaStream_t s) {
   using Z = Sz<P>;
   using L = Lay<P, double>;
   const size_t bytes = sizeof(double) * (L::TABLES + 2 * (size_t)Z::EB * L::PER_ELEM);
