@@ -214,11 +214,31 @@ def parse_clock_log(lines):
 
 
 # ---------------------------------------------------------------- GPU arm
-def kernel_roofline(name, ms, work, hbm_peak, hbm_src):
+def fixed_point_fields(kind, p, nel, flops, ms):
+    """The fields of a kernel whose FP64 arithmetic runs in 64-bit fixed point
+    on the integer pipe (the operator and its backward): its FP64-equivalent
+    rate (the direct sum-factorisation count over the FP64 peak, which it may
+    exceed) and the fraction of the integer multiply-add peak its
+    32 x 32 -> 64 bit multiply-adds take."""
+    from paper_2210_12253_gb300.perfmodel import (FP64_PEAK_TFLOPS, INT_MAD_PEAK_TOPS, MAD_WIDE_PER_FIXED_MAC,
+                                                 fixed_macs)
+    mads = MAD_WIDE_PER_FIXED_MAC * fixed_macs(kind, p, nel)
+    return {"arith": "int64 fixed point (3 mad.wide.s32 per multiply-add)",
+            "gflops_fp64_equiv": flops / (ms * 1e-3) / 1e9,
+            "frac_fp64_equiv": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "int_mad_tops": mads / (ms * 1e-3) / 1e12,
+            "int_mad_frac": mads / (ms * 1e-3) / 1e12 / INT_MAD_PEAK_TOPS}
+
+
+def kernel_roofline(name, ms, work, hbm_peak, hbm_src, p=None, nel=None):
+    from paper_2210_12253_gb300.perfmodel import FIXED_POINT_KINDS, FP64_PEAK_TFLOPS
     flops, nbytes = work
-    out = {"ms": ms, "gflops_fp64": flops / (ms * 1e-3) / 1e9, "gbs": nbytes / (ms * 1e-3) / 1e9}
-    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS
-    out["frac_fp64"] = out["gflops_fp64"] / (FP64_PEAK_TFLOPS * 1e3)
+    out = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9}
+    if name in FIXED_POINT_KINDS and p is not None:
+        out.update(fixed_point_fields(name, p, nel, flops, ms))
+    else:
+        out["gflops_fp64"] = flops / (ms * 1e-3) / 1e9
+        out["frac_fp64"] = out["gflops_fp64"] / (FP64_PEAK_TFLOPS * 1e3)
     out["frac_hbm"] = out["gbs"] / hbm_peak
     return out
 
@@ -256,7 +276,7 @@ def run_gpu(args, rank, world, local_rank):
     from paper_2210_12253_gb300.build import build
     from paper_2210_12253_gb300.inputs import power_start_vector, workload
     from paper_2210_12253_gb300.lor import launch_count
-    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS, hbm_peak_gbs, kernel_work
+    from paper_2210_12253_gb300.perfmodel import FP64_PEAK_TFLOPS, INT_MAD_PEAK_TOPS, hbm_peak_gbs, kernel_work
 
     if rank == 0:
         build()
@@ -395,25 +415,35 @@ def run_gpu(args, rank, world, local_rank):
     for n in names:
         ms = statistics.mean(per_kernel[n])
         work = kernel_work(n, p, op.ndof, op.nel, op.nnz, vbytes=8, degree=3)
-        kernels[n] = kernel_roofline(n, ms, work, hbm_peak, hbm_src)
+        kernels[n] = kernel_roofline(n, ms, work, hbm_peak, hbm_src, p, op.nel)
         kernels[n]["gdofs"] = op.ndof / (ms * 1e-3) / 1e9
     # each kernel's committed ncu summary (used only while its sources are unchanged)
     prof = {"setup": "k_setup_c2_", "assemble": "k_assemble_c2_", "apply": "k_apply_c2_",
             "backward": "k_apply_backward_c2_", "precond": "k_stencil_c2_"}
     for n in names:
-        kernels[n]["fp64_pipe_active"] = read_traffic(prof[n], "fp64_pipe_active_fraction")
+        # FP64-pipe kernels: FP64-pipe activity; fixed-point ones: issue-slot activity
+        if "int_mad_frac" in kernels[n]:
+            kernels[n]["issue_active"] = read_traffic(prof[n], "issue_active_fraction")
+        else:
+            kernels[n]["fp64_pipe_active"] = read_traffic(prof[n], "fp64_pipe_active_fraction")
     dominant = max(names, key=lambda n: kernels[n]["ms"])
     dk = kernels[dominant]
     traffic = read_traffic(prof[dominant])
-    roofline = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops_fp64"] / 1e3,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": dk["gflops_fp64"] / 1e3 / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64; no FP64 entry in "
-                               "MEASURED_PEAKS.json)",
-                "traffic": traffic,
-                "fp64_pipe_active": dk["fp64_pipe_active"],
-                "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
-                        "frac": dk["frac_hbm"]}}
+    if "int_mad_frac" in dk:
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": dk["int_mad_tops"], "peak": INT_MAD_PEAK_TOPS,
+                    "unit": "T int32 multiply-adds/s", "frac": dk["int_mad_frac"],
+                    "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2.07 GHz",
+                    "issue_active": dk["issue_active"]}
+    else:
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops_fp64"] / 1e3,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": dk["gflops_fp64"] / 1e3 / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64; no FP64 entry in "
+                                   "MEASURED_PEAKS.json)",
+                    "fp64_pipe_active": dk["fp64_pipe_active"]}
+    roofline.update({"traffic": traffic,
+                     "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                             "frac": dk["frac_hbm"]}})
 
     pcg = None
     if not args.no_pcg:
@@ -586,11 +616,13 @@ def run_refinement(args, op, b, res, u64):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         flops, byts = kernel_work(kind, op.p, op.ndof, op.nel, op.nnz)
-        peak = FP32_PEAK_TFLOPS if kind == "apply_f32" else FP64_PEAK_TFLOPS
         kern[label] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9, "gbs": byts / (ms * 1e-3) / 1e9,
-                       "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
-                       "tflops": flops / (ms * 1e-3) / 1e12, "frac_alu": flops / (ms * 1e-3) / 1e12 / peak,
-                       "alu": "fp32" if kind == "apply_f32" else "fp64"}
+                       "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm}
+        if kind == "apply_f32":
+            kern[label].update({"tflops": flops / (ms * 1e-3) / 1e12,
+                                "frac_alu": flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, "alu": "fp32"})
+        else:
+            kern[label].update(fixed_point_fields(kind, op.p, op.nel, flops, ms))
     y32 = op.apply_f32(x)
     y64 = op.apply(x)
     kern["apply_f32_max_rel_err"] = ((y32 - y64).abs().max() / y64.abs().max()).item()
@@ -794,7 +826,7 @@ def run_helmholtz(args, dev):
     for i, n in enumerate(names):
         ms = statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in evs)
         work = kernel_work(n, p, op.ndof, op.nel, op.nnz, vbytes=8, degree=3)
-        kernels[n] = kernel_roofline(n, ms, work, hbm_peak, hbm_src)
+        kernels[n] = kernel_roofline(n, ms, work, hbm_peak, hbm_src, p, op.nel)
         kernels[n]["gdofs"] = op.ndof / (ms * 1e-3) / 1e9
     step_ms = statistics.mean(ev[0].elapsed_time(ev[6]) for ev in evs)
     op.close()
@@ -1094,11 +1126,13 @@ def sweep_degree(name, dev, reps, flush, kernels=SWEEP_KERNELS, pcg=True):
         vb = 4 if kname.endswith("f32") else 8
         flops, nbytes = kernel_work(kind, p, op.ndof, op.nel, op.nnz, vbytes=vb, degree=3)
         res[kname] = {"ms": ms, "gdofs": op.ndof / (ms * 1e-3) / 1e9,
-                      "frac_fp64": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                       "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
         if kname.endswith("f32") and kname != "precond_f32":  # FP32 flops against the FP32 peak
-            del res[kname]["frac_fp64"]
             res[kname]["frac_fp32"] = flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS
+        elif kind in ("apply", "backward"):
+            res[kname].update(fixed_point_fields(kind, p, op.nel, flops, ms))
+        else:
+            res[kname]["frac_fp64"] = flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
     if pcg:
         # PCG per iteration (30 iterations from x0 = 0, fixed count), mixed
         # precision and FP64, with the same lambda_max
@@ -1165,8 +1199,10 @@ def run_sweep_compact(args, dev):
            "p": [r["p"] for r in rows], "ndof": [r["ndof"] for r in rows]}
     for k in SWEEP_KERNELS:
         out[k + "_gdofs"] = [round(r[k]["gdofs"], 4) for r in rows]
-    for k in ("assemble_f64", "apply", "backward"):
-        out[k + "_frac_fp64"] = [round(r[k]["frac_fp64"], 3) for r in rows]
+    out["assemble_f64_frac_fp64"] = [round(r["assemble_f64"]["frac_fp64"], 3) for r in rows]
+    for k in ("apply", "backward"):
+        out[k + "_int_mad_frac"] = [round(r[k]["int_mad_frac"], 3) for r in rows]
+        out[k + "_frac_fp64_equiv"] = [round(r[k]["frac_fp64_equiv"], 3) for r in rows]
     out["precond_f32_frac_hbm"] = [round(r["precond_f32"]["frac_hbm"], 3) for r in rows]
     return out
 

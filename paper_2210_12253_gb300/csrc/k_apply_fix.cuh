@@ -41,9 +41,9 @@
 // FP64.
 #pragma once
 
-namespace {
+#include "fixed_point.cuh"
 
-constexpr int kFxTop = 57;  // stored values: |X| <= 2^57
+namespace {
 
 // CTAs per SM the register budget is sized for (apply, backward): the
 // kernels are bound by issue latency, and two CTAs per SM (about 128
@@ -53,19 +53,6 @@ template <int P>
 constexpr int kFxApplyBlocks = 2;
 template <int P>
 constexpr int kFxBackwardBlocks = 2;
-
-// X = h 2^31 + l with 0 <= l < 2^31
-struct Fx {
-  int h, l;
-};
-__device__ __forceinline__ Fx fx_split(long long X) {
-  return Fx{(int)(X >> 31), (int)(X & 0x7fffffffll)};
-}
-// packed table entry: high word h, low word l (the split of C)
-__device__ __forceinline__ long long fx_pack(long long C) {
-  return (long long)(((unsigned long long)(unsigned)(int)(C >> 31) << 32) | (unsigned long long)(C & 0x7fffffffll));
-}
-__device__ __forceinline__ Fx fx_unpack(long long c) { return Fx{(int)(c >> 32), (int)(unsigned)(unsigned long long)c}; }
 
 struct FAcc {
   long long hi, mid;
@@ -77,36 +64,6 @@ __device__ __forceinline__ void fx_mac(FAcc& a, Fx x, Fx c) {
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.l), "r"(c.h));
 }
 __device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (a.mid >> 31); }
-
-// biased exponent field of x (0 for zero and subnormals)
-__device__ __forceinline__ int fx_expo(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
-
-// x 2^(1079 - emax), rounded to nearest, for |x| < 2^(emax - 1022): below 2^57.
-// Zero and subnormal x give 0.
-__device__ __forceinline__ long long fx_from_double(double x, int emax) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)(b >> 52) & 0x7ff;
-  const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);
-  const int r = emax - e - 4;  // right shift of the 53-bit significand (>= -4)
-  const int rr = r < 1 ? 1 : (r > 63 ? 63 : r);
-  const unsigned long long X = r <= 0 ? mant << (-r) : (r > 60 ? 0ull : (mant + (1ull << (rr - 1))) >> rr);
-  const long long sgn = (long long)b >> 63;
-  return e == 0 ? 0ll : ((long long)X ^ sgn) - sgn;
-}
-
-// X 2^-scale as FP64, rounded to nearest (ties away from zero); results
-// below the normal range give zero, above it infinity.
-__device__ __forceinline__ double fx_to_double(long long X, int scale) {
-  const unsigned long long sgn = (unsigned long long)(X >> 63);
-  const unsigned long long a = ((unsigned long long)X ^ sgn) - sgn;
-  const int lz = __clzll((long long)a);
-  const unsigned long long mm = a << (lz & 63);
-  const unsigned long long mant = (mm >> 11) + ((mm >> 10) & 1ull);  // 53 bits with the leading one
-  const int ex = 1085 - lz - scale;                                   // biased exponent - 1
-  unsigned long long bits = ((unsigned long long)(long long)ex << 52) + mant;
-  bits = ex < 0 ? 0ull : (ex >= 2046 ? 0x7ff0000000000000ull : bits);
-  return X == 0 ? 0.0 : __longlong_as_double((long long)(bits | (sgn << 63)));
-}
 
 // X 2^sh for a signed shift (left: sh <= 57 keeps |X| <= 2^57 by
 // construction; right: rounded to nearest, 0 beyond 62 places)
@@ -447,29 +404,26 @@ __device__ __forceinline__ void fx_line_gradient(const FxTab<P>& t, const long l
   if constexpr (MASS) fx_fwd_B<P>(t, f, u);
 }
 
-// v = D g at the q points of a z line, D[e][6][q^3] in FP64: per point the
-// gradient renormalised to 57 bits and the 6 entries at their largest
-// exponent, the 3 x 3 product in fixed point; sc[g2] is v's scale relative to
-// the gradient's (INT_MAX where v is zero).  With the reaction term also
+// v = D g at the q points of a z line, D in the setup's fixed-point form
+// (packed entries De[c][q^3] at each point's scale, offsets Ds[q^3]): per
+// point the gradient renormalised to 57 bits, the 3 x 3 product in fixed
+// point; sc[g2] is v's scale relative to the gradient's (INT_MAX where v is
+// zero).  With the reaction term also
 // u <- M u, scm[g2] the scale at which u must be aligned with v (u meets d^T
 // v2 through B^T: it sits S_D - S_B off v after the alignment).
 template <int P, bool MASS>
-__device__ __forceinline__ void fx_line_D(const double* __restrict__ De, const double* __restrict__ Me, int g01,
-                                          FxS S, long long (*g)[Sz<P>::Q], long long* u, int* sc, int* scm) {
+__device__ __forceinline__ void fx_line_D(const long long* __restrict__ De, const int* __restrict__ Ds,
+                                          const double* __restrict__ Me, int g01, FxS S, long long (*g)[Sz<P>::Q],
+                                          long long* u, int* sc, int* scm) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q;
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
     const int pt = g01 + Q2 * g2;
-    double d[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] = De[c * Q3 + pt];
-    int em = 0;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) em = max(em, fx_expo(d[c]));
     Fx D[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) D[c] = fx_split(fx_from_double(d[c], em));
+    for (int c = 0; c < 6; ++c) D[c] = fx_unpack(De[c * Q3 + pt]);
+    const int sd = Ds[pt];
     unsigned long long og = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) fx_or(og, g[c][g2]);
@@ -490,7 +444,7 @@ __device__ __forceinline__ void fx_line_D(const double* __restrict__ De, const d
     g[0][g2] = fx_res(v0);
     g[1][g2] = fx_res(v1);
     g[2][g2] = fx_res(v2);
-    sc[g2] = (em == 0 || og == 0) ? 0x7fffffff : 1079 - em - 62 + shg;
+    sc[g2] = (sd == INT_MAX || og == 0) ? INT_MAX : sd + shg;
     if constexpr (MASS) {
       const double mv = Me[pt];
       const int emm = fx_expo(mv);
@@ -500,7 +454,7 @@ __device__ __forceinline__ void fx_line_D(const double* __restrict__ De, const d
       u[g2] = fx_res(w);
       // u (B(x)B(x)B) sits S_B - S_D above the gradient; B^T u must come out
       // at the scale of d^T v2, so u is aligned as if S_B - S_D finer again
-      scm[g2] = (emm == 0 || u[g2] == 0) ? 0x7fffffff : 1079 - emm - 62 + shu + 2 * (S.B - S.D);
+      scm[g2] = (emm == 0 || u[g2] == 0) ? INT_MAX : 1079 - emm - 62 + shu + 2 * (S.B - S.D);
     }
   }
 }
@@ -512,24 +466,24 @@ template <int P, bool MASS>
 __device__ __forceinline__ int fx_line_align(long long (*v)[Sz<P>::Q], long long* u, const int* sc, const int* scm) {
   using Z = Sz<P>;
   constexpr int Q = Z::Q;
-  int smin = 0x7fffffff;
+  int smin = INT_MAX;
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
     smin = min(smin, sc[g2]);
     if (MASS) smin = min(smin, scm[g2]);
   }
-  if (smin == 0x7fffffff) smin = 0;  // D (and M) zero along the whole line
+  if (smin == INT_MAX) smin = 0;  // D (and M) zero along the whole line
   unsigned long long acc = 0;
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
-    const int r = sc[g2] == 0x7fffffff ? 63 : sc[g2] - smin;
+    const int r = sc[g2] == INT_MAX ? 63 : sc[g2] - smin;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       v[c][g2] = fx_shift(v[c][g2], -r);
       fx_or(acc, v[c][g2]);
     }
     if (MASS) {
-      const int rm = scm[g2] == 0x7fffffff ? 63 : scm[g2] - smin;
+      const int rm = scm[g2] == INT_MAX ? 63 : scm[g2] - smin;
       u[g2] = fx_shift(u[g2], -rm);
       fx_or(acc, u[g2]);
     }
@@ -783,7 +737,8 @@ __global__ void __launch_bounds__(Sz<P>::T, kFxApplyBlocks<P>) k_apply_fx(LorMes
       int ps[Q], pm[MASS ? Q : 1];
       fx_line_gradient<P, MASS>(t, A + (size_t)lez * L::PER_ELEM + L::A1, g01, kFxTop - sl[lez * kFxSlots + 2], v,
                                 u);
-      fx_line_D<P, MASS>(Dq + e * 6 * Q3, MASS ? Mq + e * Q3 : nullptr, g01, S, v, u, ps, pm);
+      fx_line_D<P, MASS>(reinterpret_cast<const long long*>(Dq) + e * 6 * Q3, lor_d_scales(Dq, m.nel * Q3) + e * Q3,
+                         MASS ? Mq + e * Q3 : nullptr, g01, S, v, u, ps, pm);
       sline = fx_line_align<P, MASS>(v, u, ps, pm);
       accT = fx_line_transpose_z<P, MASS>(t, v, u, Tz);
     }
@@ -849,7 +804,8 @@ __global__ void __launch_bounds__(Sz<P>::TBW, kFxBackwardBlocks<P>) k_apply_back
       int ps[Q], pm[MASS ? Q : 1];
       fx_line_gradient<P, MASS>(t, A + (size_t)lez * L::PER_ELEM + L::A1, g01, kFxTop - sl[lez * kFxSlots + 2], v,
                                 u);
-      fx_line_D<P, MASS>(Dq + e * 6 * Q3, MASS ? Mq + e * Q3 : nullptr, g01, S, v, u, ps, pm);
+      fx_line_D<P, MASS>(reinterpret_cast<const long long*>(Dq) + e * 6 * Q3, lor_d_scales(Dq, m.nel * Q3) + e * Q3,
+                         MASS ? Mq + e * Q3 : nullptr, g01, S, v, u, ps, pm);
       if (gkappa) {
         const int sgx = fx_fwd_scales(slx + lez * kFxSlots, S).sg;
         long long gxl[3][Q];
@@ -872,7 +828,7 @@ __global__ void __launch_bounds__(Sz<P>::TBW, kFxBackwardBlocks<P>) k_apply_back
                    fx_split((long long)((unsigned long long)v[c][g2] << shv)));
           const int pt = g01 + Q2 * g2;
           const int scale = (sgx + shx) + (sg + ps[g2] + shv) - 62;
-          const double tv = (ax && av && ps[g2] != 0x7fffffff) ? fx_to_double(fx_res(d), scale) : 0.0;
+          const double tv = (ax && av && ps[g2] != INT_MAX) ? fx_to_double(fx_res(d), scale) : 0.0;
           gkappa[e * Q3 + pt] = tv / kappa[e * Q3 + pt];
         }
       }

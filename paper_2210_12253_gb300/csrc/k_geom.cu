@@ -9,6 +9,7 @@
 // likewise for the other columns), so each Jacobian column is tabulated once
 // per element on a q x q grid in shared memory, and so are the squared column
 // norms; per point the metric follows from the rest of M = J^T J.
+#include "fixed_point.cuh"
 #include "lor_internal.cuh"
 
 namespace {
@@ -20,7 +21,11 @@ namespace {
 // det M and one reciprocal square root (fewer FP64 instructions than the
 // adjugate rows of J, its determinant and reciprocal, and six dot products).
 // det M > 0 is checked here; the sign of det J was checked at context
-// creation (the mesh does not change afterwards).
+// creation (the mesh does not change afterwards).  D is stored in the
+// fixed-point form the FP64 operator multiplies it in (fixed_point.cuh): the
+// six entries of a point at the point's largest exponent, converted here by
+// integer operations while the FP64 pipe bounds this kernel, instead of at
+// every application.
 template <int P>
 __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
                                                double* __restrict__ kcopy, double* __restrict__ Dq,
@@ -61,18 +66,33 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
       if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
       if (!(detM > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
       const double s = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(detM);
-      double* D = Dq + e * 6 * Q3 + pt;
-      D[0 * Q3] = s * A00;
-      D[1 * Q3] = s * A01;
-      D[2 * Q3] = s * A02;
-      D[3 * Q3] = s * A11;
-      D[4 * Q3] = s * A12;
-      D[5 * Q3] = s * A22;
+      const double d[6] = {s * A00, s * A01, s * A02, s * A11, s * A12, s * A22};
+      int em = 0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) em = max(em, fx_expo(d[c]));
+      long long* D = reinterpret_cast<long long*>(Dq) + e * 6 * Q3 + pt;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) D[c * Q3] = fx_pack(fx_from_double(d[c], em));
+      lor_d_scales(Dq, m.nel * Q3)[e * Q3 + pt] = em == 0 ? INT_MAX : 1079 - em - 62;
       kcopy[e * Q3 + pt] = k;
     }
     __syncthreads();
   }
   if (bad) atomicOr(status, bad);
+}
+
+// FP32 copy of D for the FP32-arithmetic operator: value = X 2^-(sd + 62).
+__global__ void __launch_bounds__(256) k_d_to_f32(const double* __restrict__ Dq, int64_t nq, float* __restrict__ out,
+                                                  int Q3) {
+  const long long* D = reinterpret_cast<const long long*>(Dq);
+  const int* sd = lor_d_scales(Dq, nq);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 6 * nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / (6 * Q3), pt = i % Q3;
+    const int sc = sd[e * Q3 + pt];
+    const Fx f = fx_unpack(D[i]);
+    const long long X = (long long)f.h * 2147483648ll + f.l;
+    out[i] = sc == INT_MAX ? 0.0f : (float)fx_to_double(X, sc + 62);
+  }
 }
 
 // Reaction term (the definite Helmholtz operator of Section 4.1): at every
@@ -228,6 +248,15 @@ cudaError_t lor_launch_setup(const LorMesh& m, const LorTables& T, const double*
 #undef LOR_CASE
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t lor_launch_d_to_f32(const LorMesh& m, const double* Dq, float* out, cudaStream_t s) {
+  const int Q3 = (m.p + 2) * (m.p + 2) * (m.p + 2);
+  const int64_t nq = m.nel * (int64_t)Q3;
+  const int64_t blocks = (6 * nq + 255) / 256;
+  k_d_to_f32<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(Dq, nq, out, Q3);
+  lor_count_launch();
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 #include <new>
 #include <string>
 
+#include "fixed_point.cuh"
 #include "lor_internal.cuh"
 
 namespace {
@@ -278,7 +279,7 @@ int lor_ensure_f32_factors(lor_ctx* c, cudaStream_t s) {
   int rc = alloc(c, &c->Dq32, 6 * nq, "FP32 D");
   if (!rc && c->have_beta) rc = alloc(c, &c->Mq32, nq, "FP32 beta w detJ");
   if (rc) return rc;
-  cudaError_t e = lor_launch_to_f32(c->Dq, c->Dq32, 6 * nq, s);
+  cudaError_t e = lor_launch_d_to_f32(c->m, c->Dq, c->Dq32, s);
   if (e == cudaSuccess && c->have_beta) e = lor_launch_to_f32(c->Mq, c->Mq32, nq, s);
   if (e != cudaSuccess) return cuda_err(c, e, "FP32 operator factors");
   c->have_d32 = true;
@@ -467,7 +468,7 @@ int lor_set_coefficient(lor_ctx* c, const double* d_kappa, void* stream) {
   if (!c) return LOR_EINVAL;
   if (!d_kappa) return set_err(c, LOR_EINVAL, "lor_set_coefficient: kappa is NULL");
   const int64_t nq = c->m.nel * (int64_t)c->T.q * c->T.q * c->T.q;
-  int rc = alloc(c, &c->Dq, 6 * nq, "D");
+  int rc = alloc(c, &c->Dq, (size_t)lor_d_doubles(nq), "D");
   if (!rc) rc = alloc(c, &c->kappa, nq, "kappa");
   if (rc) return rc;
   cudaError_t e = lor_launch_setup(c->m, c->T, d_kappa, c->kappa, c->Dq, c->d_status, S(stream));

@@ -59,7 +59,7 @@ struct lor_ctx {
   size_t device_bytes = 0;  // held by the buffers below (allocated through alloc())
   // owned device buffers
   double* verts = nullptr;
-  double* Dq = nullptr;        // [nel][6][q^3]: kappa w detJ J^-1 J^-T (00,01,02,11,12,22)
+  double* Dq = nullptr;        // kappa w detJ J^-1 J^-T (00,01,02,11,12,22) in fixed point: [nel][6][q^3] packed + [nel][q^3] scales (fixed_point.cuh)
   double* kappa = nullptr;     // [nel][q^3]
   double* beta = nullptr;      // [nel][q^3] reaction coefficient (copy), when set
   double* Mq = nullptr;        // [nel][q^3] beta w detJ, when set
@@ -301,6 +301,8 @@ cudaError_t lor_launch_apply_f32v_accumulate(const LorMesh& m, const LorTables& 
                                              const float* x, float* y, cudaStream_t s);
 // b = (float) a, n elements
 cudaError_t lor_launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+// FP32 copy of the setup's fixed-point D (6 nq floats, [e][c][q^3])
+cudaError_t lor_launch_d_to_f32(const LorMesh& m, const double* Dq, float* out, cudaStream_t s);
 cudaError_t lor_launch_apply_backward(const LorMesh& m, const LorTables& T, const double* Dq, const double* Mq,
                                       const double* kappa, const double* x, const double* gy, double* gx,
                                       double* gkappa, cudaStream_t s);

@@ -14,9 +14,16 @@ The HBM peak is MEASURED_PEAKS.json's copy bandwidth.
 import json
 import os
 
-SMS, DFMA_PER_CLK_SM, FFMA_PER_CLK_SM, MAX_SM_GHZ = 152, 2, 128, 2.07
+SMS, DFMA_PER_CLK_SM, FFMA_PER_CLK_SM, IMAD_PER_CLK_SM, MAX_SM_GHZ = 152, 2, 128, 64, 2.07
 FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * MAX_SM_GHZ / 1e3  # 1.2586
 FP32_PEAK_TFLOPS = SMS * FFMA_PER_CLK_SM * 2 * MAX_SM_GHZ / 1e3  # 80.55 (an own FFMA loop: 74.6)
+# 32 x 32 -> 64 bit integer multiply-adds (mad.wide.s32), lanes per second:
+# 152 x 64 x 2.07 GHz = 20.14 T (an own loop: 59.4 lanes/clk/SM)
+INT_MAD_PEAK_TOPS = SMS * IMAD_PER_CLK_SM * MAX_SM_GHZ / 1e3
+# the FP64 operator and its backward run in 64-bit fixed point on the integer
+# pipe; each fixed-point multiply-add is three 32 x 32 -> 64 bit ones
+FIXED_POINT_KINDS = ("apply", "backward", "apply_helmholtz", "backward_helmholtz")
+MAD_WIDE_PER_FIXED_MAC = 3
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -105,6 +112,52 @@ def backward_flops_per_element(p):
     return 6 * sumfact_fma(p) + 21 * (p + 2) ** 3
 
 
+def folded_forward_macs(p):
+    """Multiply-adds of one even-odd folded 1D contraction n -> q (B_1D or
+    d_1D): per output pair the even part (n/2 entries, plus the middle node
+    when n is odd) and the odd part (n/2); the middle output (q odd) takes
+    the even or the odd part alone."""
+    n, q = p + 1, p + 2
+    return (q // 2) * ((n & 1) + 2 * (n // 2)) + (q & 1) * (n // 2)
+
+
+def folded_transpose_macs(p, parts=1):
+    """Multiply-adds of one folded transposed contraction q -> n with `parts`
+    tables summed (B^T v1, or B^T v1 + d^T v2)."""
+    n, q = p + 1, p + 2
+    return parts * ((n // 2) * ((q & 1) + 2 * (q // 2)) + (n & 1) * (q // 2))
+
+
+def apply_fixed_macs_per_element(p, mass=False):
+    """Fixed-point multiply-adds per element of the FP64 apply as the kernel
+    runs it: x stage (B and d on n^2 lines), y stage (3 contractions on n q
+    lines), z stage (3, with the reaction term 4, on q^2 lines), the 3 x 3
+    D product (9 per Gauss point, the reaction's M 1 more), the transposed z
+    (B^T, B^T, d^T or B^T + d^T), y (B^T and B^T + d^T) and x (B^T + d^T)
+    stages."""
+    n, q = p + 1, p + 2
+    f, t1, t2 = folded_forward_macs(p), folded_transpose_macs(p, 1), folded_transpose_macs(p, 2)
+    return (n * n * 2 * f + n * q * 3 * f + q * q * (4 if mass else 3) * f
+            + q ** 3 * (10 if mass else 9)
+            + q * q * (2 * t1 + (t2 if mass else t1)) + n * q * (t1 + t2) + n * n * t2)
+
+
+def backward_fixed_macs_per_element(p, mass=False):
+    """The apply's multiply-adds plus the second field's forward pass (x, y
+    and z stages) and grad(x) . (D grad(gy)) (3 per Gauss point)."""
+    n, q = p + 1, p + 2
+    f = folded_forward_macs(p)
+    return apply_fixed_macs_per_element(p, mass) + n * n * 2 * f + n * q * 3 * f + q * q * 3 * f + 3 * q ** 3
+
+
+def fixed_macs(kind, p, nel):
+    """Fixed-point multiply-adds of one launch of a FIXED_POINT_KINDS kernel."""
+    mass = kind.endswith("helmholtz")
+    per = backward_fixed_macs_per_element(p, mass) if kind.startswith("backward") else \
+        apply_fixed_macs_per_element(p, mass)
+    return per * nel
+
+
 def reaction_extra_apply_flops_per_element(p):
     """The reaction term's share of the apply: B_z on the q^2 BB lines and its
     transpose (q^3 n FMAs each) and the scaling by beta w detJ (q^3)."""
@@ -134,17 +187,18 @@ def kernel_work(kind, p, ndof, nel, nnz, vbytes=8, degree=3):
     nq = nel * q ** 3
     nsub = nel * p ** 3
     if kind == "setup":
-        return setup_flops_per_element(p) * nel, 64 * nq  # kappa in, D (48) + kappa copy out
+        # kappa in, D (48 + a 4-byte scale per point) and the kappa copy out
+        return setup_flops_per_element(p) * nel, 68 * nq
     if kind == "assemble":
         f = assemble_flops_per_element(p) if vbytes == 8 else assemble_f32_flops_per_element(p)
         return f * nel, vbytes * nnz + 8 * nq
     if kind == "apply":
-        return apply_flops_per_element(p) * nel, 16 * ndof + 48 * nq
+        return apply_flops_per_element(p) * nel, 16 * ndof + 52 * nq
     if kind == "apply_f32":
         # the same contractions in FP32 (flops are FP32 here); D read as FP32
         return apply_flops_per_element(p) * nel, 16 * ndof + 24 * nq
     if kind == "backward":
-        return backward_flops_per_element(p) * nel, 24 * ndof + 64 * nq
+        return backward_flops_per_element(p) * nel, 24 * ndof + 68 * nq
     if kind == "reaction_setup":
         # det (3 cross-product terms, 5) and beta w detJ (3); beta in, beta copy and M out
         return 8 * nq, 24 * nq

@@ -541,9 +541,97 @@ def test_kernel_work_uses_the_per_element_counts():
     q = p + 2
     assert pm.kernel_work("setup", p, ndof, nel, nnz)[0] == nel * pm.setup_flops_per_element(p)
     assert pm.kernel_work("assemble", p, ndof, nel, nnz)[0] == nel * pm.assemble_flops_per_element(p)
+    # x in, y read and written; D (48 bytes and a 4-byte scale) per Gauss point
     assert pm.kernel_work("apply", p, ndof, nel, nnz) == (nel * pm.apply_flops_per_element(p),
-                                                           16 * ndof + 48 * nel * q ** 3)
+                                                           16 * ndof + 52 * nel * q ** 3)
     assert pm.kernel_work("backward", p, ndof, nel, nnz)[0] == nel * pm.backward_flops_per_element(p)
     # bytes: values once per nonzero and kappa once per Gauss point
     assert pm.kernel_work("assemble", p, ndof, nel, nnz, vbytes=4) == (nel * pm.assemble_f32_flops_per_element(p),
                                                                        4 * nnz + 8 * nel * q ** 3)
+
+
+def _folded_forward(C, u, odd_table):
+    """Even-odd folded y = C u for a table with C[q-1-g][n-1-i] = +-C[g][i]
+    (+ for B_1D, - for d_1D), counting multiply-adds as the fixed-point
+    kernels do."""
+    q, n = C.shape
+    nh, qh = n // 2, q // 2
+    e = [u[i] + u[n - 1 - i] for i in range(nh)]
+    o = [u[i] - u[n - 1 - i] for i in range(nh)]
+    CE = [[(C[g][i] + C[g][n - 1 - i]) / 2 for i in range(nh)] for g in range(q)]
+    CO = [[(C[g][i] - C[g][n - 1 - i]) / 2 for i in range(nh)] for g in range(q)]
+    y, macs = np.zeros(q), 0
+    for g in range(qh):
+        a = 0.0
+        if n & 1:
+            a += C[g][n // 2] * u[n // 2]
+            macs += 1
+        a += sum(CE[g][i] * e[i] for i in range(nh))
+        b = sum(CO[g][i] * o[i] for i in range(nh))
+        macs += 2 * nh
+        y[g], y[q - 1 - g] = (b + a, b - a) if odd_table else (a + b, a - b)
+    if q & 1:
+        y[q // 2] = sum((CO if odd_table else CE)[q // 2][i] * (o if odd_table else e)[i] for i in range(nh))
+        macs += nh
+    return y, macs
+
+
+def _folded_transpose(C, v, odd_table):
+    """y = C^T v, folded over the q points, with its multiply-add count."""
+    q, n = C.shape
+    nh, qh = n // 2, q // 2
+    e = [v[g] + v[q - 1 - g] for g in range(qh)]
+    o = [v[g] - v[q - 1 - g] for g in range(qh)]
+    CE = [[(C[g][i] + C[g][n - 1 - i]) / 2 for i in range(n)] for g in range(q)]
+    CO = [[(C[g][i] - C[g][n - 1 - i]) / 2 for i in range(n)] for g in range(q)]
+    y, macs = np.zeros(n), 0
+    for i in range(nh):
+        a1 = a2 = 0.0
+        if q & 1:
+            if odd_table:
+                a2 += C[q // 2][i] * v[q // 2]
+            else:
+                a1 += C[q // 2][i] * v[q // 2]
+            macs += 1
+        for g in range(qh):
+            if odd_table:
+                a1 += CE[g][i] * o[g]
+                a2 += CO[g][i] * e[g]
+            else:
+                a1 += CE[g][i] * e[g]
+                a2 += CO[g][i] * o[g]
+            macs += 2
+        y[i], y[n - 1 - i] = a1 + a2, a1 - a2
+    if n & 1:
+        y[n // 2] = sum(C[g][n // 2] * (o if odd_table else e)[g] for g in range(qh))
+        macs += qh
+    return y, macs
+
+
+@pytest.mark.parametrize("p", range(1, 11))
+def test_folded_contraction_counts(p):
+    """The fixed-point kernels' multiply-add counts per 1D contraction: an
+    emulation of the folded contraction reproduces the dense product with
+    B_1D- and d_1D-symmetric tables and takes exactly the counted
+    multiply-adds."""
+    n, q = p + 1, p + 2
+    rng = np.random.default_rng(p)
+    R = rng.standard_normal((q, n))
+    Bt = R + R[::-1, ::-1]  # B[q-1-g][n-1-i] = B[g][i]
+    Dt = R - R[::-1, ::-1]  # d[q-1-g][n-1-i] = -d[g][i]
+    u, v = rng.standard_normal(n), rng.standard_normal(q)
+    for C, odd in ((Bt, False), (Dt, True)):
+        y, macs = _folded_forward(C, u, odd)
+        np.testing.assert_allclose(y, C @ u, rtol=0, atol=1e-12)
+        assert macs == pm.folded_forward_macs(p)
+        y, macs = _folded_transpose(C, v, odd)
+        np.testing.assert_allclose(y, C.T @ v, rtol=0, atol=1e-12)
+        assert macs == pm.folded_transpose_macs(p, 1)
+    assert pm.folded_transpose_macs(p, 2) == 2 * pm.folded_transpose_macs(p, 1)
+    # per element: the stages' line counts times these, plus 9 (10) per Gauss point
+    f, t1, t2 = pm.folded_forward_macs(p), pm.folded_transpose_macs(p, 1), pm.folded_transpose_macs(p, 2)
+    fwd = 2 * n * n * f + 3 * n * q * f + 3 * q * q * f
+    tr = q * q * 3 * t1 + n * q * (t1 + t2) + n * n * t2
+    assert pm.apply_fixed_macs_per_element(p) == fwd + 9 * q ** 3 + tr
+    assert pm.backward_fixed_macs_per_element(p) == 2 * fwd + 12 * q ** 3 + tr
+    assert pm.apply_fixed_macs_per_element(p, mass=True) == fwd + q * q * f + 10 * q ** 3 + tr - q * q * t1 + q * q * t2
