@@ -45,14 +45,25 @@
 
 namespace {
 
-// CTAs per SM the register budget is sized for (apply, backward): the
-// kernels are bound by issue latency, and two CTAs per SM (about 128
-// registers a thread, a few spilled at p >= 8) beat one CTA with all state
-// in registers by 1.3-1.7x (measured at p = 4, 6, 8); three lose again.
+// Launch shape per degree, measured (apply and backward at about 3M DOFs,
+// p = 4..8, against 2-4 alternatives each): elements per CTA (one thread per
+// z line) and the CTAs per SM the register budget is sized for.  The kernels
+// are bound by issue latency: two CTAs per SM (about 128 registers a thread,
+// some spilled at high degree) beat one CTA with all state in registers by
+// 1.3-1.7x for the apply; the backward holds two fields, and from p = 7 its
+// spills at that budget cost more than the second CTA gains.
 template <int P>
 constexpr int kFxApplyBlocks = 2;
 template <int P>
-constexpr int kFxBackwardBlocks = 2;
+constexpr int kFxBackwardBlocks = P >= 7 ? 1 : 2;
+template <int P>
+constexpr int kFxE = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 4 : P == 7 ? 3 : 2;
+template <int P>
+constexpr int kFxEB = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P <= 5 ? 5 : P <= 8 ? 3 : P == 9 ? 2 : 1;
+template <int P>
+constexpr int kFxT = ((kFxE<P> * (P + 2) * (P + 2) + 31) / 32) * 32;
+template <int P>
+constexpr int kFxTB = ((kFxEB<P> * (P + 2) * (P + 2) + 31) / 32) * 32;
 
 struct FAcc {
   long long hi, mid;
@@ -63,7 +74,8 @@ __device__ __forceinline__ void fx_mac(FAcc& a, Fx x, Fx c) {
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.h), "r"(c.l));
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.l), "r"(c.h));
 }
-__device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (a.mid >> 31); }
+// |mid| < 2^62, so mid >> 31 fits in 32 bits (one funnel shift, a sign-extended add)
+__device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (long long)(int)(a.mid >> 31); }
 
 // X 2^sh for a signed shift (left: sh <= 57 keeps |X| <= 2^57 by
 // construction; right: rounded to nearest, 0 beyond 62 places)
@@ -708,12 +720,12 @@ __device__ __forceinline__ void fx_forward_xy(const LorMesh& m, const FxTab<P>& 
 }
 
 template <int P, bool MASS, bool GEN>
-__global__ void __launch_bounds__(Sz<P>::T, kFxApplyBlocks<P>) k_apply_fx(LorMesh m, LorTables T, const double* __restrict__ Dq,
+__global__ void __launch_bounds__(kFxT<P>, kFxApplyBlocks<P>) k_apply_fx(LorMesh m, LorTables T, const double* __restrict__ Dq,
                                                        const double* __restrict__ Mq, const double* __restrict__ x,
                                                        double* __restrict__ y) {
   using Z = Sz<P>;
   using L = Lay<P, double>;
-  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::E, N = Z::N;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = kFxE<P>, N = Z::N;
   extern __shared__ __align__(16) unsigned char apply_smem[];
   __shared__ int sl[E * kFxSlots];
   long long* sm = reinterpret_cast<long long*>(apply_smem);
@@ -723,6 +735,21 @@ __global__ void __launch_bounds__(Sz<P>::T, kFxApplyBlocks<P>) k_apply_fx(LorMes
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
     for (int i = threadIdx.x; i < E * kFxSlots; i += blockDim.x) sl[i] = 0;
     __syncthreads();
+    {  // L2 prefetch of the batch's D (and M), read by the z stage after the x and y stages
+      const int64_t ne = m.nel - e_first < E ? m.nel - e_first : E;
+      const char* d0 = reinterpret_cast<const char*>(Dq + e_first * 6 * Q3);
+      const int64_t nb = ne * 6 * Q3 * (int64_t)sizeof(double);
+      for (int64_t off = (int64_t)threadIdx.x * 128; off < nb; off += (int64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(d0 + off));
+      const char* s0 = reinterpret_cast<const char*>(lor_d_scales(Dq, m.nel * Q3) + e_first * Q3);
+      for (int64_t off = (int64_t)threadIdx.x * 128; off < ne * Q3 * 4; off += (int64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + off));
+      if constexpr (MASS) {
+        const char* m0 = reinterpret_cast<const char*>(Mq + e_first * Q3);
+        for (int64_t off = (int64_t)threadIdx.x * 128; off < nb / 6; off += (int64_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(m0 + off));
+      }
+    }
     fx_forward_xy<P, GEN>(m, t, e_first, E, x, A, sl);
     const int w = threadIdx.x, lez = w / Q2, g01 = w % Q2;
     const bool az = w < E * Q2 && e_first + lez < m.nel;
@@ -752,12 +779,12 @@ cudaError_t apply_fx_p(const LorMesh& m, const LorTables& T, const double* Dq, c
                        double* y, cudaStream_t s) {
   using Z = Sz<P>;
   using L = Lay<P, double>;
-  const size_t bytes = sizeof(long long) * (Z::TABLES + (size_t)Z::E * L::PER_ELEM);
+  const size_t bytes = sizeof(long long) * (Z::TABLES + (size_t)kFxE<P> * L::PER_ELEM);
   static unsigned mask = 0;
   cudaError_t err = configure(k_apply_fx<P, MASS, GEN>, bytes, &mask);
   if (err != cudaSuccess) return err;
-  const int64_t blocks = (m.nel + Z::E - 1) / Z::E;
-  k_apply_fx<P, MASS, GEN><<<(unsigned)blocks, Z::T, bytes, s>>>(m, T, Dq, Mq, x, y);
+  const int64_t blocks = (m.nel + kFxE<P> - 1) / kFxE<P>;
+  k_apply_fx<P, MASS, GEN><<<(unsigned)blocks, kFxT<P>, bytes, s>>>(m, T, Dq, Mq, x, y);
   lor_count_launch();
   return cudaGetLastError();
 }
@@ -766,7 +793,7 @@ cudaError_t apply_fx_p(const LorMesh& m, const LorTables& T, const double* Dq, c
 // gkappa = grad(x)^T (D / kappa) grad(gy) per Gauss point, gx = A_p gy
 // through the same transposed half as the apply.
 template <int P, bool MASS, bool GEN>
-__global__ void __launch_bounds__(Sz<P>::TBW, kFxBackwardBlocks<P>) k_apply_backward_fx(LorMesh m, LorTables T,
+__global__ void __launch_bounds__(kFxTB<P>, kFxBackwardBlocks<P>) k_apply_backward_fx(LorMesh m, LorTables T,
                                                                   const double* __restrict__ Dq,
                                                                   const double* __restrict__ Mq,
                                                                   const double* __restrict__ kappa,
@@ -776,7 +803,7 @@ __global__ void __launch_bounds__(Sz<P>::TBW, kFxBackwardBlocks<P>) k_apply_back
                                                                   double* __restrict__ gkappa) {
   using Z = Sz<P>;
   using L = Lay<P, double>;
-  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = Z::EB, N = Z::N;
+  constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = kFxEB<P>, N = Z::N;
   extern __shared__ __align__(16) unsigned char apply_smem[];
   __shared__ int sl[E * kFxSlots], slx[E * kFxSlots];
   long long* sm = reinterpret_cast<long long*>(apply_smem);
@@ -790,6 +817,21 @@ __global__ void __launch_bounds__(Sz<P>::TBW, kFxBackwardBlocks<P>) k_apply_back
       slx[i] = 0;
     }
     __syncthreads();
+    {  // L2 prefetch of the batch's D (and M), read by the z stage after the x and y stages
+      const int64_t ne = m.nel - e_first < E ? m.nel - e_first : E;
+      const char* d0 = reinterpret_cast<const char*>(Dq + e_first * 6 * Q3);
+      const int64_t nb = ne * 6 * Q3 * (int64_t)sizeof(double);
+      for (int64_t off = (int64_t)threadIdx.x * 128; off < nb; off += (int64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(d0 + off));
+      const char* s0 = reinterpret_cast<const char*>(lor_d_scales(Dq, m.nel * Q3) + e_first * Q3);
+      for (int64_t off = (int64_t)threadIdx.x * 128; off < ne * Q3 * 4; off += (int64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + off));
+      if constexpr (MASS) {
+        const char* m0 = reinterpret_cast<const char*>(Mq + e_first * Q3);
+        for (int64_t off = (int64_t)threadIdx.x * 128; off < nb / 6; off += (int64_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(m0 + off));
+      }
+    }
     fx_forward_xy<P, GEN>(m, t, e_first, E, gy, A, sl, gkappa ? x : nullptr, AX, slx);
     const int w = threadIdx.x, lez = w / Q2, g01 = w % Q2;
     const bool az = w < E * Q2 && e_first + lez < m.nel;
@@ -848,12 +890,12 @@ cudaError_t backward_fx_p(const LorMesh& m, const LorTables& T, const double* Dq
                           cudaStream_t s) {
   using Z = Sz<P>;
   using L = Lay<P, double>;
-  const size_t bytes = sizeof(long long) * (Z::TABLES + 2 * (size_t)Z::EB * L::PER_ELEM);
+  const size_t bytes = sizeof(long long) * (Z::TABLES + 2 * (size_t)kFxEB<P> * L::PER_ELEM);
   static unsigned mask = 0;
   cudaError_t err = configure(k_apply_backward_fx<P, MASS, GEN>, bytes, &mask);
   if (err != cudaSuccess) return err;
-  const int64_t blocks = (m.nel + Z::EB - 1) / Z::EB;
-  k_apply_backward_fx<P, MASS, GEN><<<(unsigned)blocks, Z::TBW, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
+  const int64_t blocks = (m.nel + kFxEB<P> - 1) / kFxEB<P>;
+  k_apply_backward_fx<P, MASS, GEN><<<(unsigned)blocks, kFxTB<P>, bytes, s>>>(m, T, Dq, Mq, kappa, x, gy, gx, gk);
   lor_count_launch();
   return cudaGetLastError();
 }
