@@ -4,15 +4,15 @@
 //
 // A value is an int64 X with |X| <= 2^57 and a power-of-two scale s kept
 // beside it (real value = X 2^-s).  For 32 x 32 -> 64 bit multiply-adds it is
-// split as X = h 2^31 + l with 0 <= l < 2^31; the packed form keeps h in the
-// high and l in the low word of one 64-bit word.
+// split as X = h 2^28 + l with 0 <= l < 2^28 (|h| < 2^30 for |X| <= 2^58);
+// the packed form keeps h in the high and l in the low word of one 64-bit
+// word.
 //
 // Storage of D (k_setup's output, one allocation of 6 nq doubles' worth plus
 // nq int32): entries [e][c][q^3] (c = 00, 01, 02, 11, 12, 22) as packed
 // int64 words, each Gauss point's six at the point's own scale (its largest
-// entry below 2^57), then the points' scale offsets [e][q^3] as int32:
-// sd = 1079 - emax - 62, INT_MAX where all six are zero; a product
-// (g D) / 2^62 of a gradient at scale sg with them has scale sg + sd.
+// entry at most 2^57), then the points' scales [e][q^3] as int32:
+// sd = 1079 - emax (entry = X 2^-sd), INT_MAX where all six are zero.
 #pragma once
 
 #include <climits>
@@ -20,14 +20,14 @@
 
 constexpr int kFxTop = 57;  // stored values: |X| <= 2^57
 
-// X = h 2^31 + l with 0 <= l < 2^31
+// X = h 2^28 + l with 0 <= l < 2^28
 struct Fx {
   int h, l;
 };
-__device__ __forceinline__ Fx fx_split(long long X) { return Fx{(int)(X >> 31), (int)(X & 0x7fffffffll)}; }
+__device__ __forceinline__ Fx fx_split(long long X) { return Fx{(int)(X >> 28), (int)(X & 0xfffffffll)}; }
 // packed word: high word h, low word l (the split of X)
 __device__ __forceinline__ long long fx_pack(long long X) {
-  return (long long)(((unsigned long long)(unsigned)(int)(X >> 31) << 32) | (unsigned long long)(X & 0x7fffffffll));
+  return (long long)(((unsigned long long)(unsigned)(int)(X >> 28) << 32) | (unsigned long long)(X & 0xfffffffll));
 }
 __device__ __forceinline__ Fx fx_unpack(long long c) { return Fx{(int)(c >> 32), (int)(unsigned)(unsigned long long)c}; }
 

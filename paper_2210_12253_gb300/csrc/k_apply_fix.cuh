@@ -17,19 +17,15 @@
 //    gradient components share a scale), and so do the transposed sums that
 //    meet (d^T T1 + B^T T2, d^T U0 + B^T U1); the mass values B(x)B(x)B sit
 //    S_B - S_D above the gradient and are aligned before B^T u meets d^T v2.
-//  * multiply-add: X = Xh 2^31 + Xl and C = Ch 2^31 + Cl (0 <= Xl, Cl < 2^31)
-//    give X C / 2^62 = Xh Ch + (Xh Cl + Xl Ch) / 2^31 + Xl Cl / 2^62; two
-//    int64 accumulators take Xh Ch and Xh Cl + Xl Ch by 32 x 32 -> 64 bit
-//    multiply-adds (mad.wide.s32), and the result is hi + (mid >> 31).  The
-//    dropped Xl Cl term and the final rounding cost under one unit (2^-57 of
-//    the element's largest value) per MAC; FP64 rounds each product and each
-//    partial sum to 2^-53 of its own magnitude.  No term overflows: with
-//    folded inputs below 2^58 and at most 14 MACs per accumulator,
-//    |hi| < 2^57 and |mid| < 2^62.
-//  * the pointwise product v = D g (D in FP64 from the setup): each Gauss
-//    point's gradient is renormalised to 57 bits and its 6 entries of D are
-//    converted with their own largest exponent, the 3 x 3 product is taken in
-//    the same fixed point, the line's points are aligned to its largest scale,
+//  * multiply-add (details at fx_mac below): the product X C / 2^56 from
+//    three 32 x 32 -> 64 bit multiply-adds (mad.wide.s32) into two int64
+//    accumulators; a contraction's output (at most 14 products) is rounded
+//    once and reaches up to 2^62, so its largest value keeps 58-61 bits
+//    before the next stage shifts it to 57.
+//  * the pointwise product v = D g (D stored by the setup in fixed point, each
+//    Gauss point's 6 entries at the point's largest exponent): each point's
+//    gradient is renormalised to 57 bits, the 3 x 3 product is taken in the
+//    same fixed point, the line's points are aligned to its largest scale,
 //    and after the transposed z stage the lines of an element are aligned to
 //    the element's largest (one more barrier).
 //  * conversions int64 <-> FP64 by integer operations (rounding to nearest).
@@ -65,17 +61,31 @@ constexpr int kFxT = ((kFxE<P> * (P + 2) * (P + 2) + 31) / 32) * 32;
 template <int P>
 constexpr int kFxTB = ((kFxEB<P> * (P + 2) * (P + 2) + 31) / 32) * 32;
 
+// A multiply-add's operands (data X and coefficient C: tables, D, M), both
+// |.| <= 2^58, split as X = Xh 2^28 + Xl (0 <= Xl < 2^28, |Xh| < 2^30):
+//   X C / 2^56 = Xh Ch + (Xh Cl + Xl Ch) / 2^28 + Xl Cl / 2^56,
+// hi += Xh Ch and mid += Xh Cl + Xl Ch by 32 x 32 -> 64 bit multiply-adds
+// (mad.wide.s32); the dropped Xl Cl / 2^56 is below one unit.  With at most
+// 14 products (|Xh Ch| < 2^59, |Xh Cl + Xl Ch| < 2^58.6) neither accumulator
+// overflows, and the result hi + mid / 2^28, rounded once, reaches up to
+// 2^62: a stage's largest output keeps 58-61 bits.
+using FxX = Fx;
+using FxC = Fx;
+constexpr int kFxMacShift = 56;  // a multiply-add's product is X C / 2^56
+__device__ __forceinline__ FxX fx_x(long long X) { return fx_split(X); }
+__device__ __forceinline__ FxC fx_c(long long C) { return fx_split(C); }
+__device__ __forceinline__ FxC fx_c_packed(long long c) { return fx_unpack(c); }
+
 struct FAcc {
   long long hi, mid;
 };
-__device__ __forceinline__ FAcc fx_acc() { return FAcc{0ll, 1ll << 30}; }  // mid's bias rounds the final shift
-__device__ __forceinline__ void fx_mac(FAcc& a, Fx x, Fx c) {
+__device__ __forceinline__ FAcc fx_acc() { return FAcc{0ll, 1ll << 27}; }  // mid's bias rounds the final shift
+__device__ __forceinline__ void fx_mac(FAcc& a, FxX x, FxC c) {
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.hi) : "r"(x.h), "r"(c.h));
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.h), "r"(c.l));
   asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.l), "r"(c.h));
 }
-// |mid| < 2^62, so mid >> 31 fits in 32 bits (one funnel shift, a sign-extended add)
-__device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (long long)(int)(a.mid >> 31); }
+__device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (a.mid >> 28); }
 
 // X 2^sh for a signed shift (left: sh <= 57 keeps |X| <= 2^57 by
 // construction; right: rounded to nearest, 0 beyond 62 places)
@@ -84,6 +94,12 @@ __device__ __forceinline__ long long fx_shift(long long X, int sh) {
   const int r = -sh;
   return r > 62 ? 0ll : (X + (1ll << (r - 1))) >> r;
 }
+// the same without a branch, for the renormalising loads (-6 <= sh <= 57;
+// a right shift truncates: under a unit of the 57-bit result)
+__device__ __forceinline__ long long fx_rescale(long long X, int sh) {
+  const int l = sh > 0 ? sh : 0, r = sh > 0 ? 0 : -sh;
+  return (long long)((unsigned long long)X << l) >> r;
+}
 
 // bit length of the largest |X| among the values OR-ed into acc as X ^ (X >> 63)
 __device__ __forceinline__ void fx_or(unsigned long long& acc, long long X) {
@@ -91,8 +107,10 @@ __device__ __forceinline__ void fx_or(unsigned long long& acc, long long X) {
 }
 __device__ __forceinline__ int fx_bits(unsigned long long acc) { return 64 - __clzll((long long)acc); }
 
-// volatile table read (re-read at each use, as the FP64 kernels do)
-__device__ __forceinline__ Fx fx_tab(const long long* tbl, int k) {
+// table entry k, re-read from shared memory at each use (volatile: the
+// tables are not held in registers across the line loops, as in the FP64
+// kernels)
+__device__ __forceinline__ FxC fx_tab(const long long* tbl, int k) {
   return fx_unpack(static_cast<const volatile long long*>(tbl)[k]);
 }
 
@@ -101,9 +119,8 @@ struct FxS {
   int B, D;
 };
 
-// Tables in shared memory with the FP64 layout of Sz: B, d (q x n), BE, BO,
-// DE, DO (q x n/2); returns their scales.  The caller's barrier publishes
-// them.
+// Tables in shared memory (packed words, the order of Sz's FP64 layout): B, d (q x n), BE, BO, DE, DO (q x n/2); returns their scales.  The
+// caller's barrier publishes them.
 template <int P>
 __device__ __forceinline__ FxS fx_load_tables(const LorTables& T, long long* s) {
   using Z = Sz<P>;
@@ -156,7 +173,7 @@ __device__ __forceinline__ FxTab<P> fx_tables(const long long* s) {
 // folded input of a contraction over n nodes (u: |u| <= 2^57)
 template <int P>
 struct FxFoldN {
-  Fx e[Sz<P>::NH > 0 ? Sz<P>::NH : 1], o[Sz<P>::NH > 0 ? Sz<P>::NH : 1], m;
+  FxX e[Sz<P>::NH > 0 ? Sz<P>::NH : 1], o[Sz<P>::NH > 0 ? Sz<P>::NH : 1], m;
 };
 template <int P>
 __device__ __forceinline__ FxFoldN<P> fx_fold_n(const long long* u) {
@@ -164,16 +181,16 @@ __device__ __forceinline__ FxFoldN<P> fx_fold_n(const long long* u) {
   FxFoldN<P> f;
 #pragma unroll
   for (int i = 0; i < Z::NH; ++i) {
-    f.e[i] = fx_split(u[i] + u[Z::N - 1 - i]);
-    f.o[i] = fx_split(u[i] - u[Z::N - 1 - i]);
+    f.e[i] = fx_x(u[i] + u[Z::N - 1 - i]);
+    f.o[i] = fx_x(u[i] - u[Z::N - 1 - i]);
   }
-  f.m = fx_split(Z::NODD ? u[Z::NM] : 0ll);
+  f.m = fx_x(Z::NODD ? u[Z::NM] : 0ll);
   return f;
 }
 // folded input of a transposed contraction over q points
 template <int P>
 struct FxFoldQ {
-  Fx e[Sz<P>::QH], o[Sz<P>::QH], m;
+  FxX e[Sz<P>::QH], o[Sz<P>::QH], m;
 };
 template <int P>
 __device__ __forceinline__ FxFoldQ<P> fx_fold_q(const long long* v) {
@@ -181,10 +198,10 @@ __device__ __forceinline__ FxFoldQ<P> fx_fold_q(const long long* v) {
   FxFoldQ<P> f;
 #pragma unroll
   for (int g = 0; g < Z::QH; ++g) {
-    f.e[g] = fx_split(v[g] + v[Z::Q - 1 - g]);
-    f.o[g] = fx_split(v[g] - v[Z::Q - 1 - g]);
+    f.e[g] = fx_x(v[g] + v[Z::Q - 1 - g]);
+    f.o[g] = fx_x(v[g] - v[Z::Q - 1 - g]);
   }
-  f.m = fx_split(Z::QODD ? v[Z::QM] : 0ll);
+  f.m = fx_x(Z::QODD ? v[Z::QM] : 0ll);
   return f;
 }
 
@@ -278,12 +295,14 @@ __device__ __forceinline__ void fx_bwd(const FxTab<P>& t, const FxFoldQ<P>& f1, 
 // stage's outputs share one shift; the scales named are those of the
 // components with the fewest d, the others sit S_D - S_B off):
 //   [0] largest exponent of the gathered x  -> s0 = 1079 - it
-//   [1] bit length after the x stage        -> Bu at s1 = s0 + S_B - 62 + (57 - it)
-//   [2] bit length after the y stage        -> BB at s2 = s1 + S_B - 62 + (57 - it);
-//                                              gradient at sg = s2 + S_D - 62
+//   [1] bit length after the x stage        -> Bu at s1 = s0 + S_B - 58 + (57 - it)
+//   [2] bit length after the y stage        -> BB at s2 = s1 + S_B - 58 + (57 - it);
+//                                              gradient at sg = s2 + S_D - 58
 //   [3] largest real exponent after the z^T stage, + kFxBias -> T0 at s3 = 57 - (it - kFxBias)
-//   [4] bit length after the y^T stage      -> U0 at s4 = s3 + S_B - 62 + (57 - it);
-//                                              output at s4 + S_D - 62
+//   [4] bit length after the y^T stage      -> U0 at s4 = s3 + S_B - 58 + (57 - it);
+//                                              output at s4 + S_D - 58
+// (a stage's outputs reach up to 2^61; the next stage reads them shifted to
+// 57 bits, right or left)
 constexpr int kFxSlots = 5, kFxBias = 1 << 14;
 
 struct FxScales {
@@ -292,9 +311,9 @@ struct FxScales {
 __device__ __forceinline__ FxScales fx_fwd_scales(const int* sl, FxS S) {
   FxScales r;
   const int s0 = 1079 - sl[0];
-  r.s1 = s0 + S.B - 62 + (kFxTop - sl[1]);
-  r.s2 = r.s1 + S.B - 62 + (kFxTop - sl[2]);
-  r.sg = r.s2 + S.D - 62;
+  r.s1 = s0 + S.B - kFxMacShift + (kFxTop - sl[1]);
+  r.s2 = r.s1 + S.B - kFxMacShift + (kFxTop - sl[2]);
+  r.sg = r.s2 + S.D - kFxMacShift;
   return r;
 }
 
@@ -367,8 +386,8 @@ __device__ __forceinline__ void fx_stage_y(const FxTab<P>& t, long long* A, int 
   long long bu[N], du[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    bu[j] = (long long)((unsigned long long)a1[k * L::KS1 + j * L::LS + g0] << sh);
-    du[j] = (long long)((unsigned long long)a1[L::C1 + k * L::KS1 + j * L::LS + g0] << sh);
+    bu[j] = fx_rescale(a1[k * L::KS1 + j * L::LS + g0], sh);
+    du[j] = fx_rescale(a1[L::C1 + k * L::KS1 + j * L::LS + g0], sh);
   }
   const FxFoldN<P> fb = fx_fold_n<P>(bu), fd = fx_fold_n<P>(du);
   long long y[Q];
@@ -404,13 +423,13 @@ __device__ __forceinline__ void fx_line_gradient(const FxTab<P>& t, const long l
   constexpr int N = Z::N;
   long long v[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = (long long)((unsigned long long)a2[L::C2 + k * L::KS2 + g01] << sh);
+  for (int k = 0; k < N; ++k) v[k] = fx_rescale(a2[L::C2 + k * L::KS2 + g01], sh);
   fx_fwd_B<P>(t, fx_fold_n<P>(v), g[0]);
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = (long long)((unsigned long long)a2[2 * L::C2 + k * L::KS2 + g01] << sh);
+  for (int k = 0; k < N; ++k) v[k] = fx_rescale(a2[2 * L::C2 + k * L::KS2 + g01], sh);
   fx_fwd_B<P>(t, fx_fold_n<P>(v), g[1]);
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = (long long)((unsigned long long)a2[k * L::KS2 + g01] << sh);
+  for (int k = 0; k < N; ++k) v[k] = fx_rescale(a2[k * L::KS2 + g01], sh);
   const FxFoldN<P> f = fx_fold_n<P>(v);
   fx_fwd_D<P>(t, f, g[2]);
   if constexpr (MASS) fx_fwd_B<P>(t, f, u);
@@ -432,17 +451,15 @@ __device__ __forceinline__ void fx_line_D(const long long* __restrict__ De, cons
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
     const int pt = g01 + Q2 * g2;
-    Fx D[6];
+    FxC D[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) D[c] = fx_unpack(De[c * Q3 + pt]);
+    for (int c = 0; c < 6; ++c) D[c] = fx_c_packed(De[c * Q3 + pt]);
     const int sd = Ds[pt];
     unsigned long long og = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) fx_or(og, g[c][g2]);
     const int shg = kFxTop - fx_bits(og);
-    const Fx a = fx_split((long long)((unsigned long long)g[0][g2] << shg)),
-             b = fx_split((long long)((unsigned long long)g[1][g2] << shg)),
-             c = fx_split((long long)((unsigned long long)g[2][g2] << shg));
+    const FxX a = fx_x(fx_shift(g[0][g2], shg)), b = fx_x(fx_shift(g[1][g2], shg)), c = fx_x(fx_shift(g[2][g2], shg));
     FAcc v0 = fx_acc(), v1 = fx_acc(), v2 = fx_acc();
     fx_mac(v0, a, D[0]);
     fx_mac(v0, b, D[1]);
@@ -456,17 +473,17 @@ __device__ __forceinline__ void fx_line_D(const long long* __restrict__ De, cons
     g[0][g2] = fx_res(v0);
     g[1][g2] = fx_res(v1);
     g[2][g2] = fx_res(v2);
-    sc[g2] = (sd == INT_MAX || og == 0) ? INT_MAX : sd + shg;
+    sc[g2] = (sd == INT_MAX || og == 0) ? INT_MAX : sd - kFxMacShift + shg;
     if constexpr (MASS) {
       const double mv = Me[pt];
       const int emm = fx_expo(mv);
       const int shu = kFxTop - fx_bits((unsigned long long)(u[g2] ^ (u[g2] >> 63)));
       FAcc w = fx_acc();
-      fx_mac(w, fx_split((long long)((unsigned long long)u[g2] << shu)), fx_split(fx_from_double(mv, emm)));
+      fx_mac(w, fx_x(fx_shift(u[g2], shu)), fx_c(fx_from_double(mv, emm)));
       u[g2] = fx_res(w);
       // u (B(x)B(x)B) sits S_B - S_D above the gradient; B^T u must come out
       // at the scale of d^T v2, so u is aligned as if S_B - S_D finer again
-      scm[g2] = (emm == 0 || u[g2] == 0) ? INT_MAX : 1079 - emm - 62 + shu + 2 * (S.B - S.D);
+      scm[g2] = (emm == 0 || u[g2] == 0) ? INT_MAX : 1079 - emm - kFxMacShift + shu + 2 * (S.B - S.D);
     }
   }
 }
@@ -504,8 +521,8 @@ __device__ __forceinline__ int fx_line_align(long long (*v)[Sz<P>::Q], long long
 #pragma unroll
   for (int g2 = 0; g2 < Q; ++g2) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c][g2] = (long long)((unsigned long long)v[c][g2] << sh);
-    if (MASS) u[g2] = (long long)((unsigned long long)u[g2] << sh);
+    for (int c = 0; c < 3; ++c) v[c][g2] = fx_shift(v[c][g2], sh);
+    if (MASS) u[g2] = fx_shift(u[g2], sh);
   }
   return smin + sh;
 }
@@ -554,7 +571,7 @@ __device__ __forceinline__ void fx_stage_y_t(const FxTab<P>& t, long long* A, in
   long long v[Q], y[N];
   unsigned long long acc = 0;
 #pragma unroll
-  for (int g = 0; g < Q; ++g) v[g] = (long long)((unsigned long long)a2[k * L::KS2 + g * Q + g0] << sh);
+  for (int g = 0; g < Q; ++g) v[g] = fx_rescale(a2[k * L::KS2 + g * Q + g0], sh);
   {
     const FxFoldQ<P> f = fx_fold_q<P>(v);
     fx_bwd<P, true, false>(t, f, f, y);
@@ -565,10 +582,10 @@ __device__ __forceinline__ void fx_stage_y_t(const FxTab<P>& t, long long* A, in
     fx_or(acc, y[j]);
   }
 #pragma unroll
-  for (int g = 0; g < Q; ++g) v[g] = (long long)((unsigned long long)a2[2 * L::C2 + k * L::KS2 + g * Q + g0] << sh);
+  for (int g = 0; g < Q; ++g) v[g] = fx_rescale(a2[2 * L::C2 + k * L::KS2 + g * Q + g0], sh);
   const FxFoldQ<P> f1 = fx_fold_q<P>(v);  // T2 (B^T)
 #pragma unroll
-  for (int g = 0; g < Q; ++g) v[g] = (long long)((unsigned long long)a2[L::C2 + k * L::KS2 + g * Q + g0] << sh);
+  for (int g = 0; g < Q; ++g) v[g] = fx_rescale(a2[L::C2 + k * L::KS2 + g * Q + g0], sh);
   const FxFoldQ<P> f2 = fx_fold_q<P>(v);  // T1 (d^T)
   fx_bwd<P, true, true>(t, f1, f2, y);
 #pragma unroll
@@ -591,10 +608,10 @@ __device__ __forceinline__ void fx_stage_x_t(const LorMesh& m, const FxTab<P>& t
   const long long* a1 = A + k * L::KS1 + j * L::LS;
   long long v[Q], yl[N];
 #pragma unroll
-  for (int g = 0; g < Q; ++g) v[g] = (long long)((unsigned long long)a1[L::C1 + g] << sh);  // U1 (B^T)
+  for (int g = 0; g < Q; ++g) v[g] = fx_rescale(a1[L::C1 + g], sh);  // U1 (B^T)
   const FxFoldQ<P> f1 = fx_fold_q<P>(v);
 #pragma unroll
-  for (int g = 0; g < Q; ++g) v[g] = (long long)((unsigned long long)a1[g] << sh);  // U0 (d^T)
+  for (int g = 0; g < Q; ++g) v[g] = fx_rescale(a1[g], sh);  // U0 (d^T)
   const FxFoldQ<P> f2 = fx_fold_q<P>(v);
   fx_bwd<P, true, true>(t, f1, f2, yl);
   if constexpr (GEN) {
@@ -631,7 +648,7 @@ __device__ __forceinline__ void fx_transposed(const LorMesh& m, const FxTab<P>& 
   constexpr int N = Z::N, Q = Z::Q, NN = N * N, NQ = N * Q;
   const int w = threadIdx.x;
   // line's real magnitude exponent: bits - (scale of T)
-  const int sT = sg + sline + S.B - 62;
+  const int sT = sg + sline + S.B - kFxMacShift;
   if (az && accT) atomicMax(&sl[lez * kFxSlots + 3], fx_bits(accT) - sT + kFxBias);
   __syncthreads();
   if (az && accT) {
@@ -662,8 +679,9 @@ __device__ __forceinline__ void fx_transposed(const LorMesh& m, const FxTab<P>& 
       const int* s = sl + le * kFxSlots;
       const int s3 = kFxTop - (s[3] - kFxBias);
       const int dyn4 = kFxTop - s[4];
-      const int s4 = s3 + S.B - 62 + dyn4;
-      fx_stage_x_t<P, GEN>(m, t, e_first + le, w % NN, A + (size_t)le * L::PER_ELEM, dyn4, s4 + S.D - 62, y);
+      const int s4 = s3 + S.B - kFxMacShift + dyn4;
+      fx_stage_x_t<P, GEN>(m, t, e_first + le, w % NN, A + (size_t)le * L::PER_ELEM, dyn4, s4 + S.D - kFxMacShift,
+                           y);
     }
   }
 }
@@ -728,10 +746,10 @@ __global__ void __launch_bounds__(kFxT<P>, kFxApplyBlocks<P>) k_apply_fx(LorMesh
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = kFxE<P>, N = Z::N;
   extern __shared__ __align__(16) unsigned char apply_smem[];
   __shared__ int sl[E * kFxSlots];
-  long long* sm = reinterpret_cast<long long*>(apply_smem);
-  const FxS S = fx_load_tables<P>(T, sm);
-  const FxTab<P> t = fx_tables<P>(sm);
-  long long* A = sm + Z::TABLES;
+  long long* tb = reinterpret_cast<long long*>(apply_smem);
+  const FxS S = fx_load_tables<P>(T, tb);
+  const FxTab<P> t = fx_tables<P>(tb);
+  long long* A = tb + Z::TABLES;
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
     for (int i = threadIdx.x; i < E * kFxSlots; i += blockDim.x) sl[i] = 0;
     __syncthreads();
@@ -806,10 +824,10 @@ __global__ void __launch_bounds__(kFxTB<P>, kFxBackwardBlocks<P>) k_apply_backwa
   constexpr int Q = Z::Q, Q2 = Q * Q, Q3 = Q2 * Q, E = kFxEB<P>, N = Z::N;
   extern __shared__ __align__(16) unsigned char apply_smem[];
   __shared__ int sl[E * kFxSlots], slx[E * kFxSlots];
-  long long* sm = reinterpret_cast<long long*>(apply_smem);
-  const FxS S = fx_load_tables<P>(T, sm);
-  const FxTab<P> t = fx_tables<P>(sm);
-  long long* A = sm + Z::TABLES;               // gy: element slots 0..E-1
+  long long* tb = reinterpret_cast<long long*>(apply_smem);
+  const FxS S = fx_load_tables<P>(T, tb);
+  const FxTab<P> t = fx_tables<P>(tb);
+  long long* A = tb + Z::TABLES;  // gy: element slots 0..E-1
   long long* AX = A + (size_t)E * L::PER_ELEM;  // x:  element slots E..2E-1
   for (int64_t e_first = (int64_t)blockIdx.x * E; e_first < m.nel; e_first += (int64_t)gridDim.x * E) {
     for (int i = threadIdx.x; i < E * kFxSlots; i += blockDim.x) {
@@ -866,10 +884,9 @@ __global__ void __launch_bounds__(kFxTB<P>, kFxBackwardBlocks<P>) k_apply_backwa
           FAcc d = fx_acc();
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            fx_mac(d, fx_split((long long)((unsigned long long)gxl[c][g2] << shx)),
-                   fx_split((long long)((unsigned long long)v[c][g2] << shv)));
+            fx_mac(d, fx_x(fx_shift(gxl[c][g2], shx)), fx_c(fx_shift(v[c][g2], shv)));
           const int pt = g01 + Q2 * g2;
-          const int scale = (sgx + shx) + (sg + ps[g2] + shv) - 62;
+          const int scale = (sgx + shx) + (sg + ps[g2] + shv) - kFxMacShift;
           const double tv = (ax && av && ps[g2] != INT_MAX) ? fx_to_double(fx_res(d), scale) : 0.0;
           gkappa[e * Q3 + pt] = tv / kappa[e * Q3 + pt];
         }

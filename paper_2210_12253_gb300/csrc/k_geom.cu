@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
       long long* D = reinterpret_cast<long long*>(Dq) + e * 6 * Q3 + pt;
 #pragma unroll
       for (int c = 0; c < 6; ++c) D[c * Q3] = fx_pack(fx_from_double(d[c], em));
-      lor_d_scales(Dq, m.nel * Q3)[e * Q3 + pt] = em == 0 ? INT_MAX : 1079 - em - 62;
+      lor_d_scales(Dq, m.nel * Q3)[e * Q3 + pt] = em == 0 ? INT_MAX : 1079 - em;
       kcopy[e * Q3 + pt] = k;
     }
     __syncthreads();
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   if (bad) atomicOr(status, bad);
 }
 
-// FP32 copy of D for the FP32-arithmetic operator: value = X 2^-(sd + 62).
+// FP32 copy of D for the FP32-arithmetic operator: value = X 2^-sd.
 __global__ void __launch_bounds__(256) k_d_to_f32(const double* __restrict__ Dq, int64_t nq, float* __restrict__ out,
                                                   int Q3) {
   const long long* D = reinterpret_cast<const long long*>(Dq);
@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(256) k_d_to_f32(const double* __restrict__ Dq,
     const int64_t e = i / (6 * Q3), pt = i % Q3;
     const int sc = sd[e * Q3 + pt];
     const Fx f = fx_unpack(D[i]);
-    const long long X = (long long)f.h * 2147483648ll + f.l;
-    out[i] = sc == INT_MAX ? 0.0f : (float)fx_to_double(X, sc + 62);
+    const long long X = (long long)f.h * 268435456ll + f.l;
+    out[i] = sc == INT_MAX ? 0.0f : (float)fx_to_double(X, sc);
   }
 }
 

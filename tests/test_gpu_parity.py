@@ -348,3 +348,64 @@ def test_fp64_path_at_extreme_mesh_scales(scale):
     ref = oracle.ho_apply(mesh, p, p + 2, prob.kappa, x)
     assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
     op.close()
+
+
+@pytest.mark.parametrize("p", [2, 5, 8])
+def test_fixed_point_operator_scale_invariance_and_zero(p):
+    """The FP64 operator and its backward carry one power-of-two scale per
+    element and stage: inputs scaled by 2^k (k = -600, 600) give each
+    element's contributions scaled by exactly 2^k, so gkappa (one value per
+    Gauss point) scales bit for bit and y, gx (sums of the elements'
+    contributions by FP64 atomics, whose order varies from run to run) to
+    within a few units of the last place; a zero input gives an exactly zero
+    output."""
+    dims = (2, 2, 2)
+    prob, mesh, op = setup(dims, p)
+    rng = np.random.default_rng(30 + p)
+    x, gy = rng.standard_normal(op.ndof), rng.standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    gx, gk = (a.cpu().numpy() for a in op.apply_backward(t(x), t(gy)))
+    def near(a, b):  # a few units of the last place of the largest entry
+        assert np.abs(a - b).max() <= 4e-16 * np.abs(b).max()
+
+    for k in (-600, 600):
+        s = 2.0 ** k
+        near(op.apply(t(x * s)).cpu().numpy() / s, y)
+        gxs, gks = (a.cpu().numpy() for a in op.apply_backward(t(x * s), t(gy)))
+        near(gxs, gx)
+        np.testing.assert_array_equal(gks, gk * s)
+        gxs, gks = (a.cpu().numpy() for a in op.apply_backward(t(x), t(gy * s)))
+        near(gxs / s, gx)
+        np.testing.assert_array_equal(gks, gk * s)
+    z = np.zeros(op.ndof)
+    assert not op.apply(t(z)).cpu().numpy().any()
+    gxz, gkz = (a.cpu().numpy() for a in op.apply_backward(t(z), t(z)))
+    assert not gxz.any() and not gkz.any()
+    op.close()
+
+
+@pytest.mark.parametrize("p", [3, 6])
+def test_fixed_point_operator_mixed_magnitudes(p):
+    """Nodal values spanning ten orders of magnitude inside each element (the
+    element's largest value sets its fixed-point scale) and a coefficient
+    spanning six: the apply and the backward stay within 1e-12 of the
+    oracle relative to the output maximum."""
+    from paper_2210_12253_gb300 import LOR
+    dims = (3, 2, 2)
+    prob = make_problem("t", *dims, p, seed=4, jitter=0.1, kappa="lognormal", rhs="normal")
+    kappa = prob.kappa * np.exp(np.random.default_rng(5).uniform(-7, 7, prob.kappa.shape))
+    mesh = oracle.Mesh(*dims, prob.vertices)
+    op = LOR(p, *dims, t(prob.vertices))
+    op.set_coefficient(t(kappa).reshape(-1), check=True)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(op.ndof) * 10.0 ** rng.uniform(-10, 0, op.ndof)
+    gy = rng.standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ref = oracle.ho_apply(mesh, p, p + 2, kappa, x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    gx, gk = op.apply_backward(t(x), t(gy))
+    rgx, rgk = oracle.ho_apply_backward(mesh, p, p + 2, kappa, x, gy)
+    assert np.abs(gx.cpu().numpy() - rgx).max() <= 1e-12 * np.abs(rgx).max()
+    gk = gk.cpu().numpy().reshape(rgk.shape)
+    assert np.abs(gk - rgk).max() <= 1e-12 * np.abs(rgk).max()
+    op.close()
