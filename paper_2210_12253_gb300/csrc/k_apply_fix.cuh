@@ -46,16 +46,18 @@ namespace {
 // z line) and the CTAs per SM the register budget is sized for.  The kernels
 // are bound by issue latency: two CTAs per SM (about 128 registers a thread,
 // some spilled at high degree) beat one CTA with all state in registers by
-// 1.3-1.7x for the apply; the backward holds two fields, and from p = 7 its
-// spills at that budget cost more than the second CTA gains.
+// 1.3-1.7x for the apply; the backward holds two fields, and from p = 8 its
+// spills at that budget cost more than the second CTA gains (at p = 4..7 one
+// CTA per SM is 1.3-2.2x slower).
 template <int P>
 constexpr int kFxApplyBlocks = 2;
 template <int P>
-constexpr int kFxBackwardBlocks = P >= 7 ? 1 : 2;
+constexpr int kFxBackwardBlocks = P >= 8 ? 1 : 2;
 template <int P>
 constexpr int kFxE = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 4 : P == 7 ? 3 : 2;
 template <int P>
-constexpr int kFxEB = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P <= 5 ? 5 : P <= 8 ? 3 : P == 9 ? 2 : 1;
+constexpr int kFxEB = P == 1 ? 28 : P == 2 ? 16 : P == 3 ? 10 : P == 4 ? 7 : P == 5 ? 5 : P == 6 ? 3 : P == 7 ? 2
+                    : P == 8 ? 3 : P == 9 ? 2 : 1;
 template <int P>
 constexpr int kFxT = ((kFxE<P> * (P + 2) * (P + 2) + 31) / 32) * 32;
 template <int P>
