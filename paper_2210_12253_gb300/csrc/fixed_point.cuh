@@ -61,6 +61,52 @@ __device__ __forceinline__ double fx_to_double(long long X, int scale) {
   return X == 0 ? 0.0 : __longlong_as_double((long long)(bits | (sgn << 63)));
 }
 
+// A multiply-add's operands (data X and coefficient C: tables, D, M), both
+// |.| <= 2^58, split as X = Xh 2^28 + Xl (0 <= Xl < 2^28, |Xh| < 2^30):
+//   X C / 2^56 = Xh Ch + (Xh Cl + Xl Ch) / 2^28 + Xl Cl / 2^56,
+// hi += Xh Ch and mid += Xh Cl + Xl Ch by 32 x 32 -> 64 bit multiply-adds
+// (mad.wide.s32); the dropped Xl Cl / 2^56 is below one unit.  With at most
+// 14 products (|Xh Ch| < 2^59, |Xh Cl + Xl Ch| < 2^58.6) neither accumulator
+// overflows, and the result hi + mid / 2^28, rounded once, reaches up to
+// 2^62: a stage's largest output keeps 58-61 bits.
+using FxX = Fx;
+using FxC = Fx;
+constexpr int kFxMacShift = 56;  // a multiply-add's product is X C / 2^56
+__device__ __forceinline__ FxX fx_x(long long X) { return fx_split(X); }
+__device__ __forceinline__ FxC fx_c(long long C) { return fx_split(C); }
+__device__ __forceinline__ FxC fx_c_packed(long long c) { return fx_unpack(c); }
+
+struct FAcc {
+  long long hi, mid;
+};
+__device__ __forceinline__ FAcc fx_acc() { return FAcc{0ll, 1ll << 27}; }  // mid's bias rounds the final shift
+__device__ __forceinline__ void fx_mac(FAcc& a, FxX x, FxC c) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.hi) : "r"(x.h), "r"(c.h));
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.h), "r"(c.l));
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a.mid) : "r"(x.l), "r"(c.h));
+}
+__device__ __forceinline__ long long fx_res(const FAcc& a) { return a.hi + (a.mid >> 28); }
+
+// X 2^sh for a signed shift (left: sh <= 57 keeps |X| <= 2^57 by
+// construction; right: rounded to nearest, 0 beyond 62 places)
+__device__ __forceinline__ long long fx_shift(long long X, int sh) {
+  if (sh >= 0) return (long long)((unsigned long long)X << sh);
+  const int r = -sh;
+  return r > 62 ? 0ll : (X + (1ll << (r - 1))) >> r;
+}
+// the same without a branch, for the renormalising loads (-6 <= sh <= 57;
+// a right shift truncates: under a unit of the 57-bit result)
+__device__ __forceinline__ long long fx_rescale(long long X, int sh) {
+  const int l = sh > 0 ? sh : 0, r = sh > 0 ? 0 : -sh;
+  return (long long)((unsigned long long)X << l) >> r;
+}
+
+// bit length of the largest |X| among the values OR-ed into acc as X ^ (X >> 63)
+__device__ __forceinline__ void fx_or(unsigned long long& acc, long long X) {
+  acc |= (unsigned long long)(X ^ (X >> 63));
+}
+__device__ __forceinline__ int fx_bits(unsigned long long acc) { return 64 - __clzll((long long)acc); }
+
 // The scale offsets of D's points, stored after its 6 nq packed entries.
 __host__ __device__ __forceinline__ int* lor_d_scales(double* Dq, int64_t nq) {
   return reinterpret_cast<int*>(Dq + 6 * nq);

@@ -29,10 +29,16 @@
 // detJ_e = sqrt(det M).  M's diagonal |c_d|^2 depends on the two coordinates
 // its column is tabulated on, so it is tabulated per element too; per Gauss
 // point remain the three off-diagonal products, the cofactors, det M and one
-// reciprocal square root (fewer FP64 instructions than the adjugate rows of
-// J_e, their products and a determinant with its reciprocal).
+// reciprocal square root.  These products run in 64-bit fixed point on the
+// integer pipe (fixed_point.cuh): the column tables are converted once per
+// element, one scale per table, and each of M, adj(M) and det M is
+// renormalised per Gauss point; only 1/sqrt(det M) (range-reduced, as in the
+// setup) and the kappa_s averages stay FP64.  The 48 metric values and 8 mass
+// weights of a sub-hex then enter the block algebra as integers on one
+// scale.
 #pragma once
 
+#include "fixed_point.cuh"
 #include "lor_internal.cuh"
 
 namespace {
@@ -183,25 +189,12 @@ __device__ __forceinline__ void hadamard_axis(VT* K) {
     for (int j = i; j < 8; ++j) K[sym(i, j)] = out[sym(i, j)];
 }
 
-// The FP64 sub-hex block from its metric G[ab][g] (F_ab and 1/64 folded in)
-// and mass weights W[g]: Walsh transforms, modal block, Hadamard sandwich, in
+// The FP64 sub-hex block from its metric X[ab][g] (F_ab and 1/64 folded in)
+// and mass weights Xw[g] in fixed point, all below 2^56 at one scale (real
+// value = X 2^-scale): Walsh transforms, modal block, Hadamard sandwich, in
 // the fixed point described above; K receives the 36 nodal entries in FP64.
 template <bool MASS>
-__device__ __forceinline__ void fix_block(const double (&G)[6][8], const double* W, double* K) {
-  unsigned hmax = 0;
-#pragma unroll
-  for (int ab = 0; ab < 6; ++ab)
-#pragma unroll
-    for (int g = 0; g < 8; ++g) hmax = max(hmax, (unsigned)__double2hiint(G[ab][g]) & 0x7FF00000u);
-  if constexpr (MASS)
-#pragma unroll
-    for (int g = 0; g < 8; ++g) hmax = max(hmax, (unsigned)__double2hiint(W[g]) & 0x7FF00000u);
-  const int emax = (int)(hmax >> 20);
-  long long X[6][8];
-#pragma unroll
-  for (int ab = 0; ab < 6; ++ab)
-#pragma unroll
-    for (int g = 0; g < 8; ++g) X[ab][g] = to_fix(G[ab][g], emax);
+__device__ __forceinline__ void fix_block_x(long long (&X)[6][8], long long* Xw, int scale_in, double* K) {
   walsh8<long long, 0>(X[0]);
   walsh8<long long, 0>(X[1]);
   walsh8<long long, 0>(X[2]);
@@ -226,9 +219,6 @@ __device__ __forceinline__ void fix_block(const double (&G)[6][8], const double*
       Kf[sym(mm, nn)] = k > 0 ? fix_mul(acc, q63(k)) : acc;
     }
   if constexpr (MASS) {
-    long long Xw[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) Xw[g] = to_fix(W[g], emax);
     walsh8<long long, 0>(Xw);
 #pragma unroll
     for (int mm = 0; mm < 8; ++mm)
@@ -259,11 +249,34 @@ __device__ __forceinline__ void fix_block(const double (&G)[6][8], const double*
   hadamard_axis<long long, 0>(Kf);
   hadamard_axis<long long, 1>(Kf);
   hadamard_axis<long long, 2>(Kf);
-  const int scale = 1078 - emax - sft;
+  const int scale = scale_in - sft;
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = i; j < 8; ++j) K[sym(i, j)] = from_fix(Kf[sym(i, j)], scale);
+}
+// The same from the metric in FP64: converted with the sub-hex's largest
+// exponent (X < 2^56 at scale 1078 - emax).
+template <bool MASS>
+__device__ __forceinline__ void fix_block(const double (&G)[6][8], const double* W, double* K) {
+  unsigned hmax = 0;
+#pragma unroll
+  for (int ab = 0; ab < 6; ++ab)
+#pragma unroll
+    for (int g = 0; g < 8; ++g) hmax = max(hmax, (unsigned)__double2hiint(G[ab][g]) & 0x7FF00000u);
+  if constexpr (MASS)
+#pragma unroll
+    for (int g = 0; g < 8; ++g) hmax = max(hmax, (unsigned)__double2hiint(W[g]) & 0x7FF00000u);
+  const int emax = (int)(hmax >> 20);
+  long long X[6][8], Xw[MASS ? 8 : 1];
+#pragma unroll
+  for (int ab = 0; ab < 6; ++ab)
+#pragma unroll
+    for (int g = 0; g < 8; ++g) X[ab][g] = to_fix(G[ab][g], emax);
+  if constexpr (MASS)
+#pragma unroll
+    for (int g = 0; g < 8; ++g) Xw[g] = to_fix(W[g], emax);
+  fix_block_x<MASS>(X, Xw, 1078 - emax, K);
 }
 
 template <int P>
@@ -272,16 +285,15 @@ template <int P>
 constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
                                             : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
 
-// FP64: 640 threads' worth of CTAs per SM (10 CTAs of 64 threads at p = 4,
-// about 96 registers per thread, the rest of the block's state spilled to
-// local memory): the kernel is latency-bound, and the extra warps hide the
-// integer block algebra's and the conversions' latencies better than the
-// spills cost.  Measured at p = 4 (event-timed): 0.300 ms with 128 registers
-// (8 CTAs, no spills), 0.278 ms here; 12 CTAs (80 registers) the same time
-// with 2.6x the spill traffic to DRAM (126 against 48 MB per launch); 16 CTAs
-// (64 registers) 0.302 ms.
+// FP64: 512 threads' worth of CTAs per SM (8 CTAs of 64 threads at p = 4,
+// 128 registers per thread, the rest of the block's state spilled to local
+// memory): the kernel is latency-bound.  Measured at p = 4 with the metric's
+// products in fixed point (event-timed, c2; in brackets GDOF/s at ~20M DOFs):
+// 512 threads 0.278 ms (1.21), 640 threads 0.289 ms (1.15), 384 threads
+// 0.295 ms (1.10).  With the metric in FP64 (the FP64 pipe then the bound)
+// 640 threads had been best: 0.278 ms, against 0.300 ms at 128 registers.
 template <int P, typename VT>
-constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (640 / kAsmThreads<P> > 1 ? 640 / kAsmThreads<P> : 1) : 1;
+constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (512 / kAsmThreads<P> > 1 ? 512 / kAsmThreads<P> : 1) : 1;
 
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
@@ -296,7 +308,11 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   constexpr bool F32 = sizeof(VT) == sizeof(float);
   __shared__ double Ehalf[EPB][36];
   __shared__ double tab[EPB][TAB];
-  __shared__ double mdiag[F32 ? 1 : EPB][F32 ? 1 : 3 * L * L];  // |c_d|^2 on each column's table (FP64)
+  // FP64 mode: the Jacobian columns in fixed point (packed words, one scale
+  // per column table: 1079 - cexp) and |c_d|^2 formed from them
+  __shared__ long long tabx[F32 ? 1 : EPB][F32 ? 1 : TAB];
+  __shared__ long long mdx[F32 ? 1 : EPB][F32 ? 1 : 3 * L * L];
+  __shared__ int cexp[F32 ? 1 : EPB][3];
   __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
   __shared__ double sl0[L], sl1[L];
   if (threadIdx.x < L) {
@@ -316,10 +332,23 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
     __syncthreads();
   } else {
+    constexpr int CT = L * L * 3;  // one column table
+    for (int i = threadIdx.x; i < EPB * 3; i += blockDim.x) cexp[i / 3][i % 3] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x)
+      atomicMax(&cexp[i / TAB][(i % TAB) / CT], fx_expo(tab[i / TAB][i % TAB]));
+    __syncthreads();
+    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x)
+      tabx[i / TAB][i % TAB] = fx_pack(fx_from_double(tab[i / TAB][i % TAB], cexp[i / TAB][(i % TAB) / CT]));
+    __syncthreads();
+    // |c_d|^2: at most 3 2^58 before the shift, so at most 2^58 stored (scale 2 s_d - 58)
     constexpr int ND = 3 * L * L;
     for (int i = threadIdx.x; i < EPB * ND; i += blockDim.x) {
-      const double* cc = &tab[i / ND][3 * (i % ND)];
-      mdiag[i / ND][i % ND] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+      const long long* cc = &tabx[i / ND][3 * (i % ND)];
+      FAcc acc = fx_acc();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fx_mac(acc, fx_unpack(cc[k]), fx_unpack(cc[k]));
+      mdx[i / ND][i % ND] = fx_pack(fx_res(acc) >> 2);
     }
     __syncthreads();
   }
@@ -346,49 +375,171 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     // G_sub^{ab}(g) = F_ab adj(M)_ab / det_e, F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64
     // (the 1/64 of the modal-to-nodal transform folded in); in FP32 from the
     // adjugate rows A_a of J_e (A_a . A_b = adj(M)_ab).
-    VT G[6][8];
-    VT W[MASS ? 8 : 1];  // reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
+    VT G[F32 ? 6 : 1][F32 ? 8 : 1];  // FP32: the metric (pair order 00, 01, 02, 11, 12, 22)
+    VT W[(MASS && F32) ? 8 : 1];      // FP32 reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
     const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
-    double FF[6];  // F_ab in pair order (00, 01, 02, 11, 12, 22) (FP64 only)
+    // FP64: the metric's products in fixed point (see fixed_point.cuh) from
+    // the columns' fixed-point tables, each stage renormalised per Gauss point
+    // (one shift for the six M entries, one for the six cofactors, one for
+    // det M, so every cofactor's and det's terms share a scale); 1/sqrt(det M)
+    // by the range-reduced FP64 reciprocal square root; the sub-hex's 48
+    // metric values (and 8 mass weights) aligned to one scale for the block.
+    long long X[F32 ? 1 : 6][F32 ? 1 : 8];
+    long long Xw[(MASS && !F32) ? 8 : 1];
+    int st = 0;
     if constexpr (!F32) {
       const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
       const double k64 = ks * (1.0 / 64.0);
-      FF[0] = k64 * rb * rc * T.sub_rinv[a];
-      FF[1] = k64 * rc;
-      FF[2] = k64 * rb;
-      FF[3] = k64 * ra * rc * T.sub_rinv[b];
-      FF[4] = k64 * ra;
-      FF[5] = k64 * ra * rb * T.sub_rinv[c];
-      const double bR = MASS ? bs * (1.0 / 64.0) * ra * rb * rc : 0.0;
-      const double* t0 = tab[le];
-      const double* t1 = tab[le] + L * L * 3;
-      const double* t2 = tab[le] + 2 * L * L * 3;
-      const double* q0 = mdiag[le];
-      const double* q1 = mdiag[le] + L * L;
-      const double* q2 = mdiag[le] + 2 * L * L;
+      const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
+                            k64 * ra * rc * T.sub_rinv[b], k64 * ra, k64 * ra * rb * T.sub_rinv[c]};
+      Fx FFx[6];
+      int sF[6];
+#pragma unroll
+      for (int ab = 0; ab < 6; ++ab) {
+        const int ef = fx_expo(FF[ab]);
+        FFx[ab] = fx_split(fx_from_double(FF[ab], ef));
+        sF[ab] = 1079 - ef;
+      }
+      Fx bRx = Fx{0, 0};
+      int sbR = 0;
+      if constexpr (MASS) {
+        const double bR = bs * (1.0 / 64.0) * ra * rb * rc;
+        const int eb = fx_expo(bR);
+        bRx = fx_split(fx_from_double(bR, eb));
+        sbR = 1079 - eb;
+      }
+      constexpr int CT = L * L * 3;
+      const int s0 = 1079 - cexp[le][0], s1 = 1079 - cexp[le][1], s2 = 1079 - cexp[le][2];
+      // static scales: M_ab at s_a + s_b - 58 (+ dM); a cofactor's two products
+      // at the sum of two M scales less 56, so adj(M)_ab at sAb[ab] + sdA
+      // (sAb: 2S - 2 s_a on the diagonal, S + s_c off it, S = s0 + s1 + s2);
+      // det M's three products at 2S - 58 + dM + sdA - 56
+      const int S3 = s0 + s1 + s2;
+      const int sAb[6] = {2 * S3 - 2 * s0, S3 + s2, S3 + s1, 2 * S3 - 2 * s1, S3 + s0, 2 * S3 - 2 * s2};
+      const long long* x0 = tabx[le];
+      const long long* x1 = tabx[le] + CT;
+      const long long* x2 = tabx[le] + 2 * CT;
+      const long long* d0 = mdx[le];
+      const long long* d1 = mdx[le] + L * L;
+      const long long* d2 = mdx[le] + 2 * L * L;
+      int sG[8];
+      int sW[MASS ? 8 : 1];
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
-        const double* c0 = t0 + 3 * (u1 + L * u2);
-        const double* c1 = t1 + 3 * (u0 + L * u2);
-        const double* c2 = t2 + 3 * (u0 + L * u1);
-        const double M00 = q0[u1 + L * u2], M11 = q1[u0 + L * u2], M22 = q2[u0 + L * u1];
-        const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
-        const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
-        const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
-        const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
-        const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
-        const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
-        const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
-        const double r = lor_rsqrt(detM);  // 1 / det J_e
-        if constexpr (MASS) W[g] = (VT)(bR * (detM * r));
-        G[0][g] = (VT)((FF[0] * r) * A00);
-        G[1][g] = (VT)((FF[1] * r) * A01);
-        G[2][g] = (VT)((FF[2] * r) * A02);
-        G[3][g] = (VT)((FF[3] * r) * A11);
-        G[4][g] = (VT)((FF[4] * r) * A12);
-        G[5][g] = (VT)((FF[5] * r) * A22);
+        const long long* c0 = x0 + 3 * (u1 + L * u2);
+        const long long* c1 = x1 + 3 * (u0 + L * u2);
+        const long long* c2 = x2 + 3 * (u0 + L * u1);
+        Fx A0[3], A1[3], A2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          A0[k] = fx_unpack(c0[k]);
+          A1[k] = fx_unpack(c1[k]);
+          A2[k] = fx_unpack(c2[k]);
+        }
+        // M = J^T J: six entries, then one shift that brings the largest to 58 bits
+        long long M[6];  // 00, 01, 02, 11, 12, 22
+        {
+          FAcc t01 = fx_acc(), t02 = fx_acc(), t12 = fx_acc();
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            fx_mac(t01, A0[k], A1[k]);
+            fx_mac(t02, A0[k], A2[k]);
+            fx_mac(t12, A1[k], A2[k]);
+          }
+          M[0] = fx_unpack(d0[u1 + L * u2]).h * (1ll << 28) + fx_unpack(d0[u1 + L * u2]).l;
+          M[1] = fx_res(t01) >> 2;
+          M[2] = fx_res(t02) >> 2;
+          M[3] = fx_unpack(d1[u0 + L * u2]).h * (1ll << 28) + fx_unpack(d1[u0 + L * u2]).l;
+          M[4] = fx_res(t12) >> 2;
+          M[5] = fx_unpack(d2[u0 + L * u1]).h * (1ll << 28) + fx_unpack(d2[u0 + L * u1]).l;
+        }
+        unsigned long long om = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fx_or(om, M[k]);
+        const int dM = 58 - fx_bits(om);  // M_ab at s_a + s_b - 58 + dM
+        Fx Mx[6], nMx[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const long long v = fx_shift(M[k], dM);
+          Mx[k] = fx_split(v);
+          nMx[k] = fx_split(-v);
+        }
+        // adj(M): two products each (at most 2^61), one shift to 58 bits
+        long long Ad[6];
+        {
+          FAcc t;
+          t = fx_acc(); fx_mac(t, Mx[3], Mx[5]); fx_mac(t, nMx[4], Mx[4]); Ad[0] = fx_res(t);  // M11 M22 - M12^2
+          t = fx_acc(); fx_mac(t, Mx[2], Mx[4]); fx_mac(t, nMx[1], Mx[5]); Ad[1] = fx_res(t);  // M02 M12 - M01 M22
+          t = fx_acc(); fx_mac(t, Mx[1], Mx[4]); fx_mac(t, nMx[2], Mx[3]); Ad[2] = fx_res(t);  // M01 M12 - M02 M11
+          t = fx_acc(); fx_mac(t, Mx[0], Mx[5]); fx_mac(t, nMx[2], Mx[2]); Ad[3] = fx_res(t);  // M00 M22 - M02^2
+          t = fx_acc(); fx_mac(t, Mx[1], Mx[2]); fx_mac(t, nMx[0], Mx[4]); Ad[4] = fx_res(t);  // M01 M02 - M00 M12
+          t = fx_acc(); fx_mac(t, Mx[0], Mx[3]); fx_mac(t, nMx[1], Mx[1]); Ad[5] = fx_res(t);  // M00 M11 - M01^2
+        }
+        unsigned long long oa = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fx_or(oa, Ad[k]);
+        const int dA = 58 - fx_bits(oa);
+        Fx Ax[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Ax[k] = fx_split(fx_shift(Ad[k], dA));
+        // det M = M00 A00 + M01 A01 + M02 A02 (at most 3 2^60), to 58 bits
+        long long det;
+        {
+          FAcc t = fx_acc();
+          fx_mac(t, Mx[0], Ax[0]);
+          fx_mac(t, Mx[1], Ax[1]);
+          fx_mac(t, Mx[2], Ax[2]);
+          det = fx_res(t);
+        }
+        const int sdA = 2 * dM - 116 - kFxMacShift + dA;        // adj(M)_ab at sAb[ab] + sdA
+        const int sdet = 2 * S3 - 58 + dM + sdA - kFxMacShift;  // det M at sdet
+        const double r = lor_rsqrt(fx_to_double(det, sdet));   // 1 / det J_e
+        const int er = fx_expo(r);
+        const Fx rx = fx_split(fx_from_double(r, er));
+        const int sr = 1079 - er;
+        // G_ab = (F_ab r) adj(M)_ab: (F_ab r) at most 2^58, G at most 2^60
+#pragma unroll
+        for (int ab = 0; ab < 6; ++ab) {
+          FAcc f = fx_acc();
+          fx_mac(f, FFx[ab], rx);
+          FAcc q = fx_acc();
+          fx_mac(q, fx_split(fx_res(f)), Ax[ab]);
+          X[ab][g] = fx_res(q);
+        }
+        sG[g] = sr - kFxMacShift + sdA - kFxMacShift;  // G_ab at sF[ab] + sAb[ab] + sG[g]
+        if constexpr (MASS) {
+          // W = beta_s r_a r_b r_c / 64 detJ_e = bR det M r
+          const int ed = 58 - fx_bits((unsigned long long)(det ^ (det >> 63)));
+          FAcc f = fx_acc();
+          fx_mac(f, fx_split(fx_shift(det, ed)), rx);
+          const long long dr = fx_res(f);  // at most 2^59
+          FAcc q = fx_acc();
+          fx_mac(q, bRx, fx_split(dr >> 1));
+          Xw[g] = fx_res(q);
+          sW[g] = sbR + (sdet + ed + sr - kFxMacShift - 1) - kFxMacShift;
+        }
       }
+      // one scale for the sub-hex: its largest value below 2^56
+      int mmax = -(1 << 30);
+#pragma unroll
+      for (int ab = 0; ab < 6; ++ab)
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+          if (X[ab][g] != 0)
+            mmax = max(mmax, fx_bits((unsigned long long)(X[ab][g] ^ (X[ab][g] >> 63))) - (sF[ab] + sAb[ab] + sG[g]));
+      if constexpr (MASS)
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+          if (Xw[g] != 0) mmax = max(mmax, fx_bits((unsigned long long)(Xw[g] ^ (Xw[g] >> 63))) - sW[g]);
+      st = 56 - mmax;
+#pragma unroll
+      for (int ab = 0; ab < 6; ++ab)
+#pragma unroll
+        for (int g = 0; g < 8; ++g) X[ab][g] = fx_shift(X[ab][g], min(st - (sF[ab] + sAb[ab] + sG[g]), 63));
+      if constexpr (MASS)
+#pragma unroll
+        for (int g = 0; g < 8; ++g) Xw[g] = fx_shift(Xw[g], min(st - sW[g], 63));
     } else {
       // FP64: the first adjugate row and the determinant; FP32: the rest.
       const float ra = (float)T.sub_r[a], rb = (float)T.sub_r[b], rc = (float)T.sub_r[c];
@@ -471,8 +622,8 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
       hadamard_axis<VT, 1>(K);
       hadamard_axis<VT, 2>(K);
     } else {
-      // FP64: the same linear steps in 64-bit fixed point (see fix_block)
-      fix_block<MASS>(G, W, K);
+      // FP64: the same linear steps in 64-bit fixed point (see fix_block_x)
+      fix_block_x<MASS>(X, Xw, st, K);
     }
 
     // Scatter into the CSR values (closed-form positions on the structured
