@@ -293,7 +293,11 @@ constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P 
 // 0.295 ms (1.10).  With the metric in FP64 (the FP64 pipe then the bound)
 // 640 threads had been best: 0.278 ms, against 0.300 ms at 128 registers.
 template <int P, typename VT>
-constexpr int kAsmMinBlocks = sizeof(VT) == sizeof(double) ? (512 / kAsmThreads<P> > 1 ? 512 / kAsmThreads<P> : 1) : 1;
+constexpr int kAsmThreadBudget = P >= 2 ? 512 : 640;  // p = 1 keeps the FP64 metric (see FXG)
+template <int P, typename VT>
+constexpr int kAsmMinBlocks =
+    sizeof(VT) == sizeof(double) ? (kAsmThreadBudget<P, VT> / kAsmThreads<P> > 1 ? kAsmThreadBudget<P, VT> / kAsmThreads<P> : 1)
+                                 : 1;
 
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
@@ -306,13 +310,18 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kElemsPerCta<P>;
   constexpr int TAB = 3 * L * L * 3;  // three Jacobian-column tables per element
   constexpr bool F32 = sizeof(VT) == sizeof(float);
+  // FP64: the metric's products in fixed point from p = 2 (at p = 1 an element
+  // has one sub-hex, and converting its column tables cost more than the
+  // products saved: 0.24 against 0.38 GDOF/s at 4M DOFs)
+  constexpr bool FXG = !F32 && P >= 2;
   __shared__ double Ehalf[EPB][36];
   __shared__ double tab[EPB][TAB];
   // FP64 mode: the Jacobian columns in fixed point (packed words, one scale
   // per column table: 1079 - cexp) and |c_d|^2 formed from them
-  __shared__ long long tabx[F32 ? 1 : EPB][F32 ? 1 : TAB];
-  __shared__ long long mdx[F32 ? 1 : EPB][F32 ? 1 : 3 * L * L];
-  __shared__ int cexp[F32 ? 1 : EPB][3];
+  __shared__ long long tabx[FXG ? EPB : 1][FXG ? TAB : 1];
+  __shared__ long long mdx[FXG ? EPB : 1][FXG ? 3 * L * L : 1];
+  __shared__ int cexp[FXG ? EPB : 1][3];
+  __shared__ double mdiag[(!F32 && !FXG) ? EPB : 1][(!F32 && !FXG) ? 3 * L * L : 1];  // |c_d|^2 in FP64
   __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
   __shared__ double sl0[L], sl1[L];
   if (threadIdx.x < L) {
@@ -330,6 +339,13 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   }
   if constexpr (F32) {
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
+    __syncthreads();
+  } else if constexpr (!FXG) {
+    constexpr int ND = 3 * L * L;
+    for (int i = threadIdx.x; i < EPB * ND; i += blockDim.x) {
+      const double* cc = &tab[i / ND][3 * (i % ND)];
+      mdiag[i / ND][i % ND] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+    }
     __syncthreads();
   } else {
     constexpr int CT = L * L * 3;  // one column table
@@ -384,10 +400,12 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     // det M, so every cofactor's and det's terms share a scale); 1/sqrt(det M)
     // by the range-reduced FP64 reciprocal square root; the sub-hex's 48
     // metric values (and 8 mass weights) aligned to one scale for the block.
-    long long X[F32 ? 1 : 6][F32 ? 1 : 8];
-    long long Xw[(MASS && !F32) ? 8 : 1];
+    long long X[FXG ? 6 : 1][FXG ? 8 : 1];
+    long long Xw[(MASS && FXG) ? 8 : 1];
     int st = 0;
-    if constexpr (!F32) {
+    double Gd[(!F32 && !FXG) ? 6 : 1][(!F32 && !FXG) ? 8 : 1];  // the metric in FP64 (p = 1)
+    double Wd[(MASS && !F32 && !FXG) ? 8 : 1];
+    if constexpr (FXG) {
       const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
       const double k64 = ks * (1.0 / 64.0);
       const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
@@ -540,6 +558,46 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
       if constexpr (MASS)
 #pragma unroll
         for (int g = 0; g < 8; ++g) Xw[g] = fx_shift(Xw[g], min(st - sW[g], 63));
+    } else if constexpr (!F32) {
+      const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
+      const double k64 = ks * (1.0 / 64.0);
+      double FF[6];
+      FF[0] = k64 * rb * rc * T.sub_rinv[a];
+      FF[1] = k64 * rc;
+      FF[2] = k64 * rb;
+      FF[3] = k64 * ra * rc * T.sub_rinv[b];
+      FF[4] = k64 * ra;
+      FF[5] = k64 * ra * rb * T.sub_rinv[c];
+      const double bR = MASS ? bs * (1.0 / 64.0) * ra * rb * rc : 0.0;
+      const double* t0 = tab[le];
+      const double* t1 = tab[le] + L * L * 3;
+      const double* t2 = tab[le] + 2 * L * L * 3;
+      const double* q0 = mdiag[le];
+      const double* q1 = mdiag[le] + L * L;
+      const double* q2 = mdiag[le] + 2 * L * L;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
+        const double* c0 = t0 + 3 * (u1 + L * u2);
+        const double* c1 = t1 + 3 * (u0 + L * u2);
+        const double* c2 = t2 + 3 * (u0 + L * u1);
+        const double M00 = q0[u1 + L * u2], M11 = q1[u0 + L * u2], M22 = q2[u0 + L * u1];
+        const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
+        const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
+        const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
+        const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
+        const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
+        const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
+        const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
+        const double r = lor_rsqrt(detM);  // 1 / det J_e
+        if constexpr (MASS) Wd[g] = bR * (detM * r);
+        Gd[0][g] = ((FF[0] * r) * A00);
+        Gd[1][g] = ((FF[1] * r) * A01);
+        Gd[2][g] = ((FF[2] * r) * A02);
+        Gd[3][g] = ((FF[3] * r) * A11);
+        Gd[4][g] = ((FF[4] * r) * A12);
+        Gd[5][g] = ((FF[5] * r) * A22);
+      }
     } else {
       // FP64: the first adjugate row and the determinant; FP32: the rest.
       const float ra = (float)T.sub_r[a], rb = (float)T.sub_r[b], rc = (float)T.sub_r[c];
@@ -623,7 +681,8 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
       hadamard_axis<VT, 2>(K);
     } else {
       // FP64: the same linear steps in 64-bit fixed point (see fix_block_x)
-      fix_block_x<MASS>(X, Xw, st, K);
+      if constexpr (FXG) fix_block_x<MASS>(X, Xw, st, K);
+      else fix_block<MASS>(Gd, Wd, K);
     }
 
     // Scatter into the CSR values (closed-form positions on the structured
