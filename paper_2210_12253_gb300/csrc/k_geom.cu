@@ -4,11 +4,12 @@
 // the load vector.
 //
 // GB300 notes: FP64 runs at about 2 DFMA/clk/SM on this part (1/64 of FP32),
-// so these kernels are bound by FP64 issue, not by HBM.  The FP64 work per
-// point is kept minimal: a trilinear map has dx/dxi_0 independent of xi_0 (and
-// likewise for the other columns), so each Jacobian column is tabulated once
-// per element on a q x q grid in shared memory, and so are the squared column
-// norms; per point the metric follows from the rest of M = J^T J.
+// so these kernels would be bound by FP64 issue, not by HBM.  A trilinear map
+// has dx/dxi_0 independent of xi_0 (and likewise for the other columns), so
+// each Jacobian column is tabulated once per element on a q x q grid in shared
+// memory, and so are the squared column norms; per point the metric follows
+// from the rest of M = J^T J.  The setup forms those products in 64-bit fixed
+// point on the integer pipe (fixed_point.cuh), as the LOR assembly does.
 #include "fixed_point.cuh"
 #include "lor_internal.cuh"
 
@@ -18,22 +19,24 @@ namespace {
 // M's diagonal |c_d|^2 depends only on the two coordinates its column is
 // tabulated on, so it is tabulated per element next to the columns; per
 // Gauss point remain the three off-diagonal products, the six cofactors,
-// det M and one reciprocal square root (fewer FP64 instructions than the
-// adjugate rows of J, its determinant and reciprocal, and six dot products).
-// det M > 0 is checked here; the sign of det J was checked at context
-// creation (the mesh does not change afterwards).  D is stored in the
-// fixed-point form the FP64 operator multiplies it in (fixed_point.cuh): the
-// six entries of a point at the point's largest exponent, converted here by
-// integer operations while the FP64 pipe bounds this kernel, instead of at
-// every application.
+// det M and one reciprocal square root.  The products run in 64-bit fixed
+// point: the column tables converted once per element (one scale per table),
+// M, adj(M) and det M renormalised per point; 1/sqrt(det M) (range-reduced)
+// and kappa w times it in FP64; D_ab = (kappa w / sqrt(det M)) adj(M)_ab in
+// fixed point, stored in the form the FP64 operator multiplies it in (the
+// point's six entries at its largest, fixed_point.cuh).  det M > 0 is checked
+// here; the sign of det J was checked at context creation (the mesh does not
+// change afterwards).
 template <int P>
 __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
                                                double* __restrict__ kcopy, double* __restrict__ Dq,
                                                int* __restrict__ status) {
-  constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q;
+  constexpr int Q = P + 2, Q2 = Q * Q, Q3 = Q * Q * Q, CT = Q2 * 3;
   __shared__ double Ehalf[36];
-  __shared__ double col[3 * Q2 * 3];
-  __shared__ double mdg[3 * Q2];  // |c_d|^2 on each column's table
+  __shared__ double col[3 * CT];
+  __shared__ long long colx[3 * CT];  // the columns in fixed point, one scale per table (1079 - cexp)
+  __shared__ long long mdx[3 * Q2];   // |c_d|^2 from them (scale 2 s_d - 58)
+  __shared__ int cexp[3];
   __shared__ double sw[Q], s0[Q], s1[Q];
   if (threadIdx.x < Q) {
     sw[threadIdx.x] = T.gw[threadIdx.x];
@@ -42,38 +45,114 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   }
   __syncthreads();
   int bad = 0;
+  int* sdq = lor_d_scales(Dq, m.nel * Q3);
   for (int64_t e = blockIdx.x; e < m.nel; e += gridDim.x) {
     lor_jacobian_columns(m, e, s0, s1, Q, Ehalf, col);
+    if (threadIdx.x < 3) cexp[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * CT; i += blockDim.x) atomicMax(&cexp[i / CT], fx_expo(col[i]));
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * CT; i += blockDim.x) colx[i] = fx_pack(fx_from_double(col[i], cexp[i / CT]));
+    __syncthreads();
     for (int i = threadIdx.x; i < 3 * Q2; i += blockDim.x) {
-      const double* cc = col + 3 * i;
-      mdg[i] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+      FAcc acc = fx_acc();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fx_mac(acc, fx_unpack(colx[3 * i + k]), fx_unpack(colx[3 * i + k]));
+      mdx[i] = fx_pack(fx_res(acc) >> 2);
     }
     __syncthreads();
+    const int sc0 = 1079 - cexp[0], sc1 = 1079 - cexp[1], sc2 = 1079 - cexp[2], S3 = sc0 + sc1 + sc2;
+    const int sAb[6] = {2 * S3 - 2 * sc0, S3 + sc2, S3 + sc1, 2 * S3 - 2 * sc1, S3 + sc0, 2 * S3 - 2 * sc2};
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
-      const double* c0 = col + 0 * Q2 * 3 + 3 * (g1 + Q * g2);
-      const double* c1 = col + 1 * Q2 * 3 + 3 * (g0 + Q * g2);
-      const double* c2 = col + 2 * Q2 * 3 + 3 * (g0 + Q * g1);
-      const double M00 = mdg[g1 + Q * g2], M11 = mdg[Q2 + g0 + Q * g2], M22 = mdg[2 * Q2 + g0 + Q * g1];
-      const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
-      const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
-      const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
-      const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
-      const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
-      const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
-      const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
+      const long long* c0 = colx + 3 * (g1 + Q * g2);
+      const long long* c1 = colx + CT + 3 * (g0 + Q * g2);
+      const long long* c2 = colx + 2 * CT + 3 * (g0 + Q * g1);
+      // M = J^T J (scale s_a + s_b - 58), one shift to 58 bits
+      long long M[6];  // 00, 01, 02, 11, 12, 22
+      {
+        FAcc t01 = fx_acc(), t02 = fx_acc(), t12 = fx_acc();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const Fx a = fx_unpack(c0[k]), b = fx_unpack(c1[k]), c = fx_unpack(c2[k]);
+          fx_mac(t01, a, b);
+          fx_mac(t02, a, c);
+          fx_mac(t12, b, c);
+        }
+        const Fx d0 = fx_unpack(mdx[g1 + Q * g2]), d1 = fx_unpack(mdx[Q2 + g0 + Q * g2]),
+                 d2 = fx_unpack(mdx[2 * Q2 + g0 + Q * g1]);
+        M[0] = (long long)d0.h * (1ll << 28) + d0.l;
+        M[1] = fx_res(t01) >> 2;
+        M[2] = fx_res(t02) >> 2;
+        M[3] = (long long)d1.h * (1ll << 28) + d1.l;
+        M[4] = fx_res(t12) >> 2;
+        M[5] = (long long)d2.h * (1ll << 28) + d2.l;
+      }
+      unsigned long long om = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fx_or(om, M[k]);
+      const int dM = 58 - fx_bits(om);
+      Fx Mx[6], nMx[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const long long v = fx_shift(M[k], dM);
+        Mx[k] = fx_split(v);
+        nMx[k] = fx_split(-v);
+      }
+      // adj(M), one shift to 58 bits (adj(M)_ab at sAb[ab] + sdA)
+      long long Ad[6];
+      {
+        FAcc t;
+        t = fx_acc(); fx_mac(t, Mx[3], Mx[5]); fx_mac(t, nMx[4], Mx[4]); Ad[0] = fx_res(t);  // M11 M22 - M12^2
+        t = fx_acc(); fx_mac(t, Mx[2], Mx[4]); fx_mac(t, nMx[1], Mx[5]); Ad[1] = fx_res(t);  // M02 M12 - M01 M22
+        t = fx_acc(); fx_mac(t, Mx[1], Mx[4]); fx_mac(t, nMx[2], Mx[3]); Ad[2] = fx_res(t);  // M01 M12 - M02 M11
+        t = fx_acc(); fx_mac(t, Mx[0], Mx[5]); fx_mac(t, nMx[2], Mx[2]); Ad[3] = fx_res(t);  // M00 M22 - M02^2
+        t = fx_acc(); fx_mac(t, Mx[1], Mx[2]); fx_mac(t, nMx[0], Mx[4]); Ad[4] = fx_res(t);  // M01 M02 - M00 M12
+        t = fx_acc(); fx_mac(t, Mx[0], Mx[3]); fx_mac(t, nMx[1], Mx[1]); Ad[5] = fx_res(t);  // M00 M11 - M01^2
+      }
+      unsigned long long oa = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fx_or(oa, Ad[k]);
+      const int dA = 58 - fx_bits(oa);
+      Fx Ax[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Ax[k] = fx_split(fx_shift(Ad[k], dA));
+      long long det;
+      {
+        FAcc t = fx_acc();
+        fx_mac(t, Mx[0], Ax[0]);
+        fx_mac(t, Mx[1], Ax[1]);
+        fx_mac(t, Mx[2], Ax[2]);
+        det = fx_res(t);
+      }
+      const int sdA = 2 * dM - 116 - kFxMacShift + dA;
+      const int sdet = 2 * S3 - 58 + dM + sdA - kFxMacShift;
       const double k = kin[e * Q3 + pt];
       if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
-      if (!(detM > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
-      const double s = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(detM);
-      const double d[6] = {s * A00, s * A01, s * A02, s * A11, s * A12, s * A22};
-      int em = 0;
+      if (!(det > 0)) bad |= LOR_FLAG_BAD_GEOM;
+      // s = kappa w / sqrt(det M) in FP64, then D_ab = s adj(M)_ab in fixed point
+      const double sv = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(fx_to_double(det, sdet));
+      const int es = fx_expo(sv);
+      const Fx sx = fx_split(fx_from_double(sv, es));
+      const int ss = 1079 - es;
+      long long D[6];
+      int mx = -(1 << 30);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) em = max(em, fx_expo(d[c]));
-      long long* D = reinterpret_cast<long long*>(Dq) + e * 6 * Q3 + pt;
+      for (int ab = 0; ab < 6; ++ab) {
+        FAcc t = fx_acc();
+        fx_mac(t, sx, Ax[ab]);
+        D[ab] = fx_res(t);  // at most 2^59, scale ss + sAb[ab] + sdA - 56
+        if (D[ab] != 0)
+          mx = max(mx, fx_bits((unsigned long long)(D[ab] ^ (D[ab] >> 63))) - (ss + sAb[ab] + sdA - kFxMacShift));
+      }
+      // the point's six entries at its largest: that one at most 2^57 (entry = X 2^-sd)
+      const bool any = mx > -(1 << 30);
+      const int sd = 57 - mx;
+      long long* Dp = reinterpret_cast<long long*>(Dq) + e * 6 * Q3 + pt;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) D[c * Q3] = fx_pack(fx_from_double(d[c], em));
-      lor_d_scales(Dq, m.nel * Q3)[e * Q3 + pt] = em == 0 ? INT_MAX : 1079 - em;
+      for (int ab = 0; ab < 6; ++ab)
+        Dp[ab * Q3] = any ? fx_pack(fx_shift(D[ab], min(sd - (ss + sAb[ab] + sdA - kFxMacShift), 63))) : 0ll;
+      sdq[e * Q3 + pt] = any ? sd : INT_MAX;
       kcopy[e * Q3 + pt] = k;
     }
     __syncthreads();
