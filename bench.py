@@ -21,6 +21,17 @@ workload handed over as a general mesh under "general_mesh"; the error of
 every mixed-precision result against its FP64 counterpart under
 "mixed_precision_errors".
 
+Per kernel ("kernels"): time, GDOF/s and the fraction of the HBM peak; the
+kernels whose arithmetic runs in 64-bit fixed point on the integer pipe (the
+operator and its backward) report their FP64-equivalent rate (the direct
+sum-factorisation count over the FP64 peak, frac_fp64_equiv, which may
+exceed 1) and the fraction of the integer multiply-add peak their
+mad.wide.s32 instructions take (int_mad_frac), the others frac_fp64: the
+flops of the formula they evaluate over the FP64 peak (setup and assembly
+form their metric's products in fixed point too, so theirs is also an
+FP64-equivalent rate).  The FP64-pipe or issue-slot activity comes from the
+committed ncu summaries while their sources are unchanged.
+
 Runs as `python bench.py --gpus N --steps K --warmup W` (torchrun for N > 1:
 every rank solves its own replica; no data-path collective).  With
 `--impl reference` it times the CPU oracle instead (rank 0 only), each step
