@@ -452,6 +452,11 @@ def run_gpu(args, rank, world, local_rank):
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64; no FP64 entry in "
                                    "MEASURED_PEAKS.json)",
                     "fp64_pipe_active": dk["fp64_pipe_active"]}
+        if dominant in ("assemble", "setup"):
+            roofline["numerator"] = ("FP64-equivalent: the flops of the formula the kernel evaluates "
+                                     "(perfmodel) over the FP64 peak; the kernel forms the metric's products "
+                                     "(and the assembly its block algebra) in 64-bit fixed point on the "
+                                     "integer pipe, so the FP64 pipe is busy for part of it (fp64_pipe_active)")
     roofline.update({"traffic": traffic,
                      "hbm": {"achieved_gbs": dk["gbs"], "peak_gbs": hbm_peak, "peak_source": hbm_src,
                              "frac": dk["frac_hbm"]}})
