@@ -319,9 +319,7 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   // FP64 mode: the Jacobian columns in fixed point (packed words, one scale
   // per column table: 1079 - cexp) and |c_d|^2 formed from them
   __shared__ long long tabx[FXG ? EPB : 1][FXG ? TAB : 1];
-  __shared__ long long mdx[FXG ? EPB : 1][FXG ? 3 * L * L : 1];
   __shared__ int cexp[FXG ? EPB : 1][3];
-  __shared__ double mdiag[(!F32 && !FXG) ? EPB : 1][(!F32 && !FXG) ? 3 * L * L : 1];  // |c_d|^2 in FP64
   __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
   __shared__ double sl0[L], sl1[L];
   if (threadIdx.x < L) {
@@ -340,14 +338,7 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   if constexpr (F32) {
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
     __syncthreads();
-  } else if constexpr (!FXG) {
-    constexpr int ND = 3 * L * L;
-    for (int i = threadIdx.x; i < EPB * ND; i += blockDim.x) {
-      const double* cc = &tab[i / ND][3 * (i % ND)];
-      mdiag[i / ND][i % ND] = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
-    }
-    __syncthreads();
-  } else {
+  } else if constexpr (FXG) {
     constexpr int CT = L * L * 3;  // one column table
     for (int i = threadIdx.x; i < EPB * 3; i += blockDim.x) cexp[i / 3][i % 3] = 0;
     __syncthreads();
@@ -356,16 +347,6 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     __syncthreads();
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x)
       tabx[i / TAB][i % TAB] = fx_pack(fx_from_double(tab[i / TAB][i % TAB], cexp[i / TAB][(i % TAB) / CT]));
-    __syncthreads();
-    // |c_d|^2: at most 3 2^58 before the shift, so at most 2^58 stored (scale 2 s_d - 58)
-    constexpr int ND = 3 * L * L;
-    for (int i = threadIdx.x; i < EPB * ND; i += blockDim.x) {
-      const long long* cc = &tabx[i / ND][3 * (i % ND)];
-      FAcc acc = fx_acc();
-#pragma unroll
-      for (int k = 0; k < 3; ++k) fx_mac(acc, fx_unpack(cc[k]), fx_unpack(cc[k]));
-      mdx[i / ND][i % ND] = fx_pack(fx_res(acc) >> 2);
-    }
     __syncthreads();
   }
   const int nwork = EPB * P3;
@@ -394,12 +375,11 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     VT G[F32 ? 6 : 1][F32 ? 8 : 1];  // FP32: the metric (pair order 00, 01, 02, 11, 12, 22)
     VT W[(MASS && F32) ? 8 : 1];      // FP32 reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
     const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
-    // FP64: the metric's products in fixed point (see fixed_point.cuh) from
-    // the columns' fixed-point tables, each stage renormalised per Gauss point
-    // (one shift for the six M entries, one for the six cofactors, one for
-    // det M, so every cofactor's and det's terms share a scale); 1/sqrt(det M)
-    // by the range-reduced FP64 reciprocal square root; the sub-hex's 48
-    // metric values (and 8 mass weights) aligned to one scale for the block.
+    // FP64: the metric from the adjugate rows of J_e (cross and dot products of
+    // the columns' fixed-point tables, fx_metric), 1/det J_e by the
+    // range-reduced FP64 reciprocal square root of det M = (det J_e)^2,
+    // G = F r adj(M) in fixed point; the sub-hex's 48 metric values (and 8 mass
+    // weights) aligned to one scale for the block.
     long long X[FXG ? 6 : 1][FXG ? 8 : 1];
     long long Xw[(MASS && FXG) ? 8 : 1];
     int st = 0;
@@ -427,92 +407,25 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
         sbR = 1079 - eb;
       }
       constexpr int CT = L * L * 3;
-      const int s0 = 1079 - cexp[le][0], s1 = 1079 - cexp[le][1], s2 = 1079 - cexp[le][2];
-      // static scales: M_ab at s_a + s_b - 58 (+ dM); a cofactor's two products
-      // at the sum of two M scales less 56, so adj(M)_ab at sAb[ab] + sdA
-      // (sAb: 2S - 2 s_a on the diagonal, S + s_c off it, S = s0 + s1 + s2);
-      // det M's three products at 2S - 58 + dM + sdA - 56
-      const int S3 = s0 + s1 + s2;
-      const int sAb[6] = {2 * S3 - 2 * s0, S3 + s2, S3 + s1, 2 * S3 - 2 * s1, S3 + s0, 2 * S3 - 2 * s2};
+      const int scs[3] = {1079 - cexp[le][0], 1079 - cexp[le][1], 1079 - cexp[le][2]};
       const long long* x0 = tabx[le];
       const long long* x1 = tabx[le] + CT;
       const long long* x2 = tabx[le] + 2 * CT;
-      const long long* d0 = mdx[le];
-      const long long* d1 = mdx[le] + L * L;
-      const long long* d2 = mdx[le] + 2 * L * L;
       int sG[8];
       int sW[MASS ? 8 : 1];
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
-        const long long* c0 = x0 + 3 * (u1 + L * u2);
-        const long long* c1 = x1 + 3 * (u0 + L * u2);
-        const long long* c2 = x2 + 3 * (u0 + L * u1);
-        Fx A0[3], A1[3], A2[3];
+        Fx C[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          A0[k] = fx_unpack(c0[k]);
-          A1[k] = fx_unpack(c1[k]);
-          A2[k] = fx_unpack(c2[k]);
+          C[0][k] = fx_unpack(x0[3 * (u1 + L * u2) + k]);
+          C[1][k] = fx_unpack(x1[3 * (u0 + L * u2) + k]);
+          C[2][k] = fx_unpack(x2[3 * (u0 + L * u1) + k]);
         }
-        // M = J^T J: six entries, then one shift that brings the largest to 58 bits
-        long long M[6];  // 00, 01, 02, 11, 12, 22
-        {
-          FAcc t01 = fx_acc(), t02 = fx_acc(), t12 = fx_acc();
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            fx_mac(t01, A0[k], A1[k]);
-            fx_mac(t02, A0[k], A2[k]);
-            fx_mac(t12, A1[k], A2[k]);
-          }
-          M[0] = fx_unpack(d0[u1 + L * u2]).h * (1ll << 28) + fx_unpack(d0[u1 + L * u2]).l;
-          M[1] = fx_res(t01) >> 2;
-          M[2] = fx_res(t02) >> 2;
-          M[3] = fx_unpack(d1[u0 + L * u2]).h * (1ll << 28) + fx_unpack(d1[u0 + L * u2]).l;
-          M[4] = fx_res(t12) >> 2;
-          M[5] = fx_unpack(d2[u0 + L * u1]).h * (1ll << 28) + fx_unpack(d2[u0 + L * u1]).l;
-        }
-        unsigned long long om = 0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fx_or(om, M[k]);
-        const int dM = 58 - fx_bits(om);  // M_ab at s_a + s_b - 58 + dM
-        Fx Mx[6], nMx[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const long long v = fx_shift(M[k], dM);
-          Mx[k] = fx_split(v);
-          nMx[k] = fx_split(-v);
-        }
-        // adj(M): two products each (at most 2^61), one shift to 58 bits
-        long long Ad[6];
-        {
-          FAcc t;
-          t = fx_acc(); fx_mac(t, Mx[3], Mx[5]); fx_mac(t, nMx[4], Mx[4]); Ad[0] = fx_res(t);  // M11 M22 - M12^2
-          t = fx_acc(); fx_mac(t, Mx[2], Mx[4]); fx_mac(t, nMx[1], Mx[5]); Ad[1] = fx_res(t);  // M02 M12 - M01 M22
-          t = fx_acc(); fx_mac(t, Mx[1], Mx[4]); fx_mac(t, nMx[2], Mx[3]); Ad[2] = fx_res(t);  // M01 M12 - M02 M11
-          t = fx_acc(); fx_mac(t, Mx[0], Mx[5]); fx_mac(t, nMx[2], Mx[2]); Ad[3] = fx_res(t);  // M00 M22 - M02^2
-          t = fx_acc(); fx_mac(t, Mx[1], Mx[2]); fx_mac(t, nMx[0], Mx[4]); Ad[4] = fx_res(t);  // M01 M02 - M00 M12
-          t = fx_acc(); fx_mac(t, Mx[0], Mx[3]); fx_mac(t, nMx[1], Mx[1]); Ad[5] = fx_res(t);  // M00 M11 - M01^2
-        }
-        unsigned long long oa = 0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fx_or(oa, Ad[k]);
-        const int dA = 58 - fx_bits(oa);
-        Fx Ax[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Ax[k] = fx_split(fx_shift(Ad[k], dA));
-        // det M = M00 A00 + M01 A01 + M02 A02 (at most 3 2^60), to 58 bits
-        long long det;
-        {
-          FAcc t = fx_acc();
-          fx_mac(t, Mx[0], Ax[0]);
-          fx_mac(t, Mx[1], Ax[1]);
-          fx_mac(t, Mx[2], Ax[2]);
-          det = fx_res(t);
-        }
-        const int sdA = 2 * dM - 116 - kFxMacShift + dA;        // adj(M)_ab at sAb[ab] + sdA
-        const int sdet = 2 * S3 - 58 + dM + sdA - kFxMacShift;  // det M at sdet
-        const double r = lor_rsqrt(fx_to_double(det, sdet));   // 1 / det J_e
+        FxMetric mt;
+        fx_metric(C, scs, mt);
+        const double r = lor_rsqrt(mt.detM);  // 1 / det J_e
         const int er = fx_expo(r);
         const Fx rx = fx_split(fx_from_double(r, er));
         const int sr = 1079 - er;
@@ -522,20 +435,18 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
           FAcc f = fx_acc();
           fx_mac(f, FFx[ab], rx);
           FAcc q = fx_acc();
-          fx_mac(q, fx_split(fx_res(f)), Ax[ab]);
+          fx_mac(q, fx_split(fx_res(f)), mt.A[ab]);
           X[ab][g] = fx_res(q);
         }
-        sG[g] = sr - kFxMacShift + sdA - kFxMacShift;  // G_ab at sF[ab] + sAb[ab] + sG[g]
+        sG[g] = sr - kFxMacShift + mt.sA - kFxMacShift;  // G_ab at sF[ab] + sG[g]
         if constexpr (MASS) {
-          // W = beta_s r_a r_b r_c / 64 detJ_e = bR det M r
-          const int ed = 58 - fx_bits((unsigned long long)(det ^ (det >> 63)));
-          FAcc f = fx_acc();
-          fx_mac(f, fx_split(fx_shift(det, ed)), rx);
-          const long long dr = fx_res(f);  // at most 2^59
+          // W = beta_s r_a r_b r_c / 64 det J_e, det J_e = det M r
+          const double dj = mt.detM * r;
+          const int ej = fx_expo(dj);
           FAcc q = fx_acc();
-          fx_mac(q, bRx, fx_split(dr >> 1));
-          Xw[g] = fx_res(q);
-          sW[g] = sbR + (sdet + ed + sr - kFxMacShift - 1) - kFxMacShift;
+          fx_mac(q, bRx, fx_split(fx_from_double(dj, ej)));
+          Xw[g] = fx_res(q);  // at most 2^58
+          sW[g] = sbR + (1079 - ej) - kFxMacShift;
         }
       }
       // one scale for the sub-hex: its largest value below 2^56
@@ -545,7 +456,7 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
 #pragma unroll
         for (int g = 0; g < 8; ++g)
           if (X[ab][g] != 0)
-            mmax = max(mmax, fx_bits((unsigned long long)(X[ab][g] ^ (X[ab][g] >> 63))) - (sF[ab] + sAb[ab] + sG[g]));
+            mmax = max(mmax, fx_bits((unsigned long long)(X[ab][g] ^ (X[ab][g] >> 63))) - (sF[ab] + sG[g]));
       if constexpr (MASS)
 #pragma unroll
         for (int g = 0; g < 8; ++g)
@@ -554,49 +465,39 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
 #pragma unroll
       for (int ab = 0; ab < 6; ++ab)
 #pragma unroll
-        for (int g = 0; g < 8; ++g) X[ab][g] = fx_shift(X[ab][g], min(st - (sF[ab] + sAb[ab] + sG[g]), 63));
+        for (int g = 0; g < 8; ++g) X[ab][g] = fx_shift(X[ab][g], min(st - (sF[ab] + sG[g]), 63));
       if constexpr (MASS)
 #pragma unroll
         for (int g = 0; g < 8; ++g) Xw[g] = fx_shift(Xw[g], min(st - sW[g], 63));
     } else if constexpr (!F32) {
+      // p = 1: the same metric in FP64 (adjugate rows of J_e)
       const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
       const double k64 = ks * (1.0 / 64.0);
-      double FF[6];
-      FF[0] = k64 * rb * rc * T.sub_rinv[a];
-      FF[1] = k64 * rc;
-      FF[2] = k64 * rb;
-      FF[3] = k64 * ra * rc * T.sub_rinv[b];
-      FF[4] = k64 * ra;
-      FF[5] = k64 * ra * rb * T.sub_rinv[c];
+      const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
+                            k64 * ra * rc * T.sub_rinv[b], k64 * ra, k64 * ra * rb * T.sub_rinv[c]};
       const double bR = MASS ? bs * (1.0 / 64.0) * ra * rb * rc : 0.0;
       const double* t0 = tab[le];
       const double* t1 = tab[le] + L * L * 3;
       const double* t2 = tab[le] + 2 * L * L * 3;
-      const double* q0 = mdiag[le];
-      const double* q1 = mdiag[le] + L * L;
-      const double* q2 = mdiag[le] + 2 * L * L;
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
         const double* c0 = t0 + 3 * (u1 + L * u2);
         const double* c1 = t1 + 3 * (u0 + L * u2);
         const double* c2 = t2 + 3 * (u0 + L * u1);
-        const double M00 = q0[u1 + L * u2], M11 = q1[u0 + L * u2], M22 = q2[u0 + L * u1];
-        const double M01 = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
-        const double M02 = c0[0] * c2[0] + c0[1] * c2[1] + c0[2] * c2[2];
-        const double M12 = c1[0] * c2[0] + c1[1] * c2[1] + c1[2] * c2[2];
-        const double A00 = fma(M11, M22, -M12 * M12), A11 = fma(M00, M22, -M02 * M02);
-        const double A22 = fma(M00, M11, -M01 * M01), A01 = fma(M02, M12, -M01 * M22);
-        const double A02 = fma(M01, M12, -M02 * M11), A12 = fma(M01, M02, -M00 * M12);
-        const double detM = fma(M00, A00, fma(M01, A01, M02 * A02));
+        double R[3][3];
+        lor_cross(c1, c2, R[0]);
+        lor_cross(c2, c0, R[1]);
+        lor_cross(c0, c1, R[2]);
+        const double dj = c0[0] * R[0][0] + c0[1] * R[0][1] + c0[2] * R[0][2];
+        const double detM = dj * dj;
         const double r = lor_rsqrt(detM);  // 1 / det J_e
         if constexpr (MASS) Wd[g] = bR * (detM * r);
-        Gd[0][g] = ((FF[0] * r) * A00);
-        Gd[1][g] = ((FF[1] * r) * A01);
-        Gd[2][g] = ((FF[2] * r) * A02);
-        Gd[3][g] = ((FF[3] * r) * A11);
-        Gd[4][g] = ((FF[4] * r) * A12);
-        Gd[5][g] = ((FF[5] * r) * A22);
+#pragma unroll
+        for (int ab = 0; ab < 6; ++ab) {
+          const int pa = ab < 3 ? 0 : ab < 5 ? 1 : 2, pb = ab < 3 ? ab : ab < 5 ? ab - 2 : 2;
+          Gd[ab][g] = (FF[ab] * r) * (R[pa][0] * R[pb][0] + R[pa][1] * R[pb][1] + R[pa][2] * R[pb][2]);
+        }
       }
     } else {
       // FP64: the first adjugate row and the determinant; FP32: the rest.

@@ -7,26 +7,28 @@
 // so these kernels would be bound by FP64 issue, not by HBM.  A trilinear map
 // has dx/dxi_0 independent of xi_0 (and likewise for the other columns), so
 // each Jacobian column is tabulated once per element on a q x q grid in shared
-// memory, and so are the squared column norms; per point the metric follows
-// from the rest of M = J^T J.  The setup forms those products in 64-bit fixed
-// point on the integer pipe (fixed_point.cuh), as the LOR assembly does.
+// memory; per point the metric follows from their cross and dot products,
+// formed in 64-bit fixed point on the integer pipe (fixed_point.cuh), as the
+// LOR assembly does.
 #include "fixed_point.cuh"
 #include "lor_internal.cuh"
 
 namespace {
 
-// D = kappa w detJ J^-1 J^-T = kappa w adj(M) / sqrt(det M) with M = J^T J:
-// M's diagonal |c_d|^2 depends only on the two coordinates its column is
-// tabulated on, so it is tabulated per element next to the columns; per
-// Gauss point remain the three off-diagonal products, the six cofactors,
-// det M and one reciprocal square root.  The products run in 64-bit fixed
-// point: the column tables converted once per element (one scale per table),
-// M, adj(M) and det M renormalised per point; 1/sqrt(det M) (range-reduced)
-// and kappa w times it in FP64; D_ab = (kappa w / sqrt(det M)) adj(M)_ab in
-// fixed point, stored in the form the FP64 operator multiplies it in (the
-// point's six entries at its largest, fixed_point.cuh).  det M > 0 is checked
-// here; the sign of det J was checked at context creation (the mesh does not
-// change afterwards).
+// D = kappa w detJ J^-1 J^-T = kappa w adj(J^T J) / det J, with adj(J^T J)_ab
+// = r_a . r_b for the adjugate rows r_a = c_b x c_c of J (columns c_d,
+// (a, b, c) cyclic) and det J = c_0 . r_0: formed this way the error stays
+// O(eps cond(J)), where the cofactors of M = J^T J lose O(eps cond(J)^2) on
+// stretched or skewed elements (5e-8 of the largest entry at cond(J) = 1e5
+// in FP64).  The Jacobian columns are tabulated per element (a trilinear
+// map's dx/dxi_0 does not depend on xi_0, and so on) and converted to 64-bit
+// fixed point, one scale per column table; per Gauss point the cross and dot
+// products run on the integer pipe (fixed_point.cuh: fx_metric), 1/det J
+// (range-reduced) and kappa w times it in FP64, D_ab = (kappa w / det J)
+// adj(M)_ab in fixed point, stored in the form the FP64 operator multiplies it
+// in (the point's six entries at its largest).  det J > 0 is checked here; its
+// sign was checked at context creation too (the mesh does not change
+// afterwards).
 template <int P>
 __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const double* __restrict__ kin,
                                                double* __restrict__ kcopy, double* __restrict__ Dq,
@@ -35,7 +37,6 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
   __shared__ double Ehalf[36];
   __shared__ double col[3 * CT];
   __shared__ long long colx[3 * CT];  // the columns in fixed point, one scale per table (1079 - cexp)
-  __shared__ long long mdx[3 * Q2];   // |c_d|^2 from them (scale 2 s_d - 58)
   __shared__ int cexp[3];
   __shared__ double sw[Q], s0[Q], s1[Q];
   if (threadIdx.x < Q) {
@@ -54,84 +55,23 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * CT; i += blockDim.x) colx[i] = fx_pack(fx_from_double(col[i], cexp[i / CT]));
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * Q2; i += blockDim.x) {
-      FAcc acc = fx_acc();
-#pragma unroll
-      for (int k = 0; k < 3; ++k) fx_mac(acc, fx_unpack(colx[3 * i + k]), fx_unpack(colx[3 * i + k]));
-      mdx[i] = fx_pack(fx_res(acc) >> 2);
-    }
-    __syncthreads();
-    const int sc0 = 1079 - cexp[0], sc1 = 1079 - cexp[1], sc2 = 1079 - cexp[2], S3 = sc0 + sc1 + sc2;
-    const int sAb[6] = {2 * S3 - 2 * sc0, S3 + sc2, S3 + sc1, 2 * S3 - 2 * sc1, S3 + sc0, 2 * S3 - 2 * sc2};
+    const int scs[3] = {1079 - cexp[0], 1079 - cexp[1], 1079 - cexp[2]};
     for (int pt = threadIdx.x; pt < Q3; pt += blockDim.x) {
       const int g0 = pt % Q, g1 = (pt / Q) % Q, g2 = pt / Q2;
-      const long long* c0 = colx + 3 * (g1 + Q * g2);
-      const long long* c1 = colx + CT + 3 * (g0 + Q * g2);
-      const long long* c2 = colx + 2 * CT + 3 * (g0 + Q * g1);
-      // M = J^T J (scale s_a + s_b - 58), one shift to 58 bits
-      long long M[6];  // 00, 01, 02, 11, 12, 22
-      {
-        FAcc t01 = fx_acc(), t02 = fx_acc(), t12 = fx_acc();
+      Fx C[3][3];  // C[d][k]: component k of column d
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const Fx a = fx_unpack(c0[k]), b = fx_unpack(c1[k]), c = fx_unpack(c2[k]);
-          fx_mac(t01, a, b);
-          fx_mac(t02, a, c);
-          fx_mac(t12, b, c);
-        }
-        const Fx d0 = fx_unpack(mdx[g1 + Q * g2]), d1 = fx_unpack(mdx[Q2 + g0 + Q * g2]),
-                 d2 = fx_unpack(mdx[2 * Q2 + g0 + Q * g1]);
-        M[0] = (long long)d0.h * (1ll << 28) + d0.l;
-        M[1] = fx_res(t01) >> 2;
-        M[2] = fx_res(t02) >> 2;
-        M[3] = (long long)d1.h * (1ll << 28) + d1.l;
-        M[4] = fx_res(t12) >> 2;
-        M[5] = (long long)d2.h * (1ll << 28) + d2.l;
+      for (int k = 0; k < 3; ++k) {
+        C[0][k] = fx_unpack(colx[3 * (g1 + Q * g2) + k]);
+        C[1][k] = fx_unpack(colx[CT + 3 * (g0 + Q * g2) + k]);
+        C[2][k] = fx_unpack(colx[2 * CT + 3 * (g0 + Q * g1) + k]);
       }
-      unsigned long long om = 0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) fx_or(om, M[k]);
-      const int dM = 58 - fx_bits(om);
-      Fx Mx[6], nMx[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const long long v = fx_shift(M[k], dM);
-        Mx[k] = fx_split(v);
-        nMx[k] = fx_split(-v);
-      }
-      // adj(M), one shift to 58 bits (adj(M)_ab at sAb[ab] + sdA)
-      long long Ad[6];
-      {
-        FAcc t;
-        t = fx_acc(); fx_mac(t, Mx[3], Mx[5]); fx_mac(t, nMx[4], Mx[4]); Ad[0] = fx_res(t);  // M11 M22 - M12^2
-        t = fx_acc(); fx_mac(t, Mx[2], Mx[4]); fx_mac(t, nMx[1], Mx[5]); Ad[1] = fx_res(t);  // M02 M12 - M01 M22
-        t = fx_acc(); fx_mac(t, Mx[1], Mx[4]); fx_mac(t, nMx[2], Mx[3]); Ad[2] = fx_res(t);  // M01 M12 - M02 M11
-        t = fx_acc(); fx_mac(t, Mx[0], Mx[5]); fx_mac(t, nMx[2], Mx[2]); Ad[3] = fx_res(t);  // M00 M22 - M02^2
-        t = fx_acc(); fx_mac(t, Mx[1], Mx[2]); fx_mac(t, nMx[0], Mx[4]); Ad[4] = fx_res(t);  // M01 M02 - M00 M12
-        t = fx_acc(); fx_mac(t, Mx[0], Mx[3]); fx_mac(t, nMx[1], Mx[1]); Ad[5] = fx_res(t);  // M00 M11 - M01^2
-      }
-      unsigned long long oa = 0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) fx_or(oa, Ad[k]);
-      const int dA = 58 - fx_bits(oa);
-      Fx Ax[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Ax[k] = fx_split(fx_shift(Ad[k], dA));
-      long long det;
-      {
-        FAcc t = fx_acc();
-        fx_mac(t, Mx[0], Ax[0]);
-        fx_mac(t, Mx[1], Ax[1]);
-        fx_mac(t, Mx[2], Ax[2]);
-        det = fx_res(t);
-      }
-      const int sdA = 2 * dM - 116 - kFxMacShift + dA;
-      const int sdet = 2 * S3 - 58 + dM + sdA - kFxMacShift;
+      FxMetric mt;
+      fx_metric(C, scs, mt);
       const double k = kin[e * Q3 + pt];
       if (!(k > 0.0) || !(k < INFINITY)) bad |= LOR_FLAG_BAD_KAPPA;
-      if (!(det > 0)) bad |= LOR_FLAG_BAD_GEOM;
-      // s = kappa w / sqrt(det M) in FP64, then D_ab = s adj(M)_ab in fixed point
-      const double sv = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(fx_to_double(det, sdet));
+      if (!(mt.detM > 0.0)) bad |= LOR_FLAG_BAD_GEOM;
+      // s = kappa w / det J in FP64, then D_ab = s adj(M)_ab in fixed point
+      const double sv = k * (sw[g0] * sw[g1] * sw[g2]) * lor_rsqrt(mt.detM);
       const int es = fx_expo(sv);
       const Fx sx = fx_split(fx_from_double(sv, es));
       const int ss = 1079 - es;
@@ -140,10 +80,9 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
 #pragma unroll
       for (int ab = 0; ab < 6; ++ab) {
         FAcc t = fx_acc();
-        fx_mac(t, sx, Ax[ab]);
-        D[ab] = fx_res(t);  // at most 2^59, scale ss + sAb[ab] + sdA - 56
-        if (D[ab] != 0)
-          mx = max(mx, fx_bits((unsigned long long)(D[ab] ^ (D[ab] >> 63))) - (ss + sAb[ab] + sdA - kFxMacShift));
+        fx_mac(t, sx, mt.A[ab]);
+        D[ab] = fx_res(t);  // at most 2^59, scale ss + sA - 56
+        if (D[ab] != 0) mx = max(mx, fx_bits((unsigned long long)(D[ab] ^ (D[ab] >> 63))) - (ss + mt.sA - kFxMacShift));
       }
       // the point's six entries at its largest: that one at most 2^57 (entry = X 2^-sd)
       const bool any = mx > -(1 << 30);
@@ -151,7 +90,7 @@ __global__ void __launch_bounds__(128) k_setup(LorMesh m, LorTables T, const dou
       long long* Dp = reinterpret_cast<long long*>(Dq) + e * 6 * Q3 + pt;
 #pragma unroll
       for (int ab = 0; ab < 6; ++ab)
-        Dp[ab * Q3] = any ? fx_pack(fx_shift(D[ab], min(sd - (ss + sAb[ab] + sdA - kFxMacShift), 63))) : 0ll;
+        Dp[ab * Q3] = any ? fx_pack(fx_shift(D[ab], min(sd - (ss + mt.sA - kFxMacShift), 63))) : 0ll;
       sdq[e * Q3 + pt] = any ? sd : INT_MAX;
       kcopy[e * Q3 + pt] = k;
     }

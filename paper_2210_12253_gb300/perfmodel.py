@@ -53,23 +53,22 @@ def jacobian_columns_flops(L):
 
 
 def setup_flops_per_element(p):
-    """Jacobian columns at the q x q Gauss pairs and their squared norms (the
-    diagonal of M = J^T J, 5 each, 3 q^2); per Gauss point the off-diagonal
-    entries of M (15), its cofactors (18), det M (5), 1/sqrt(det M) (1), the
-    weight product (2), kappa w / sqrt(det M) (2) and the six scaled
-    cofactors (6): 49."""
+    """Jacobian columns at the q x q Gauss pairs; per Gauss point the
+    adjugate rows r_a = c_b x c_c (27), det J = c_0 . r_0 (5), det M =
+    (det J)^2 (1), 1/sqrt(det M) (1), the weight product (2), kappa w /
+    sqrt(det M) (2), adj(M)_ab = r_a . r_b (30) and the six scaled cofactors
+    (6): 74."""
     q = p + 2
-    return jacobian_columns_flops(q) + 15 * q * q + 49 * q ** 3
+    return jacobian_columns_flops(q) + 74 * q ** 3
 
 
 def assemble_flops_per_element(p):
     """FP64 LOR assembly as the kernel evaluates it: per element the Jacobian
-    columns at the 2p x 2p sub-hex Gauss pairs and the squared column norms
-    |c_d|^2 on the same tables (the diagonal of M = J^T J: 5 each, 3 (2p)^2);
-    per sub-hex, one 8x8 block by 2x2x2 Gauss in the modal (Walsh-Hadamard)
-    form: per Gauss point the off-diagonal entries of M (15), its cofactors
-    (18), det M (5), 1/sqrt(det M) (1), the six metric entries F_ab / sqrt(det
-    M) adj(M)_ab (12) = 51 x 8; six 8-point Walsh transforms, 24 additions
+    columns at the 2p x 2p sub-hex Gauss pairs; per sub-hex, one 8x8 block by
+    2x2x2 Gauss in the modal (Walsh-Hadamard) form: per Gauss point the
+    adjugate rows r_a = c_b x c_c (27), det J = c_0 . r_0 (5), det M (1),
+    1/sqrt(det M) (1), adj(M)_ab = r_a . r_b (30), the six metric entries
+    (F_ab / sqrt(det M)) adj(M)_ab (12) = 76 x 8; six 8-point Walsh transforms, 24 additions
     each less the 12 whose outputs the diagonal entries never use (108); the
     modal block, 28 sums of the |m||n| transformed entries (56 additions) and
     their 22 factors 3^(-(|m|+|n|-2)/2) other than 1 (78); the
@@ -81,8 +80,7 @@ def assemble_flops_per_element(p):
     additions of the transforms, the modal sums and the sandwich as exact
     64-bit integer additions; they are counted here as the flops they are.)"""
     q, L = p + 2, 2 * p
-    return (jacobian_columns_flops(L) + 15 * L * L + p ** 3 * (8 * 51 + 108 + 78 + 216 + 13) + 3 * q ** 3
-            + p * q * q)
+    return jacobian_columns_flops(L) + p ** 3 * (8 * 76 + 108 + 78 + 216 + 13) + 3 * q ** 3 + p * q * q
 
 
 def assemble_f32_flops_per_element(p):

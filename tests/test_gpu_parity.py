@@ -409,3 +409,30 @@ def test_fixed_point_operator_mixed_magnitudes(p):
     gk = gk.cpu().numpy().reshape(rgk.shape)
     assert np.abs(gk - rgk).max() <= 1e-12 * np.abs(rgk).max()
     op.close()
+
+
+@pytest.mark.parametrize("stretch,jitter,p", [((1000.0, 1.0, 1.0), 0.1, 3), ((1.0, 1e-3, 1e2), 0.1, 4),
+                                              ((1.0, 1.0, 1.0), 0.3, 4), ((1.0, 1.0, 1.0), 0.3, 2)])
+def test_fixed_point_metric_anisotropic_and_distorted(stretch, jitter, p):
+    """The setup and the LOR assembly form M = J^T J, adj(M) and det M in
+    fixed point with one scale per Jacobian-column table: elements stretched
+    1000:1 (and 1e5 between two axes) and strongly distorted ones (vertices
+    moved by up to 30% of the spacing) give the oracle's LOR values (1e-12 of
+    the row maximum) and apply (1e-12 of the maximum)."""
+    from paper_2210_12253_gb300 import LOR
+    dims = (3, 2, 2)
+    prob = make_problem("t", *dims, p, seed=9, jitter=jitter, kappa="lognormal", rhs="normal")
+    V = prob.vertices.reshape(-1, 3) * np.asarray(stretch)
+    V = V.reshape(prob.vertices.shape)
+    mesh = oracle.Mesh(*dims, V)
+    op = LOR(p, *dims, t(V))
+    op.set_coefficient(t(prob.kappa).reshape(-1), check=True)
+    op.build_pattern_internal()
+    v = op.assemble(torch.float64).cpu().numpy()
+    orp, _, ov = oracle.lor_assemble(mesh, p, p + 2, prob.kappa, True)
+    assert rowwise_rel_err(orp, v, ov) <= 1e-12
+    x = np.random.default_rng(3).standard_normal(op.ndof)
+    y = op.apply(t(x)).cpu().numpy()
+    ref = oracle.ho_apply(mesh, p, p + 2, prob.kappa, x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()

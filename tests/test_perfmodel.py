@@ -283,18 +283,16 @@ def test_setup_flops_evaluate_the_oracle_metric(p):
     xg, wg = oracle.gauss_legendre(q)
     w0, w1 = (1 - xg) / 2, (1 + xg) / 2
     col = jacobian_columns(corner_leaves(corners), w0, w1)
-    mdiag = [{key: dot3(c, c) for key, c in col[d].items()} for d in range(3)]  # |c_d|^2, tabulated
     sw = leaves(wg)  # weights are read from a table and multiplied at run time
     out = []
     for g2 in range(q):
         for g1 in range(q):
             for g0 in range(q):
                 c0, c1, c2 = col[0][g1, g2], col[1][g0, g2], col[2][g0, g1]
-                M00, M11, M22 = mdiag[0][g1, g2], mdiag[1][g0, g2], mdiag[2][g0, g1]
-                M01, M02, M12 = dot3(c0, c1), dot3(c0, c2), dot3(c1, c2)
-                adj = [M11 * M22 - M12 * M12, M02 * M12 - M01 * M22, M01 * M12 - M02 * M11,
-                       M00 * M22 - M02 * M02, M01 * M02 - M00 * M12, M00 * M11 - M01 * M01]
-                detM = M00 * adj[0] + M01 * adj[1] + M02 * adj[2]
+                R = [cross(c1, c2), cross(c2, c0), cross(c0, c1)]  # adjugate rows of J
+                dj = dot3(c0, R[0])
+                detM = dj * dj
+                adj = [dot3(R[i], R[j]) for i, j in PAIRS]
                 k = Flop(kappa[g0 + q * (g1 + q * g2)])
                 s = k * (sw[g0] * sw[g1] * sw[g2]) * rsqrt(detM)
                 out.append([s * a for a in adj])
@@ -423,9 +421,9 @@ def lor_element_modal(p, corners, kappa, beta=None, fp64=True):
     """The LOR blocks of one element, each sub-hex's 8x8 block by 2x2x2 Gauss
     in the modal form: metric at the 8 points, its Walsh transforms, the modal
     block, the Hadamard sandwich.  fp64: the metric as the FP64 kernel forms
-    it, adj(M) / sqrt(det M) from M = J^T J with M's diagonal tabulated per
-    element; otherwise from the adjugate rows of J and 1/det (the FP32
-    kernel).  Returns (blocks {(a, b, c): {(i, j): K_ij}}, all outputs)."""
+    it, adj(M) / sqrt(det M) with adj(M)_ab = r_a . r_b for the adjugate rows
+    r_a of J and det M = (c_0 . r_0)^2; otherwise from the adjugate rows and
+    1/det (the FP32 kernel).  Returns (blocks {(a, b, c): {(i, j): K_ij}}, all outputs)."""
     q, L = p + 2, 2 * p
     gll = oracle.gauss_lobatto(p)
     xg, wg = oracle.gauss_legendre(q)
@@ -433,7 +431,6 @@ def lor_element_modal(p, corners, kappa, beta=None, fp64=True):
     mid = (gll[1:] + gll[:-1]) / 2
     xi = np.array([mid[a] + s * r[a] / math.sqrt(3.0) for a in range(p) for s in (-1, 1)])
     col = jacobian_columns(corner_leaves(corners), (1 - xi) / 2, (1 + xi) / 2)
-    mdiag = [{key: dot3(c, c) for key, c in col[d].items()} for d in range(3)] if fp64 else None
     binof = np.array([int(np.sum(gll[1:-1] < x)) for x in xg])
     wn = np.array([wg[g] / wg[binof == binof[g]].sum() for g in range(q)])
     bw = leaves(wn)  # normalised Gauss weights per axis bin, read from a table
@@ -465,11 +462,10 @@ def lor_element_modal(p, corners, kappa, beta=None, fp64=True):
                     u0, u1, u2 = 2 * a + (g & 1), 2 * b + ((g >> 1) & 1), 2 * c + (g >> 2)
                     c0, c1, c2 = col[0][u1, u2], col[1][u0, u2], col[2][u0, u1]
                     if fp64:
-                        M00, M11, M22 = mdiag[0][u1, u2], mdiag[1][u0, u2], mdiag[2][u0, u1]
-                        M01, M02, M12 = dot3(c0, c1), dot3(c0, c2), dot3(c1, c2)
-                        adj = [M11 * M22 - M12 * M12, M02 * M12 - M01 * M22, M01 * M12 - M02 * M11,
-                               M00 * M22 - M02 * M02, M01 * M02 - M00 * M12, M00 * M11 - M01 * M01]
-                        detM = M00 * adj[0] + M01 * adj[1] + M02 * adj[2]
+                        R = [cross(c1, c2), cross(c2, c0), cross(c0, c1)]
+                        dj = dot3(c0, R[0])
+                        detM = dj * dj
+                        adj = [dot3(R[i], R[j]) for i, j in PAIRS]
                         rr = rsqrt(detM)
                         if bR is not None:
                             W[g] = bR * (detM * rr)
