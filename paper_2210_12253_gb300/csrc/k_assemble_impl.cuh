@@ -38,7 +38,7 @@
 // scale.
 #pragma once
 
-#include "fixed_point.cuh"
+#include "fixed_point_metric.cuh"
 #include "lor_internal.cuh"
 
 namespace {

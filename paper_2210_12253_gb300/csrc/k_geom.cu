@@ -10,7 +10,7 @@
 // memory; per point the metric follows from their cross and dot products,
 // formed in 64-bit fixed point on the integer pipe (fixed_point.cuh), as the
 // LOR assembly does.
-#include "fixed_point.cuh"
+#include "fixed_point_metric.cuh"
 #include "lor_internal.cuh"
 
 namespace {

@@ -412,13 +412,16 @@ def test_fixed_point_operator_mixed_magnitudes(p):
 
 
 @pytest.mark.parametrize("stretch,jitter,p", [((1000.0, 1.0, 1.0), 0.1, 3), ((1.0, 1e-3, 1e2), 0.1, 4),
-                                              ((1.0, 1.0, 1.0), 0.3, 4), ((1.0, 1.0, 1.0), 0.3, 2)])
+                                              ((1.0, 1.0, 1.0), 0.3, 4), ((1.0, 1.0, 1.0), 0.3, 2),
+                                              ((1.0, 1e-3, 1e2), 0.1, 1), ((1e2, 1.0, 1e-3), 0.2, 6)])
 def test_fixed_point_metric_anisotropic_and_distorted(stretch, jitter, p):
-    """The setup and the LOR assembly form M = J^T J, adj(M) and det M in
-    fixed point with one scale per Jacobian-column table: elements stretched
-    1000:1 (and 1e5 between two axes) and strongly distorted ones (vertices
-    moved by up to 30% of the spacing) give the oracle's LOR values (1e-12 of
-    the row maximum) and apply (1e-12 of the maximum)."""
+    """The setup and the LOR assembly form adj(J^T J) from J's adjugate rows
+    and det J from the first of them (fixed point from p = 2 in the assembly,
+    everywhere in the setup): elements stretched 1000:1 (and 1e5 between two
+    axes) and strongly distorted ones (vertices moved by up to 30% of the
+    spacing) give the oracle's LOR values (1e-12 of the row maximum) and
+    apply (1e-12 of the maximum).  Forming the cofactors of M = J^T J instead
+    loses O(eps cond(J)^2) and fails the 1e5 case."""
     from paper_2210_12253_gb300 import LOR
     dims = (3, 2, 2)
     prob = make_problem("t", *dims, p, seed=9, jitter=jitter, kappa="lognormal", rhs="normal")
