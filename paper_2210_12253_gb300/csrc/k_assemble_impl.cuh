@@ -636,12 +636,313 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 assembly from p = 2: eight threads per sub-hex.
+//
+// A sub-hex is handled by a group of 8 consecutive lanes of one warp.
+// - Lane g forms the metric at Gauss point g (fx_metric, as in the kernel
+//   above) and one term of the kappa_s average: for p >= 2 every LOR interval
+//   holds one or two high-order Gauss points per axis, so a sub-hex has at
+//   most 8 and lane (i0, i1, i2) takes point (first + i) of each axis' bin.
+// - The group aligns its 48 metric values (and 8 mass weights) to one scale
+//   (a max over its lanes) and runs the Walsh transforms across its lanes:
+//   the butterfly over point bit k pairs lane g with lane g ^ 2^k, so lane w
+//   ends with Ghat^{ab}(w), which it leaves in shared memory.
+// - Lane m then builds row m of the modal block from shared memory, scales
+//   it by the 3^(-k/2) factors, applies the column half of the Hadamard
+//   sandwich in registers and the row half across the group, converts its 8
+//   nodal entries to FP64 and scatters row m of the block.
+// The arithmetic is fix_block_x's (exact fixed point; the block is held as
+// full rows instead of its symmetric half, whose entries are the same
+// integers), so the values equal the one-thread kernel's up to the
+// summation order of the kappa_s average.  Per thread the state is one
+// point's metric or one block row: no spills, and four times the warps per
+// SM of the one-thread form.
+// ---------------------------------------------------------------------------
+template <int P>
+constexpr int kX8Elems = P * P * P * 8 >= 256 ? 1 : 256 / (P * P * P * 8);
+template <int P>
+constexpr int kX8Threads = kX8Elems<P> * P * P * P * 8 >= 256 ? 256 : ((kX8Elems<P> * P * P * P * 8 + 31) / 32) * 32;
+constexpr int kX8MinBlocks = 4;
+
+__constant__ long long kQ63[7] = {0, q63(1), q63(2), q63(3), q63(4), q63(5), q63(6)};
+
+__device__ __forceinline__ long long x8_walsh_step(long long v, int lane8, int bit) {
+  const long long o = __shfl_xor_sync(0xffffffffu, v, bit);
+  return (lane8 & bit) ? v - o : v + o;  // lane with the bit set holds hi: hi - lo; else lo + hi
+}
+
+template <int P, bool MASS, bool GEN>
+__global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(LorMesh m, LorTables T,
+                                                                          const double* __restrict__ kappa,
+                                                                          const double* __restrict__ beta,
+                                                                          double* __restrict__ vals) {
+  constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kX8Elems<P>, NT = kX8Threads<P>;
+  constexpr int CT = L * L * 3, TAB = 3 * CT;  // one / three Jacobian-column tables per element
+  constexpr int NG = NT / 8, NE = MASS ? 7 : 6;
+  constexpr int GS = NE * 8 + 8;  // a group's stride in Gh (words): groups 0, 2 and 1, 3 of a warp use disjoint banks
+  __shared__ double Ehalf[EPB][36];
+  // the Jacobian columns in FP64, then (in place) as packed fixed-point
+  // words at one scale per column table (1079 - cexp)
+  __shared__ long long tabx[EPB][TAB];
+  __shared__ int cexp[EPB][3];
+  __shared__ double sl0[L], sl1[L];
+  __shared__ long long Gh[NG * GS];  // per group: Ghat^{ab}(w) [ab][w], then What(w)
+  if (threadIdx.x < L) {
+    sl0[threadIdx.x] = T.sub_l0[threadIdx.x];
+    sl1[threadIdx.x] = T.sub_l1[threadIdx.x];
+  }
+  for (int i = threadIdx.x; i < EPB * 3; i += NT) cexp[i / 3][i % 3] = 0;
+  __syncthreads();
+  const int64_t e_first = (int64_t)blockIdx.x * EPB;
+  for (int le = 0; le < EPB; ++le) {
+    const int64_t e = e_first + le;
+    if (e < m.nel) lor_jacobian_columns(m, e, sl0, sl1, L, Ehalf[le], reinterpret_cast<double*>(tabx[le]));
+  }
+  for (int i = threadIdx.x; i < EPB * TAB; i += NT)
+    atomicMax(&cexp[i / TAB][(i % TAB) / CT], fx_expo(__longlong_as_double(tabx[i / TAB][i % TAB])));
+  __syncthreads();
+  for (int i = threadIdx.x; i < EPB * TAB; i += NT) {
+    const double v = __longlong_as_double(tabx[i / TAB][i % TAB]);
+    tabx[i / TAB][i % TAB] = fx_pack(fx_from_double(v, cexp[i / TAB][(i % TAB) / CT]));
+  }
+  __syncthreads();
+
+  const int lane8 = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  long long* gh = Gh + grp * GS;
+  constexpr int NSUB = EPB * P3;
+  // every thread runs every pass (the shuffles take whole warps); a group
+  // past the CTA's sub-hexes or elements computes on sub-hex 0 and stores nothing
+  for (int base = 0; base < NSUB; base += NG) {
+    const int sidx = base + grp;
+    const int le0 = sidx / P3;
+    const bool live = sidx < NSUB && e_first + le0 < m.nel;
+    const int le = live ? le0 : 0, s = live ? sidx % P3 : 0;
+    const int64_t e = e_first + le;
+    const int a = s % P, b = (s / P) % P, c = s / (P * P);
+
+    // kappa_s (and beta_s): lane (i0, i1, i2) holds one Gauss-weighted term
+    double kw = 0.0, bw = 0.0;
+    {
+      const int i0 = lane8 & 1, i1 = (lane8 >> 1) & 1, i2 = lane8 >> 2;
+      if (i0 < T.bin_count[a] && i1 < T.bin_count[b] && i2 < T.bin_count[c]) {
+        const int g0 = T.bin_first[a] + i0, g1 = T.bin_first[b] + i1, g2 = T.bin_first[c] + i2;
+        const double w = (T.bin_w[g1] * T.bin_w[g2]) * T.bin_w[g0];
+        const int64_t pt = e * Q3 + g0 + Q * (g1 + Q * g2);
+        kw = w * kappa[pt];
+        if constexpr (MASS) bw = w * beta[pt];
+      }
+    }
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+      kw += __shfl_xor_sync(0xffffffffu, kw, bit);
+      if constexpr (MASS) bw += __shfl_xor_sync(0xffffffffu, bw, bit);
+    }
+
+    // the metric at Gauss point g = lane8: G_ab = (F_ab r) adj(M)_ab
+    const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
+    const double k64 = kw * (1.0 / 64.0);
+    const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
+                          k64 * ra * rc * T.sub_rinv[b], k64 * ra, k64 * ra * rb * T.sub_rinv[c]};
+    long long X[6];
+    int sF[6];
+    const int g = lane8;
+    const int u0 = 2 * a + (g & 1), u1 = 2 * b + ((g >> 1) & 1), u2 = 2 * c + (g >> 2);
+    Fx C[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      C[0][k] = fx_unpack(tabx[le][3 * (u1 + L * u2) + k]);
+      C[1][k] = fx_unpack(tabx[le][CT + 3 * (u0 + L * u2) + k]);
+      C[2][k] = fx_unpack(tabx[le][2 * CT + 3 * (u0 + L * u1) + k]);
+    }
+    const int scs[3] = {1079 - cexp[le][0], 1079 - cexp[le][1], 1079 - cexp[le][2]};
+    FxMetric mt;
+    fx_metric(C, scs, mt);
+    const double r = lor_rsqrt(mt.detM);  // 1 / det J_e
+    const int er = fx_expo(r);
+    const Fx rx = fx_split(fx_from_double(r, er));
+    const int sG = (1079 - er) - kFxMacShift + mt.sA - kFxMacShift;  // G_ab at sF[ab] + sG
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) {
+      const int ef = fx_expo(FF[ab]);
+      sF[ab] = 1079 - ef;
+      FAcc f = fx_acc();
+      fx_mac(f, fx_split(fx_from_double(FF[ab], ef)), rx);
+      FAcc q = fx_acc();
+      fx_mac(q, fx_split(fx_res(f)), mt.A[ab]);
+      X[ab] = fx_res(q);  // (F_ab r) at most 2^58, G at most 2^60
+    }
+    long long Xw = 0;
+    int sW = 0;
+    if constexpr (MASS) {
+      // W = beta_s r_a r_b r_c / 64 det J_e, det J_e = det M r
+      const double bR = bw * (1.0 / 64.0) * ra * rb * rc;
+      const int eb = fx_expo(bR);
+      const double dj = mt.detM * r;
+      const int ej = fx_expo(dj);
+      FAcc q = fx_acc();
+      fx_mac(q, fx_split(fx_from_double(bR, eb)), fx_split(fx_from_double(dj, ej)));
+      Xw = fx_res(q);  // at most 2^58
+      sW = (1079 - eb) + (1079 - ej) - kFxMacShift;
+    }
+    // one scale for the sub-hex: its largest value below 2^56
+    int mmax = -(1 << 30);
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab)
+      if (X[ab] != 0) mmax = max(mmax, fx_bits((unsigned long long)(X[ab] ^ (X[ab] >> 63))) - (sF[ab] + sG));
+    if constexpr (MASS)
+      if (Xw != 0) mmax = max(mmax, fx_bits((unsigned long long)(Xw ^ (Xw >> 63))) - sW);
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, bit));
+    const int st = 56 - mmax;
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) X[ab] = fx_shift(X[ab], min(st - (sF[ab] + sG), 63));
+    if constexpr (MASS) Xw = fx_shift(Xw, min(st - sW, 63));
+
+    // Walsh transforms across the group (exact: |X| < 2^56 grows to < 2^59)
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+#pragma unroll
+      for (int ab = 0; ab < 6; ++ab) X[ab] = x8_walsh_step(X[ab], lane8, bit);
+      if constexpr (MASS) Xw = x8_walsh_step(Xw, lane8, bit);
+    }
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) gh[ab * 8 + lane8] = X[ab];
+    if constexpr (MASS) gh[48 + lane8] = Xw;
+    __syncwarp();
+
+    // row mm of the modal block: Kt_mn = 3^(-k/2) sum_{a in m, b in n} Ghat^{ab}((m \ a) xor (n \ b))
+    const int mm = lane8, pm = popc3(mm);
+    long long K[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) K[n] = 0;
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      const bool ina = (mm >> aa) & 1;
+      const int u = mm & ~(1 << aa);
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          if ((v >> bb) & 1) continue;
+          const long long t = gh[pair_index(aa, bb) * 8 + (u ^ v)];
+          K[v | (1 << bb)] += ina ? t : 0ll;
+        }
+    }
+#pragma unroll
+    for (int n = 1; n < 8; ++n) {
+      const int k = pm + popc3(n) - 2;  // -1 only on row 0, whose sums are zero
+      const long long f = fix_mul(K[n], kQ63[k > 0 ? k : 1]);
+      K[n] = k > 0 ? f : K[n];
+    }
+    if constexpr (MASS) {
+      // modal mass block: 3^{-(|m|+|n|)/2} What(m xor n)
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int k = pm + popc3(n);
+        const long long w = gh[48 + (mm ^ n)];
+        const long long f = fix_mul(w, kQ63[k > 0 ? k : 1]);
+        K[n] += k > 0 ? f : w;
+      }
+    }
+    __syncwarp();  // the group's shared values are read; the next pass may overwrite them
+
+    // the shift that brings the largest modal entry below 2^56 (as in fix_block_x)
+    unsigned hacc = 0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int hi = (int)(K[n] >> 32);
+      hacc |= (unsigned)(hi ^ (hi >> 31));
+    }
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) hacc |= __shfl_xor_sync(0xffffffffu, hacc, bit);
+    const int bits = hacc ? 64 - __clz((int)hacc) : 32;
+    const int sft = bits > 56 ? bits - 56 : 0;
+    const long long half = sft ? (1ll << (sft - 1)) : 0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) K[n] = (K[n] + half) >> sft;
+    // Hadamard sandwich K <- H Kt H^T: per axis (lo, hi) -> (lo - hi, lo + hi)
+    // on the column index (in registers) and on the row index (across lanes)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int bit = 1 << k;
+#pragma unroll
+      for (int j0 = 0; j0 < 8; ++j0) {
+        if (j0 & bit) continue;
+        const long long x = K[j0], y = K[j0 | bit];
+        K[j0] = x - y;
+        K[j0 | bit] = x + y;
+      }
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const long long o = __shfl_xor_sync(0xffffffffu, K[n], bit);
+        K[n] = (mm & bit) ? o + K[n] : K[n] - o;
+      }
+    }
+    const int scale = st - sft;
+    double Kd[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) Kd[n] = from_fix(K[n], scale);
+    if (!live) continue;
+
+    // scatter row r = mm of the block (as the one-thread kernel, one row per lane)
+    const int rr = mm;
+    if constexpr (GEN) {
+      constexpr int N = P + 1;
+      const int64_t* dm = m.edofs + e * (N * N * N);
+      int64_t dv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) dv[t] = dm[(a + (t & 1)) + N * ((b + ((t >> 1) & 1)) + N * (c + (t >> 2)))];
+      const int64_t rb0 = m.rowptr[dv[rr]], re0 = m.rowptr[dv[rr] + 1];
+      if (m.ess[dv[rr]]) {
+        const int64_t pos = lor_find_col(m.colidx, rb0, re0, dv[rr]);
+        if (pos >= 0) vals[pos] = 1.0;
+        continue;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (m.ess[dv[t]]) continue;
+        const int64_t pos = lor_find_col(m.colidx, rb0, re0, dv[t]);
+        if (pos >= 0) atomic_add<double>(vals + pos, Kd[t]);
+      }
+    } else {
+      const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+      const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
+      const int64_t I = I0 + (rr & 1), J = J0 + ((rr >> 1) & 1), Kk = K0 + (rr >> 2);
+      const int64_t base_pos = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
+      if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) {
+        vals[base_pos] = 1.0;
+        continue;
+      }
+      const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
+        if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
+        const int di = (t & 1) - (rr & 1), dj = ((t >> 1) & 1) - ((rr >> 1) & 1), dk = (t >> 2) - (rr >> 2);
+        atomic_add<double>(vals + base_pos + (dk * cy + dj) * cx + di, Kd[t]);
+      }
+    }
+  }
+}
+
+constexpr bool kAsmX8 = true;  // FP64 from p = 2: the eight-thread form
+
 template <int P, typename VT, bool MASS, bool GEN>
-void launch_assemble_p(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
-                       cudaStream_t s) {
-  k_assemble<P, VT, MASS, GEN><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(
-      m, T, kappa, beta, vals);
+cudaError_t launch_assemble_p(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
+                              cudaStream_t s) {
+  if constexpr (kAsmX8 && sizeof(VT) == sizeof(double) && P >= 2) {
+    // one lane per high-order Gauss point of a sub-hex's bins: one or two per axis
+    for (int a = 0; a < P; ++a)
+      if (T.bin_count[a] < 1 || T.bin_count[a] > 2) return cudaErrorInvalidValue;
+    k_assemble_x8<P, MASS, GEN><<<(unsigned)((m.nel + kX8Elems<P> - 1) / kX8Elems<P>), kX8Threads<P>, 0, s>>>(
+        m, T, kappa, beta, (double*)vals);
+  } else {
+    k_assemble<P, VT, MASS, GEN><<<(unsigned)((m.nel + kElemsPerCta<P> - 1) / kElemsPerCta<P>), kAsmThreads<P>, 0, s>>>(
+        m, T, kappa, beta, vals);
+  }
   lor_count_launch();
+  return cudaSuccess;
 }
 
 template <typename VT, bool MASS, bool GEN>
@@ -649,7 +950,10 @@ cudaError_t assemble_dispatch(const LorMesh& m, const LorTables& T, const double
                               cudaStream_t s) {
   switch (m.p) {
 #define LOR_CASE(P) \
-  case P: launch_assemble_p<P, VT, MASS, GEN>(m, T, kappa, beta, vals, s); break;
+  case P: {                                                                  \
+    const cudaError_t err = launch_assemble_p<P, VT, MASS, GEN>(m, T, kappa, beta, vals, s); \
+    if (err != cudaSuccess) return err;                                      \
+  } break;
     LOR_CASE(1) LOR_CASE(2) LOR_CASE(3) LOR_CASE(4) LOR_CASE(5)
     LOR_CASE(6) LOR_CASE(7) LOR_CASE(8) LOR_CASE(9) LOR_CASE(10)
 #undef LOR_CASE
