@@ -7,11 +7,10 @@
 
 #include "fixed_point.cuh"
 
-// -X in split form
-__device__ __forceinline__ Fx fx_neg(Fx x) {
-  const int nz = x.l != 0;
-  return Fx{-x.h - nz, nz ? (1 << 28) - x.l : 0};
-}
+// -X as a split with a non-positive low part (-h, -l): the multiply-add's
+// identity X C = Xh Ch 2^56 + (Xh Cl + Xl Ch) 2^28 + Xl Cl holds for any
+// split with |Xl| < 2^28, and the dropped |Xl Cl| / 2^56 stays below one unit
+__device__ __forceinline__ Fx fx_neg(Fx x) { return Fx{-x.h, -x.l}; }
 
 // The metric of a trilinear map at one point from its Jacobian columns c_d
 // in fixed point (C[d][k], column d at scale s_d, |C| <= 2^57): the adjugate
@@ -43,9 +42,9 @@ __device__ __forceinline__ void fx_metric(const Fx (&C)[3][3], const int (&sc)[3
       R[a][k] = fx_res(t);  // at most 2^59, scale s_b + s_c - 56
       fx_or(o, R[a][k]);
     }
-    const int d = o ? 58 - fx_bits(o) : 0;
+    const int d = o ? 58 - fx_bits(o) : 0;  // -2 <= d <= 58
 #pragma unroll
-    for (int k = 0; k < 3; ++k) R[a][k] = fx_shift(R[a][k], d);
+    for (int k = 0; k < 3; ++k) R[a][k] = fx_rescale(R[a][k], d);
     sR[a] = sc[b] + sc[c] - kFxMacShift + d;
   }
   Fx Rx[3][3];

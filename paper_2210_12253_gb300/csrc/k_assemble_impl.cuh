@@ -2,11 +2,14 @@
 // (kernel template; instantiated without the reaction term in k_assemble.cu
 // and with it in k_assemble_mass.cu).
 //
-// One CTA per macro element (a high-order element split at the Gauss-Lobatto
-// points into p^3 sub-hexes, Section 2.1), one thread per sub-hex, as in the
-// paper's A1 (one block per macro element, one thread per sub-element).  Each
-// thread forms its sub-hex's 8x8 stiffness block by 2x2x2 Gauss quadrature on
-// the sub-hex's trilinear map with the sub-hex coefficient kappa_s (the
+// One CTA per macro element or a few (a high-order element split at the
+// Gauss-Lobatto points into p^3 sub-hexes, Section 2.1).  The paper's A1 has
+// one block per macro element and one thread per sub-element.  Here the
+// FP32 values and the FP64 values at p = 1 follow that form (k_assemble); the
+// FP64 values from p = 2 give each sub-hex 8 threads, one per Gauss point of
+// the 2x2x2 rule and then one per row of its block (k_assemble_x8).  Either
+// forms the sub-hex's 8x8 stiffness block by 2x2x2 Gauss quadrature on the
+// sub-hex's trilinear map with the sub-hex coefficient kappa_s (the
 // Gauss-weight average of kappa over the high-order Gauss points inside the
 // sub-hex), then adds the entries straight into the CSR values at positions
 // computed in closed form (no macro-element sparse block is stored), with
@@ -22,20 +25,20 @@
 // Geometry: the sub-hex map is the element's trilinear map restricted to the
 // sub-box, so J_sub(tau) = J_e(xi(tau)) diag(r_a, r_b, r_c) with r the half
 // widths of the GLL intervals; only the element Jacobian columns (bilinear in
-// the two other coordinates) are evaluated, in FP64.  In FP64 the metric is
-// formed from M = J_e^T J_e: with V = r_a r_b r_c,
+// the two other coordinates) are evaluated, in FP64.  With V = r_a r_b r_c
+// and M = J_e^T J_e,
 //   detJ_sub J_sub^-1 J_sub^-T = adj(J_sub^T J_sub) / detJ_sub
 //                             = V / (r_a r_b) adj(M)_ab / detJ_e,
-// detJ_e = sqrt(det M).  M's diagonal |c_d|^2 depends on the two coordinates
-// its column is tabulated on, so it is tabulated per element too; per Gauss
-// point remain the three off-diagonal products, the cofactors, det M and one
-// reciprocal square root.  These products run in 64-bit fixed point on the
-// integer pipe (fixed_point.cuh): the column tables are converted once per
-// element, one scale per table, and each of M, adj(M) and det M is
-// renormalised per Gauss point; only 1/sqrt(det M) (range-reduced, as in the
-// setup) and the kappa_s averages stay FP64.  The 48 metric values and 8 mass
-// weights of a sub-hex then enter the block algebra as integers on one
-// scale.
+// where adj(M)_ab = A_a . A_b for the adjugate rows A_a = c_b x c_c of J_e
+// and detJ_e = |c_0 . A_0| (formed this way the error is O(eps cond(J_e));
+// M's cofactors would lose O(eps cond(J_e)^2) on stretched elements).  In
+// the FP64 values from p = 2 these products run in 64-bit fixed point on the
+// integer pipe (fixed_point_metric.cuh): the column tables are converted once
+// per element, one scale per table, and the rows and adj(M) are renormalised
+// per Gauss point; only 1/detJ_e (range-reduced reciprocal square root of
+// (detJ_e)^2, as in the setup) and the kappa_s averages stay FP64.  The 48
+// metric values and 8 mass weights of a sub-hex then enter the block algebra
+// as integers on one scale.
 #pragma once
 
 #include "fixed_point_metric.cuh"
@@ -285,19 +288,13 @@ template <int P>
 constexpr int kAsmThreads = P * P * P >= 64 ? (P * P * P >= 256 ? 256 : ((P * P * P + 31) / 32) * 32)
                                             : ((kElemsPerCta<P> * P * P * P + 31) / 32) * 32;
 
-// FP64: 512 threads' worth of CTAs per SM (8 CTAs of 64 threads at p = 4,
-// 128 registers per thread, the rest of the block's state spilled to local
-// memory): the kernel is latency-bound.  Measured at p = 4 with the metric's
-// products in fixed point (event-timed, c2; in brackets GDOF/s at ~20M DOFs):
-// 512 threads 0.278 ms (1.21), 640 threads 0.289 ms (1.15), 384 threads
-// 0.295 ms (1.10).  With the metric in FP64 (the FP64 pipe then the bound)
-// 640 threads had been best: 0.278 ms, against 0.300 ms at 128 registers.
-template <int P, typename VT>
-constexpr int kAsmThreadBudget = P >= 2 ? 512 : 640;  // p = 1 keeps the FP64 metric (see FXG)
+// FP64 (this kernel's FP64 form serves p = 1; from p = 2 k_assemble_x8
+// below): 640 threads' worth of CTAs per SM, the measured best with the
+// metric in FP64 (0.278 ms against 0.300 ms at 128 registers, p = 4).
+constexpr int kAsmThreadBudget = 640;
 template <int P, typename VT>
 constexpr int kAsmMinBlocks =
-    sizeof(VT) == sizeof(double) ? (kAsmThreadBudget<P, VT> / kAsmThreads<P> > 1 ? kAsmThreadBudget<P, VT> / kAsmThreads<P> : 1)
-                                 : 1;
+    sizeof(VT) == sizeof(double) ? (kAsmThreadBudget / kAsmThreads<P> > 1 ? kAsmThreadBudget / kAsmThreads<P> : 1) : 1;
 
 template <typename VT>
 __device__ __forceinline__ void atomic_add(VT* p, VT v) { atomicAdd(p, v); }
@@ -310,16 +307,8 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kElemsPerCta<P>;
   constexpr int TAB = 3 * L * L * 3;  // three Jacobian-column tables per element
   constexpr bool F32 = sizeof(VT) == sizeof(float);
-  // FP64: the metric's products in fixed point from p = 2 (at p = 1 an element
-  // has one sub-hex, and converting its column tables cost more than the
-  // products saved: 0.24 against 0.38 GDOF/s at 4M DOFs)
-  constexpr bool FXG = !F32 && P >= 2;
   __shared__ double Ehalf[EPB][36];
   __shared__ double tab[EPB][TAB];
-  // FP64 mode: the Jacobian columns in fixed point (packed words, one scale
-  // per column table: 1079 - cexp) and |c_d|^2 formed from them
-  __shared__ long long tabx[FXG ? EPB : 1][FXG ? TAB : 1];
-  __shared__ int cexp[FXG ? EPB : 1][3];
   __shared__ float tabf[F32 ? EPB : 1][F32 ? TAB : 1];
   __shared__ double sl0[L], sl1[L];
   if (threadIdx.x < L) {
@@ -337,16 +326,6 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
   }
   if constexpr (F32) {
     for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x) tabf[i / TAB][i % TAB] = (float)tab[i / TAB][i % TAB];
-    __syncthreads();
-  } else if constexpr (FXG) {
-    constexpr int CT = L * L * 3;  // one column table
-    for (int i = threadIdx.x; i < EPB * 3; i += blockDim.x) cexp[i / 3][i % 3] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x)
-      atomicMax(&cexp[i / TAB][(i % TAB) / CT], fx_expo(tab[i / TAB][i % TAB]));
-    __syncthreads();
-    for (int i = threadIdx.x; i < EPB * TAB; i += blockDim.x)
-      tabx[i / TAB][i % TAB] = fx_pack(fx_from_double(tab[i / TAB][i % TAB], cexp[i / TAB][(i % TAB) / CT]));
     __syncthreads();
   }
   const int nwork = EPB * P3;
@@ -375,102 +354,11 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
     VT G[F32 ? 6 : 1][F32 ? 8 : 1];  // FP32: the metric (pair order 00, 01, 02, 11, 12, 22)
     VT W[(MASS && F32) ? 8 : 1];      // FP32 reaction: W(g) = beta_s detJ_sub(g) / 64 (Gauss weights 1)
     const int u0a = 2 * a, u1a = 2 * b, u2a = 2 * c;
-    // FP64: the metric from the adjugate rows of J_e (cross and dot products of
-    // the columns' fixed-point tables, fx_metric), 1/det J_e by the
-    // range-reduced FP64 reciprocal square root of det M = (det J_e)^2,
-    // G = F r adj(M) in fixed point; the sub-hex's 48 metric values (and 8 mass
-    // weights) aligned to one scale for the block.
-    long long X[FXG ? 6 : 1][FXG ? 8 : 1];
-    long long Xw[(MASS && FXG) ? 8 : 1];
-    int st = 0;
-    double Gd[(!F32 && !FXG) ? 6 : 1][(!F32 && !FXG) ? 8 : 1];  // the metric in FP64 (p = 1)
-    double Wd[(MASS && !F32 && !FXG) ? 8 : 1];
-    if constexpr (FXG) {
-      const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
-      const double k64 = ks * (1.0 / 64.0);
-      const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
-                            k64 * ra * rc * T.sub_rinv[b], k64 * ra, k64 * ra * rb * T.sub_rinv[c]};
-      Fx FFx[6];
-      int sF[6];
-#pragma unroll
-      for (int ab = 0; ab < 6; ++ab) {
-        const int ef = fx_expo(FF[ab]);
-        FFx[ab] = fx_split(fx_from_double(FF[ab], ef));
-        sF[ab] = 1079 - ef;
-      }
-      Fx bRx = Fx{0, 0};
-      int sbR = 0;
-      if constexpr (MASS) {
-        const double bR = bs * (1.0 / 64.0) * ra * rb * rc;
-        const int eb = fx_expo(bR);
-        bRx = fx_split(fx_from_double(bR, eb));
-        sbR = 1079 - eb;
-      }
-      constexpr int CT = L * L * 3;
-      const int scs[3] = {1079 - cexp[le][0], 1079 - cexp[le][1], 1079 - cexp[le][2]};
-      const long long* x0 = tabx[le];
-      const long long* x1 = tabx[le] + CT;
-      const long long* x2 = tabx[le] + 2 * CT;
-      int sG[8];
-      int sW[MASS ? 8 : 1];
-#pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        const int u0 = u0a + (g & 1), u1 = u1a + ((g >> 1) & 1), u2 = u2a + (g >> 2);
-        Fx C[3][3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          C[0][k] = fx_unpack(x0[3 * (u1 + L * u2) + k]);
-          C[1][k] = fx_unpack(x1[3 * (u0 + L * u2) + k]);
-          C[2][k] = fx_unpack(x2[3 * (u0 + L * u1) + k]);
-        }
-        FxMetric mt;
-        fx_metric(C, scs, mt);
-        const double r = lor_rsqrt(mt.detM);  // 1 / det J_e
-        const int er = fx_expo(r);
-        const Fx rx = fx_split(fx_from_double(r, er));
-        const int sr = 1079 - er;
-        // G_ab = (F_ab r) adj(M)_ab: (F_ab r) at most 2^58, G at most 2^60
-#pragma unroll
-        for (int ab = 0; ab < 6; ++ab) {
-          FAcc f = fx_acc();
-          fx_mac(f, FFx[ab], rx);
-          FAcc q = fx_acc();
-          fx_mac(q, fx_split(fx_res(f)), mt.A[ab]);
-          X[ab][g] = fx_res(q);
-        }
-        sG[g] = sr - kFxMacShift + mt.sA - kFxMacShift;  // G_ab at sF[ab] + sG[g]
-        if constexpr (MASS) {
-          // W = beta_s r_a r_b r_c / 64 det J_e, det J_e = det M r
-          const double dj = mt.detM * r;
-          const int ej = fx_expo(dj);
-          FAcc q = fx_acc();
-          fx_mac(q, bRx, fx_split(fx_from_double(dj, ej)));
-          Xw[g] = fx_res(q);  // at most 2^58
-          sW[g] = sbR + (1079 - ej) - kFxMacShift;
-        }
-      }
-      // one scale for the sub-hex: its largest value below 2^56
-      int mmax = -(1 << 30);
-#pragma unroll
-      for (int ab = 0; ab < 6; ++ab)
-#pragma unroll
-        for (int g = 0; g < 8; ++g)
-          if (X[ab][g] != 0)
-            mmax = max(mmax, fx_bits((unsigned long long)(X[ab][g] ^ (X[ab][g] >> 63))) - (sF[ab] + sG[g]));
-      if constexpr (MASS)
-#pragma unroll
-        for (int g = 0; g < 8; ++g)
-          if (Xw[g] != 0) mmax = max(mmax, fx_bits((unsigned long long)(Xw[g] ^ (Xw[g] >> 63))) - sW[g]);
-      st = 56 - mmax;
-#pragma unroll
-      for (int ab = 0; ab < 6; ++ab)
-#pragma unroll
-        for (int g = 0; g < 8; ++g) X[ab][g] = fx_shift(X[ab][g], min(st - (sF[ab] + sG[g]), 63));
-      if constexpr (MASS)
-#pragma unroll
-        for (int g = 0; g < 8; ++g) Xw[g] = fx_shift(Xw[g], min(st - sW[g], 63));
-    } else if constexpr (!F32) {
-      // p = 1: the same metric in FP64 (adjugate rows of J_e)
+    // FP64 (p = 1): the metric in FP64 from the adjugate rows of J_e and
+    // 1/det J_e by the range-reduced reciprocal square root of (det J_e)^2
+    double Gd[F32 ? 1 : 6][F32 ? 1 : 8];
+    double Wd[(MASS && !F32) ? 8 : 1];
+    if constexpr (!F32) {
       const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
       const double k64 = ks * (1.0 / 64.0);
       const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
@@ -582,8 +470,7 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
       hadamard_axis<VT, 2>(K);
     } else {
       // FP64: the same linear steps in 64-bit fixed point (see fix_block_x)
-      if constexpr (FXG) fix_block_x<MASS>(X, Xw, st, K);
-      else fix_block<MASS>(Gd, Wd, K);
+      fix_block<MASS>(Gd, Wd, K);
     }
 
     // Scatter into the CSR values (closed-form positions on the structured
@@ -681,6 +568,7 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
   constexpr int CT = L * L * 3, TAB = 3 * CT;  // one / three Jacobian-column tables per element
   constexpr int NG = NT / 8, NE = MASS ? 7 : 6;
   constexpr int GS = NE * 8 + 8;  // a group's stride in Gh (words): groups 0, 2 and 1, 3 of a warp use disjoint banks
+  constexpr int ZW = NE * 8;      // a zero word in each group's block (the terms a row does not have)
   __shared__ double Ehalf[EPB][36];
   // the Jacobian columns in FP64, then (in place) as packed fixed-point
   // words at one scale per column table (1079 - cexp)
@@ -692,6 +580,7 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
     sl0[threadIdx.x] = T.sub_l0[threadIdx.x];
     sl1[threadIdx.x] = T.sub_l1[threadIdx.x];
   }
+  if (threadIdx.x < NG) Gh[threadIdx.x * GS + ZW] = 0;
   for (int i = threadIdx.x; i < EPB * 3; i += NT) cexp[i / 3][i % 3] = 0;
   __syncthreads();
   const int64_t e_first = (int64_t)blockIdx.x * EPB;
@@ -739,13 +628,30 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
       if constexpr (MASS) bw += __shfl_xor_sync(0xffffffffu, bw, bit);
     }
 
-    // the metric at Gauss point g = lane8: G_ab = (F_ab r) adj(M)_ab
+    // F_ab = kappa_s (r_a r_b r_c) / (r_a r_b) / 64 in fixed point: lane ab < 6
+    // forms F_ab (the 1/64 goes into its scale) and the group shares them
     const double ra = T.sub_r[a], rb = T.sub_r[b], rc = T.sub_r[c];
-    const double k64 = kw * (1.0 / 64.0);
-    const double FF[6] = {k64 * rb * rc * T.sub_rinv[a], k64 * rc, k64 * rb,
-                          k64 * ra * rc * T.sub_rinv[b], k64 * ra, k64 * ra * rb * T.sub_rinv[c]};
-    long long X[6];
+    Fx FFx[6];
     int sF[6];
+    {
+      const int ab = lane8;
+      const double xa = ab == 1 ? rc : (ab == 0 || ab == 2) ? rb : ra;
+      const double ya = (ab == 0 || ab == 3) ? rc : ab == 5 ? rb : 1.0;
+      const double za = ab == 0 ? T.sub_rinv[a] : ab == 3 ? T.sub_rinv[b] : ab == 5 ? T.sub_rinv[c] : 1.0;
+      const double f = ((kw * xa) * ya) * za;
+      const int ef = fx_expo(f);
+      const Fx fx = fx_split(fx_from_double(f, ef));
+      const int sf = 1079 - ef + 6;
+      const int gb = threadIdx.x & 24;  // the group's first lane in the warp
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        FFx[k].h = __shfl_sync(0xffffffffu, fx.h, gb + k);
+        FFx[k].l = __shfl_sync(0xffffffffu, fx.l, gb + k);
+        sF[k] = __shfl_sync(0xffffffffu, sf, gb + k);
+      }
+    }
+    // the metric at Gauss point g = lane8: G_ab = (F_ab r) adj(M)_ab
+    long long X[6];
     const int g = lane8;
     const int u0 = 2 * a + (g & 1), u1 = 2 * b + ((g >> 1) & 1), u2 = 2 * c + (g >> 2);
     Fx C[3][3];
@@ -764,10 +670,8 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
     const int sG = (1079 - er) - kFxMacShift + mt.sA - kFxMacShift;  // G_ab at sF[ab] + sG
 #pragma unroll
     for (int ab = 0; ab < 6; ++ab) {
-      const int ef = fx_expo(FF[ab]);
-      sF[ab] = 1079 - ef;
       FAcc f = fx_acc();
-      fx_mac(f, fx_split(fx_from_double(FF[ab], ef)), rx);
+      fx_mac(f, FFx[ab], rx);
       FAcc q = fx_acc();
       fx_mac(q, fx_split(fx_res(f)), mt.A[ab]);
       X[ab] = fx_res(q);  // (F_ab r) at most 2^58, G at most 2^60
@@ -776,14 +680,14 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
     int sW = 0;
     if constexpr (MASS) {
       // W = beta_s r_a r_b r_c / 64 det J_e, det J_e = det M r
-      const double bR = bw * (1.0 / 64.0) * ra * rb * rc;
+      const double bR = ((bw * ra) * rb) * rc;  // the 1/64 goes into the scale
       const int eb = fx_expo(bR);
       const double dj = mt.detM * r;
       const int ej = fx_expo(dj);
       FAcc q = fx_acc();
       fx_mac(q, fx_split(fx_from_double(bR, eb)), fx_split(fx_from_double(dj, ej)));
       Xw = fx_res(q);  // at most 2^58
-      sW = (1079 - eb) + (1079 - ej) - kFxMacShift;
+      sW = (1079 - eb + 6) + (1079 - ej) - kFxMacShift;
     }
     // one scale for the sub-hex: its largest value below 2^56
     int mmax = -(1 << 30);
@@ -825,8 +729,7 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
           if ((v >> bb) & 1) continue;
-          const long long t = gh[pair_index(aa, bb) * 8 + (u ^ v)];
-          K[v | (1 << bb)] += ina ? t : 0ll;
+          K[v | (1 << bb)] += gh[ina ? pair_index(aa, bb) * 8 + (u ^ v) : ZW];
         }
     }
 #pragma unroll
@@ -883,6 +786,14 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
     double Kd[8];
 #pragma unroll
     for (int n = 0; n < 8; ++n) Kd[n] = from_fix(K[n], scale);
+    // the essential corners of the sub-hex: lane t tests corner t, a ballot shares them
+    unsigned essb = 0;
+    if constexpr (!GEN) {
+      const int64_t ex = e % m.nex, ey = (e / m.nex) % m.ney, ez = e / ((int64_t)m.nex * m.ney);
+      const bool es = lor_is_essential(ex * P + a + (mm & 1), ey * P + b + ((mm >> 1) & 1), ez * P + c + (mm >> 2),
+                                       m.nx, m.ny, m.nz);
+      essb = (__ballot_sync(0xffffffffu, es) >> (threadIdx.x & 24)) & 0xffu;
+    }
     if (!live) continue;
 
     // scatter row r = mm of the block (as the one-thread kernel, one row per lane)
@@ -910,15 +821,14 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
       const int64_t I0 = ex * P + a, J0 = ey * P + b, K0 = ez * P + c;
       const int64_t I = I0 + (rr & 1), J = J0 + ((rr >> 1) & 1), Kk = K0 + (rr >> 2);
       const int64_t base_pos = lor_entry_pos(I, J, Kk, 0, 0, 0, m.nx, m.ny, m.nz);
-      if (lor_is_essential(I, J, Kk, m.nx, m.ny, m.nz)) {
+      if ((essb >> rr) & 1u) {
         vals[base_pos] = 1.0;
         continue;
       }
       const int64_t cx = lor_axis_count(I, m.nx), cy = lor_axis_count(J, m.ny);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const int64_t I2 = I0 + (t & 1), J2 = J0 + ((t >> 1) & 1), K2 = K0 + (t >> 2);
-        if (lor_is_essential(I2, J2, K2, m.nx, m.ny, m.nz)) continue;
+        if ((essb >> t) & 1u) continue;
         const int di = (t & 1) - (rr & 1), dj = ((t >> 1) & 1) - ((rr >> 1) & 1), dk = (t >> 2) - (rr >> 2);
         atomic_add<double>(vals + base_pos + (dk * cy + dj) * cx + di, Kd[t]);
       }
@@ -926,12 +836,10 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
   }
 }
 
-constexpr bool kAsmX8 = true;  // FP64 from p = 2: the eight-thread form
-
 template <int P, typename VT, bool MASS, bool GEN>
 cudaError_t launch_assemble_p(const LorMesh& m, const LorTables& T, const double* kappa, const double* beta, VT* vals,
                               cudaStream_t s) {
-  if constexpr (kAsmX8 && sizeof(VT) == sizeof(double) && P >= 2) {
+  if constexpr (sizeof(VT) == sizeof(double) && P >= 2) {
     // one lane per high-order Gauss point of a sub-hex's bins: one or two per axis
     for (int a = 0; a < P; ++a)
       if (T.bin_count[a] < 1 || T.bin_count[a] > 2) return cudaErrorInvalidValue;
