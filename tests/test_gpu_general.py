@@ -134,7 +134,8 @@ def permuted_csr(rp, ci, v, perm):
     return SimpleNamespace(indptr=indptr, indices=indices, data=data, nnz=int(indptr[-1]))
 
 
-@pytest.mark.parametrize("dims,p", [((2, 2, 2), 1), ((2, 3, 2), 2), ((2, 2, 2), 4), ((2, 2, 2), 6)])
+# (3, 3, 3) at p = 2: 27 elements, the FP64 assembly's last four-element CTA three slots short
+@pytest.mark.parametrize("dims,p", [((2, 2, 2), 1), ((2, 3, 2), 2), ((3, 3, 3), 2), ((2, 2, 2), 4), ((2, 2, 2), 6)])
 def test_general_pattern_and_values(dims, p):
     prob, mesh, op, perm, *_ = make(dims, p)
     rp, ci = op.build_pattern()

@@ -77,6 +77,17 @@ def test_lor_values_with_reaction_fp64(dims, p):
     op.close()
 
 
+def test_lor_values_with_reaction_partial_last_cta():
+    """p = 2, 27 elements: the last four-element CTA of the FP64 assembly
+    holds three empty slots."""
+    prob, mesh, op, beta = setup((3, 3, 3), 2)
+    op.build_pattern_internal()
+    v = op.assemble(torch.float64).cpu().numpy()
+    orp, _, ov = oracle.lor_assemble(mesh, 2, 4, prob.kappa, True, beta=beta)
+    assert rowwise_rel_err(orp, v, ov) <= 1e-12
+    op.close()
+
+
 @pytest.mark.parametrize("dims,p", [((3, 2, 4), 2), ((4, 3, 3), 4), ((2, 2, 2), 6), ((2, 2, 2), 10)])
 def test_lor_values_with_reaction_fp32(dims, p):
     prob, mesh, op, beta = setup(dims, p)

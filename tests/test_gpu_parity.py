@@ -74,6 +74,19 @@ def test_lor_values_fp64(dims, p):
     assert rowwise_rel_err(orp, v, ov) <= 1e-12
 
 
+@pytest.mark.parametrize("dims", [(3, 3, 3), (5, 2, 3)])
+def test_lor_values_fp64_partial_last_cta(dims):
+    """At p = 2 the FP64 assembly takes four elements per CTA; 27 and 30
+    elements leave the last CTA three and two slots short, whose threads
+    compute on a stand-in sub-hex and store nothing."""
+    p = 2
+    prob, mesh, op = setup(dims, p)
+    op.build_pattern_internal()
+    v = op.assemble(torch.float64).cpu().numpy()
+    orp, _, ov = oracle.lor_assemble(mesh, p, p + 2, prob.kappa, True)
+    assert rowwise_rel_err(orp, v, ov) <= 1e-12
+
+
 @pytest.mark.parametrize("dims,p", [((3, 2, 4), 2), ((4, 3, 3), 4), ((2, 1, 2), 6)])
 def test_lor_values_fp32(dims, p):
     prob, mesh, op = setup(dims, p)
