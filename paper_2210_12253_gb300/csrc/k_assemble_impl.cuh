@@ -543,8 +543,9 @@ __global__ void __launch_bounds__(kAsmThreads<P>, kAsmMinBlocks<P, VT>) k_assemb
 // full rows instead of its symmetric half, whose entries are the same
 // integers), so the values equal the one-thread kernel's up to the
 // summation order of the kappa_s average.  Per thread the state is one
-// point's metric or one block row: no spills, and four times the warps per
-// SM of the one-thread form.
+// point's metric or one block row: 64 registers without spills up to p = 5,
+// and twice the active warps per SM of the one-thread form (30 against 15 at
+// p = 4).
 // ---------------------------------------------------------------------------
 template <int P>
 constexpr int kX8Elems = P * P * P * 8 >= 256 ? 1 : 256 / (P * P * P * 8);
@@ -567,7 +568,9 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
   constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kX8Elems<P>, NT = kX8Threads<P>;
   constexpr int CT = L * L * 3, TAB = 3 * CT;  // one / three Jacobian-column tables per element
   constexpr int NG = NT / 8, NE = MASS ? 7 : 6;
-  constexpr int GS = NE * 8 + 8;  // a group's stride in Gh (words): groups 0, 2 and 1, 3 of a warp use disjoint banks
+  // a group's stride in Gh (words, 8 bytes): GS = 8 (mod 16), so the two groups of a
+  // half-warp (one phase of a 64-bit access) fall in opposite halves of the banks
+  constexpr int GS = NE * 8 + 8;
   constexpr int ZW = NE * 8;      // a zero word in each group's block (the terms a row does not have)
   __shared__ double Ehalf[EPB][36];
   // the Jacobian columns in FP64, then (in place) as packed fixed-point
