@@ -568,8 +568,9 @@ __global__ void __launch_bounds__(kX8Threads<P>, kX8MinBlocks) k_assemble_x8(Lor
   constexpr int Q = P + 2, Q3 = Q * Q * Q, P3 = P * P * P, L = 2 * P, EPB = kX8Elems<P>, NT = kX8Threads<P>;
   constexpr int CT = L * L * 3, TAB = 3 * CT;  // one / three Jacobian-column tables per element
   constexpr int NG = NT / 8, NE = MASS ? 7 : 6;
-  // a group's stride in Gh (words, 8 bytes): GS = 8 (mod 16), so the two groups of a
-  // half-warp (one phase of a 64-bit access) fall in opposite halves of the banks
+  // a group's stride in Gh (words, 8 bytes).  Without the reaction term GS = 56 = 8
+  // (mod 16): the two groups of a half-warp (one phase of a 64-bit access) fall in
+  // opposite halves of the banks.  With it GS = 64 puts them on the same banks.
   constexpr int GS = NE * 8 + 8;
   constexpr int ZW = NE * 8;      // a zero word in each group's block (the terms a row does not have)
   __shared__ double Ehalf[EPB][36];
