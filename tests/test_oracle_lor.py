@@ -366,3 +366,26 @@ def test_general_lor_on_cube_in_cube_is_q1_matrix_of_its_lor_mesh(m, p):
     np.testing.assert_array_equal(rp2, rp)
     np.testing.assert_array_equal(ci2, ci)
     np.testing.assert_allclose(csr_to_dense(rp2, ci2, v2, N), eliminate(A, ess.astype(bool)), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("p", range(2, 11))
+def test_each_lor_interval_holds_one_or_two_gauss_points(p):
+    """The FP64 LOR assembly from p = 2 gives each high-order Gauss point of
+    a sub-hex's kappa_s average a lane of an 8-lane group, so every LOR
+    interval must hold one or two of the q = p + 2 Gauss-Legendre points per
+    axis (a point on a GLL node belongs to the lower interval); its launcher
+    returns an error otherwise.  p = 1 (three points in its one interval)
+    uses the one-thread kernel."""
+    gx, _ = oracle.gauss_legendre(p + 2)
+    gll = oracle.gauss_lobatto(p)
+    counts = np.bincount([int(np.sum(gll[1:p] < x)) for x in gx], minlength=p)
+    assert counts.min() >= 1 and counts.max() <= 2, counts
+    # the same count from the oracle's kappa_s: a coefficient that is 1 at
+    # one Gauss point (and 0 elsewhere) reaches exactly one sub-hex per axis
+    q = p + 2
+    for g in range(q):
+        kappa = np.zeros((1, q, q, q))
+        kappa[0, 0, 0, g] = 1.0  # Gauss point (g, 0, 0), the first index fastest
+        ks = oracle.lor_kappa_sub(p, q, kappa).reshape(p, p, p)  # [c][b][a]
+        hit = np.nonzero(ks[0, 0, :])[0]
+        assert len(hit) == 1 and hit[0] == int(np.sum(gll[1:p] < gx[g]))
